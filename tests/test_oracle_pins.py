@@ -1,0 +1,290 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself:
+closed forms, brute-force dense solves, invariants, special cases.  Planted-mistake
+tests at the end show that plausible slips in the oracle fail one of these pins."""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import labpsd as L
+from paper_1308_2445_gb300 import pufe_inputs as pi
+
+
+def _angles(A, B, M=None):
+    """Largest principal angle between span(A) and span(B) (M-inner product if given)."""
+    if M is not None:
+        C = np.linalg.cholesky(M)
+        A, B = C.T @ A, C.T @ B
+    qa, _ = np.linalg.qr(A)
+    qb, _ = np.linalg.qr(B)
+    s = np.linalg.svd(qa.conj().T @ qb, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+# ------------------------------------------------------------------ closed form
+@pytest.mark.parametrize("nev", [7, 19, 27])
+def test_closed_form_eigenvalues(nev):
+    # unenriched periodic Q1, constant V = 0.3: lambda = 0.3 + sum_d 3(1-cos t)/(h^2(2+cos t))
+    q = pi.generate(6, 0, 0, 0.1, 1, v0=0.3)
+    r = L.labpsd(q, nev, 1e-10, seed=2)
+    ref = pi.closed_form_eigenvalues(6, 0.3)[:nev]
+    assert r.converged
+    assert np.abs(r.lam - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_closed_form_cluster_subspace():
+    # the 6-fold cluster of the 6^3 mesh is spanned by the sampled cos/sin(2 pi x_d) modes
+    N = 6
+    q = pi.generate(N, 0, 0, 0.1, 1, v0=0.3)
+    r = L.labpsd(q, 7, 1e-10, seed=3)
+    i = np.arange(N ** 3)
+    x = np.stack([i % N, (i // N) % N, i // (N * N)], axis=1) / N
+    modes = np.concatenate([np.cos(2 * np.pi * x), np.sin(2 * np.pi * x)], axis=1)
+    assert _angles(r.X[:, 1:7], modes) < 1e-6
+    assert _angles(r.X[:, :1], np.ones((N ** 3, 1))) < 1e-6
+
+
+def test_closed_form_bloch_complex():
+    k = (0.5 * np.pi, -0.5 * np.pi, 0.5 * np.pi)
+    q = pi.generate(5, 0, 0, 0.1, 1, v0=0.3, kpt=k)
+    X0 = pi.seed_normal_block(4, q.n, 8) + 1j * pi.seed_normal_block(5, q.n, 8)
+    r = L.labpsd(q, 5, 1e-10, X0=X0)
+    ref = pi.closed_form_eigenvalues(5, 0.3, k)[:5]
+    assert r.converged and np.iscomplexobj(r.X)
+    assert np.abs(r.lam - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ brute force
+def _brute(p):
+    H, S = p.scipy_pair()
+    return sla.eigh(H.toarray(), S.toarray())
+
+
+@pytest.mark.parametrize("case", [(4, 1, 2, 0.3, 1, 6), (6, 2, 2, 0.2, 3, 10), (8, 2, 2, 0.25, 1, 16)])
+def test_brute_force_dense(case):
+    N, na, ne, rc, seed, nev = case
+    p = pi.generate(N, na, ne, rc, seed)
+    w, V = _brute(p)
+    r = L.labpsd(p, nev, 1e-9, seed=seed)
+    assert r.converged
+    scale = np.abs(w[:nev]).max()
+    assert np.abs(r.lam - w[:nev]).max() <= 1e-9 * scale
+    # compare subspaces at every gap g = 1e-2 max|lambda| that ends at or before nev
+    H, S = p.scipy_pair()
+    Sd = S.toarray()
+    gaps = [j for j in range(1, nev) if w[j] - w[j - 1] > 1e-2 * scale]
+    for j in gaps:
+        assert _angles(r.X[:, :j], V[:, :j], Sd) < 1e-6
+
+
+def test_inertia_count_small(small_problem):
+    # Sylvester: #eigenvalues below sigma = #negative eigenvalues of H - sigma S
+    p = small_problem
+    r = L.labpsd(p, 16, 1e-8, seed=1)
+    H, S = p.scipy_pair()
+    Hd, Sd = H.toarray(), S.toarray()
+    sigma = r.lam[0] + 0.5 * (r.E_all[1] - r.E_all[0])
+    neg = np.count_nonzero(np.linalg.eigvalsh(Hd - sigma * Sd) < 0)
+    assert neg == 1
+    sigma = 0.5 * (r.lam[6] + r.lam[7])
+    neg = np.count_nonzero(np.linalg.eigvalsh(Hd - sigma * Sd) < 0)
+    assert neg == 7
+
+
+# ------------------------------------------------------------------ invariants
+def test_invariants_small(small_problem):
+    p = small_problem
+    r = L.labpsd(p, 16, 1e-8, seed=1)
+    H, S = p.scipy_pair()
+    # S-orthonormal Ritz vectors
+    assert np.abs(r.X.T @ (S @ r.X) - np.eye(16)).max() <= 1e-10
+    # Courant-Fischer: span(Z_l) contains span(Psi_{l-1}), so Ritz values never increase
+    hist = np.array(r.ritz_history)
+    scale = np.abs(hist).max()
+    assert np.all(np.diff(hist, axis=0) <= 1e-12 * scale)
+    # Ritz values lie above the exact eigenvalues
+    w, _ = _brute(p)
+    assert np.all(hist + r.sigma0 >= w[None, : hist.shape[1]] - 1e-10 * scale)
+    # stopping claim re-checked in extended precision, unshifted definition of Eq. res1
+    Hs = (H - r.sigma0 * S).tocsr()
+    Xl = r.X.astype(np.longdouble)
+    HX = np.stack([_spmv_ld(Hs, Xl[:, j]) for j in range(16)], axis=1)
+    SX = np.stack([_spmv_ld(S.tocsr(), Xl[:, j]) for j in range(16)], axis=1)
+    E = (r.lam - r.sigma0).astype(np.longdouble)
+    res = np.linalg.norm((HX - SX * E).astype(np.float64), axis=0) / np.linalg.norm(HX.astype(np.float64), axis=0)
+    assert res.max() <= 1e-8 * 1.01
+    # La within the paper's reported range (0..4 MINRES steps per column per iteration)
+    steps = np.concatenate([s for s in r.minres_steps if s.size])
+    assert steps.max() <= 20 and steps.mean() <= 4
+
+
+def _spmv_ld(A, x):
+    out = np.zeros(A.shape[0], dtype=np.longdouble)
+    data = A.data.astype(np.longdouble)
+    for i in range(A.shape[0]):
+        s, e = A.indptr[i], A.indptr[i + 1]
+        out[i] = np.dot(data[s:e], x[A.indices[s:e]])
+    return out
+
+
+def test_exact_invariant_subspace_zero_iterations(small_problem):
+    p = small_problem
+    w, V = _brute(p)
+    r = L.labpsd(p, 16, 1e-8, X0=V[:, :19])
+    assert r.converged and r.iters == 0
+
+
+def test_hybrid_beats_global_only(small_problem):
+    p = small_problem
+    rh = L.labpsd(p, 16, 1e-8, seed=1)
+    rg = L.labpsd(p, 16, 1e-8, seed=1, opts=L.Options(local=False))
+    assert rh.converged and rg.converged
+    assert rh.iters < rg.iters
+    assert np.abs(rh.lam - rg.lam).max() <= 1e-9 * np.abs(rh.lam).max()
+
+
+# ------------------------------------------------------------------ MINRES
+def _indefinite(n, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.concatenate([-np.linspace(0.5, 3, n // 3), np.linspace(0.2, 5, n - n // 3)])
+    return (Q * ev) @ Q.T
+
+
+def test_minres_equals_direct_solve():
+    A = _indefinite(40, 1)
+    b = np.random.default_rng(2).standard_normal(40)
+    x0 = np.random.default_rng(3).standard_normal(40)
+    x, k, hist = L.minres(lambda v: A @ v, b, x0, 1e-13 * np.linalg.norm(b), 200)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-10)
+    # the recurrence estimate is the true residual norm and never increases
+    assert np.all(np.diff(hist) <= 1e-12 * hist[0])
+
+
+def test_minres_recurrence_residual_is_true_residual():
+    A = _indefinite(30, 4)
+    b = np.random.default_rng(5).standard_normal(30)
+    for maxit in range(1, 8):
+        x, k, hist = L.minres(lambda v: A @ v, b, np.zeros(30), 0.0, maxit)
+        assert k == maxit
+        assert abs(np.linalg.norm(b - A @ x) - hist[-1]) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_minres_minimises_over_krylov_space():
+    # x_k minimises ||b - A x|| over x0 + K_k(A, r0): compare with a least-squares solve
+    A = _indefinite(25, 6)
+    b = np.random.default_rng(7).standard_normal(25)
+    x0 = np.random.default_rng(8).standard_normal(25)
+    r0 = b - A @ x0
+    for k in (1, 2, 3, 5):
+        K = np.stack([np.linalg.matrix_power(A, j) @ r0 for j in range(k)], axis=1)
+        c, *_ = np.linalg.lstsq(A @ K, r0, rcond=None)
+        best = np.linalg.norm(r0 - A @ K @ c)
+        x, _, hist = L.minres(lambda v: A @ v, b, x0, 0.0, k)
+        assert abs(np.linalg.norm(b - A @ x) - best) <= 1e-9 * np.linalg.norm(r0)
+
+
+def test_minres_zero_steps_when_start_meets_eta():
+    A = _indefinite(20, 9)
+    xs = np.random.default_rng(10).standard_normal(20)
+    b = A @ xs
+    x, k, _ = L.minres(lambda v: A @ v, b, xs + 1e-9, 1e-3, 20)
+    assert k == 0 and np.array_equal(x, xs + 1e-9)
+
+
+# ------------------------------------------------------------------ global preconditioner and RR
+def test_global_preconditioner_solves(small_problem):
+    p = small_problem
+    Hs, S, s0 = L.make_shifted(p)
+    K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
+    R = np.random.default_rng(1).standard_normal((p.n, 5))
+    P = K.apply(R)
+    Ad = Hs.toarray()
+    assert np.allclose(Ad @ P, -R, rtol=0, atol=1e-9 * np.abs(R).max())
+    assert np.allclose(P, -np.linalg.solve(Ad, R), rtol=1e-6, atol=0)
+
+
+def test_nested_dissection_is_permutation():
+    for N in (4, 6, 8, 9):
+        o = L.nested_dissection_nodes(N)
+        assert np.array_equal(np.sort(o), np.arange(N ** 3))
+
+
+def test_rayleigh_ritz_against_generalized_eigh():
+    rng = np.random.default_rng(11)
+    q = 12
+    B = rng.standard_normal((q, q))
+    SR = B @ B.T + 0.1 * np.eye(q)
+    HR = rng.standard_normal((q, q))
+    HR = HR + HR.T
+    g, W, fb = L.rayleigh_ritz(HR, SR, 5)
+    ref = sla.eigh(HR, SR, eigvals_only=True)[:5]
+    assert not fb
+    assert np.allclose(g, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    assert np.allclose(W.T @ SR @ W, np.eye(5), atol=1e-12)
+    assert np.allclose(W.T @ HR @ W, np.diag(g), atol=1e-11)
+
+
+def test_rayleigh_ritz_rank_deficient_fallback():
+    rng = np.random.default_rng(12)
+    n, q = 30, 8
+    Bm = rng.standard_normal((n, n))
+    Sf = Bm @ Bm.T + n * np.eye(n)
+    Hf = rng.standard_normal((n, n))
+    Hf = Hf + Hf.T
+    Z = rng.standard_normal((n, q))
+    Z[:, -1] = Z[:, 0] * 2.0 - Z[:, 1]            # exactly dependent column
+    HR, SR = Z.T @ Hf @ Z, Z.T @ Sf @ Z
+    HR, SR = 0.5 * (HR + HR.T), 0.5 * (SR + SR.T)
+    g, W, fb = L.rayleigh_ritz(HR, SR, 4)
+    assert fb
+    # reference on an independent basis of the same space
+    Zi = Z[:, :-1]
+    ref = sla.eigh(Zi.T @ Hf @ Zi, Zi.T @ Sf @ Zi, eigvals_only=True)[:4]
+    assert np.allclose(g, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
+def test_default_m0():
+    assert [L.default_m0(m) for m in (1, 16, 30, 31, 64, 256)] == [3, 3, 3, 4, 7, 26]
+
+
+# ------------------------------------------------------------------ planted mistakes
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each plausible slip below, planted in the oracle, fails a pin used above."""
+    p = pi.generate(6, 2, 2, 0.2, 3)
+    w, V = _brute(p)
+    nev = 10
+
+    def pinned():
+        try:
+            r = L.labpsd(p, nev, 1e-9, seed=3, opts=L.Options(max_outer=200))
+        except (np.linalg.LinAlgError, ValueError, FloatingPointError):
+            return False
+        return bool(r.converged and np.abs(r.lam - w[:nev]).max() <= 1e-9 * np.abs(w[:nev]).max())
+
+    assert pinned()
+    orig_res, orig_rr, orig_ref, orig_red = L.residual, L.rayleigh_ritz, L.refine, L.reduced_pair
+
+    # (a) wrong sign in the residual of step 4
+    monkeypatch.setattr(L, "residual", lambda PH, PS, E, m: orig_res(PH, -PS, E, m))
+    assert not pinned()
+    monkeypatch.setattr(L, "residual", orig_res)
+    # (b) Rayleigh-Ritz keeps the highest instead of the lowest pairs
+    def rr_high(HR, SR, k):
+        g, W, fb = orig_rr(-HR, SR, k)
+        return -g, W, fb
+    monkeypatch.setattr(L, "rayleigh_ritz", rr_high)
+    assert not pinned()
+    monkeypatch.setattr(L, "rayleigh_ritz", orig_rr)
+    # (c) S_R formed from H-products (a transposed / swapped operand in step 8)
+    monkeypatch.setattr(L, "reduced_pair", lambda Z, ZH, ZS: orig_red(Z, ZH, ZH + ZS))
+    assert not pinned()
+    monkeypatch.setattr(L, "reduced_pair", orig_red)
+    # (d) refinement shift with the wrong sign: (H + eps_i S) instead of (H - eps_i S)
+    monkeypatch.setattr(L, "refine", lambda Hs, S, e, r, p0, eta, mx: orig_ref(Hs, S, -e - 50.0, r, p0, eta, mx))
+    r = L.labpsd(p, nev, 1e-9, seed=3, opts=L.Options(max_outer=200))
+    ref = L.labpsd.__wrapped__ if hasattr(L.labpsd, "__wrapped__") else None
+    monkeypatch.setattr(L, "refine", orig_ref)
+    good = L.labpsd(p, nev, 1e-9, seed=3)
+    assert r.iters > good.iters
