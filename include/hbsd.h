@@ -1,0 +1,222 @@
+/*
+ * hbsd.h -- C ABI of the GB300 LABPSD library: block preconditioned steepest descent with
+ * the hybrid (global + locally accelerated) preconditioner of Cai, Bai, Pask and Sukumar
+ * (Sec. 3 "LABPSD" outline and remarks; Sec. 4 implementation of step 6).
+ *
+ * Problem (Eq. ghep): lowest nev eigenpairs of H x = lambda S x, H Hermitian, S Hermitian
+ * positive definite, H and S sparse with one shared pattern (Sec. 4 footnote).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: 0 on success, HBSD_NOT_CONVERGED (1) when the outer iteration cap was hit
+ *     (outputs then hold the best iterate), HBSD_BUSY (2) from hbsd_poll while a request
+ *     runs, and a negative HBSD_ERR_* code on error.  No exception or abort crosses the ABI;
+ *     hbsd_last_error() returns a thread-local message for the last failing call.
+ *   - Block vectors on the device are ROW-MAJOR: entry (i, j) of an n x k block with leading
+ *     dimension ld (ld >= k, in elements) sits at ptr[i * ld + j].  Every device pointer
+ *     must be 16-byte aligned and every ld even, so that a row pair of doubles is one
+ *     16-byte access.
+ *   - Host arrays (hbsd_csr, X0, outputs of hbsd_solve) are plain C arrays; the caller owns
+ *     them; the library copies what it keeps.  Device buffers passed to step-level entry
+ *     points are owned by the caller; the library never frees them.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = legacy default
+ *     stream).  Step-level calls are asynchronous on that stream unless stated otherwise.
+ *   - The library holds no torch or Python types; a caller may hand in device pointers of
+ *     any allocator.
+ */
+#ifndef HBSD_H
+#define HBSD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------ */
+#define HBSD_OK               0
+#define HBSD_NOT_CONVERGED    1
+#define HBSD_BUSY             2
+#define HBSD_ERR_ARG        (-1)   /* invalid argument (sizes, NULL, layout)               */
+#define HBSD_ERR_OOM        (-2)   /* device allocation failed or admission refused        */
+#define HBSD_ERR_NOT_SPD    (-3)   /* factorisation of H - sigma_bar S met a pivot <= 0:   */
+                                   /* sigma_bar is not below the spectrum (Sec. 5)         */
+#define HBSD_ERR_RR_RANK    (-4)   /* search space rank below the number of wanted pairs   */
+#define HBSD_ERR_TIMEOUT    (-5)   /* a device-side wait gave up                           */
+#define HBSD_ERR_CUDA       (-6)   /* CUDA runtime error; see hbsd_last_error()            */
+#define HBSD_ERR_UNSUPPORTED (-7)  /* valid request for a feature this build does not have */
+
+/* ---- problem description ----------------------------------------------------------- */
+
+/* Sparse matrix in CSR form (host memory).  row_ptr has n+1 int64 entries, col_idx nnz
+ * int32 column indices sorted within each row, val nnz doubles (is_complex = 0) or 2*nnz
+ * interleaved (re, im) doubles (is_complex = 1).  H and S given to hbsd_create must have
+ * identical n, row_ptr and col_idx (Sec. 4 footnote: one pattern). */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const double* val;
+    int is_complex;
+} hbsd_csr;
+
+/* Geometry of the discretisation (host memory), used to order the sparse factorisation of
+ * the global preconditioner (Sec. 4, Eq. ldl) by nested dissection of the periodic node
+ * grid.  dof_node[i] in [0, grid[0]*grid[1]*grid[2]) is the mesh node carrying dof i, with
+ * node index ix + grid[0]*(iy + grid[1]*iz); dof_cluster[i] is the atom cluster of an
+ * enrichment dof or -1 (informational). */
+typedef struct {
+    const int32_t* dof_node;
+    const int32_t* dof_cluster;
+    int32_t grid[3];
+} hbsd_local_blocks;
+
+#define HBSD_PRECISION_FP64   0   /* every step in FP64                                  */
+#define HBSD_PRECISION_MIXED  1   /* FP32 sparse steps + FP64 Rayleigh-Ritz and final check */
+
+#define HBSD_PRECOND_HYBRID   0   /* steps 6(a) + 6(b) (Sec. 3 hybrid scheme)           */
+#define HBSD_PRECOND_GLOBAL   1   /* step 6(a) only (Eq. globalprecond)                  */
+
+/* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
+ * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,
+ * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar). */
+typedef struct {
+    double sigma_bar;   /* global shift eps_bar of K = (H - eps_bar S)^{-1}; must lie below the spectrum */
+    double sigma0;      /* shift making H - sigma0 S positive definite (Sec. 5); NaN -> sigma_bar        */
+    int m0;             /* guard vectors (remark 1); -1 -> default                                       */
+    double tau1, tau2;  /* localisation thresholds (remark 4)                                           */
+    double eta;         /* inexact-solve tolerance (Eq. approxp)                                        */
+    int max_minres;     /* MINRES step cap per refinement                                               */
+    int max_outer;      /* BPSD iteration cap                                                           */
+    int precision;      /* HBSD_PRECISION_*                                                             */
+    int precond;        /* HBSD_PRECOND_*                                                               */
+    uint64_t seed;      /* seed of the SplitMix64 normals used when X0 is NULL                           */
+} hbsd_options;
+
+/* Statistics of one solve (all counts cumulative over the solve). */
+typedef struct {
+    int iters;               /* outer BPSD iterations (steps 4-11)                         */
+    int iters_fp64;          /* of which run in FP64 (the final refinement sweep, mixed)   */
+    int64_t minres_steps;    /* total MINRES steps over all refined columns (M_s)          */
+    int64_t precond_cols;    /* total columns through step 6(a)                            */
+    int64_t local_cols;      /* total columns through step 6(b)                            */
+    int rr_fallbacks;        /* Rayleigh-Ritz calls that took the rank-revealing branch    */
+    double res_max;          /* final Res_max (Eq. res1), recomputed in FP64               */
+    double t_factor_ms;      /* factorisation time of hbsd_create (host clock)            */
+    double t_solve_ms;       /* hbsd_solve wall time                                       */
+    int64_t nnz_L;           /* stored entries of the supernodal factor                    */
+    int n_supernodes;
+    int gpu_launches;        /* kernels launched by the last hbsd_solve                     */
+    /* device time per LABPSD step class over the last solve (CUDA events on the session
+     * stream), the breakdown of Sec. 5.3 / Fig. 8: */
+    double t_matvec_ms;      /* steps 3 and 7: fused SpMM (H X, S X)                        */
+    double t_resid_ms;       /* steps 4-5: residuals and norms                              */
+    double t_precond_ms;     /* step 6(a): supernodal triangular solves                     */
+    double t_local_ms;       /* step 6(b): MINRES refinement (shifted SpMM included)        */
+    double t_gram_ms;        /* step 8                                                      */
+    double t_rr_ms;          /* step 9                                                      */
+    double t_update_ms;      /* steps 10-11                                                 */
+    int64_t matvec_cols;     /* columns through steps 3 and 7                              */
+    int64_t minres_spmm_cols;/* columns through the shifted SpMM of step 6(b)              */
+    int precond_calls;       /* applications of step 6(a)                                   */
+} hbsd_stats;
+
+typedef struct hbsd_handle hbsd_handle;
+
+void hbsd_options_default(hbsd_options* opt);
+
+/* Create a solver session: copies H and S to the device, builds the SELL-C-sigma pattern
+ * with interleaved (h, s) values (Sec. 4 footnote: one pattern), and factorises
+ * H - sigma_bar S once (Sec. 4, Eq. ldl; remark: computed once and reused).  lb is required
+ * (the ordering of the factorisation); opt may be NULL (defaults, sigma_bar must then be
+ * set by hbsd_set_sigma, else HBSD_ERR_ARG).  stream: cudaStream_t as void* for all work of
+ * the session (NULL = a stream the session creates).  Returns HBSD_ERR_NOT_SPD if the
+ * factorisation meets a non-positive pivot, HBSD_ERR_UNSUPPORTED for complex input. */
+int hbsd_create(const hbsd_csr* H, const hbsd_csr* S, const hbsd_local_blocks* lb,
+                const hbsd_options* opt, void* stream, hbsd_handle** out);
+
+/* Replace H's values (same pattern) for an SCF follow-up; the global factor keeps the
+ * first H (Sec. 4: K built from H^(1) and reused through the SCF). */
+int hbsd_update_H(hbsd_handle* h, const double* H_val);
+
+/* LABPSD (Sec. 3 outline, steps 1-12): lowest nev eigenpairs to Res_max <= tol (remark 2).
+ * X0: host, row-major n x (nev + m0) start block (remark 1), or NULL for seed-normal draws,
+ * or the previous solve's block if warm != 0 (X0 must then be NULL).  lambda: host, nev
+ * unshifted eigenvalues ascending.  X: host, row-major n x nev S-orthonormal eigenvectors, or
+ * NULL.  iters, st: nullable.  Synchronous. */
+int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm,
+               double* lambda, double* X, int* iters, hbsd_stats* st);
+
+/* Same as hbsd_solve with device buffers: X0_dev row-major n x (nev+m0), ld = ldx0 (or NULL),
+ * lambda_dev nev doubles, X_dev row-major n x nev with ld = ldx (or NULL). */
+int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0,
+                      double* lambda_dev, double* X_dev, int64_t ldx, int* iters, hbsd_stats* st);
+
+void hbsd_destroy(hbsd_handle* h);
+const char* hbsd_status_string(int status);
+const char* hbsd_last_error(void);
+int64_t hbsd_n(const hbsd_handle* h);
+double hbsd_sigma0(const hbsd_handle* h);
+void hbsd_get_stats(const hbsd_handle* h, hbsd_stats* st);
+
+/* ---- step-level entry points (device pointers, the session's stream) -------------------
+ * Each runs one step of the LABPSD outline exactly as hbsd_solve does, so that each step can
+ * be checked on its own.  All block vectors are row-major FP64 with the ld given. */
+
+/* Steps 3 and 7: HX = (H - sigma0 S) X and SX = S X for an n x k block X. */
+int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k,
+                   double* HX, int64_t ldhx, double* SX, int64_t ldsx);
+
+/* Operator of step 6(b): Y(:,j) = (H - sigma0 S - e_j S) X(:,j), e (device, k doubles)
+ * shifts relative to sigma0. */
+int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e,
+                      double* Y, int64_t ldy);
+
+/* Steps 4-5 (Eq. res1): for j < m, r_j = PsiH(:,j) - PsiS(:,j) E_j and
+ * res[j] = ||r_j|| / ||PsiH(:,j)|| (device outputs: R n x m with ldr, res m doubles). */
+int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double* PsiS,
+                  int64_t lds, const double* E, int m, double* R, int64_t ldr, double* res);
+
+/* Step 6(a) (Eq. k1p): P = -(H - sigma_bar S)^{-1} R for an n x k block, by the
+ * supernodal factor of hbsd_create. */
+int hbsd_precond_apply(hbsd_handle* h, const double* R, int64_t ldr, int k, double* P,
+                       int64_t ldp);
+
+/* Step 6(b) (Eq. indls, Eq. approxp): for each column j of the n x k block P, MINRES on
+ * (H - sigma0 S - e_j S) y = -r_j from y0 = P(:,j), stopped when the recurrence residual is
+ * <= eta ||r_j|| or after max_minres steps; P(:,j) := y.  steps (device, k ints): steps
+ * taken per column. */
+int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k,
+                double eta, int max_minres, double* P, int64_t ldp, int* steps);
+
+/* Step 8: H_R = Z^T ZH and S_R = Z^T ZS (q x q, row-major, ld q), made exactly symmetric
+ * as (A + A^T)/2; Z, ZH, ZS are n x q row-major blocks. */
+int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
+              int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream);
+
+/* Step 9: lowest k eigenpairs of H_R W = S_R W Theta (q x q inputs row-major, ld q, device).
+ * Diagonal scaling D = diag(S_R)^{-1/2}, Cholesky of D S_R D, symmetric eigensolve of
+ * L^{-1} D H_R D L^{-T}; if the Cholesky breaks down or a pivot is below 1e-14 the
+ * eigen-directions of D S_R D below 1e-14 * max are dropped instead.  Outputs (device):
+ * theta k doubles ascending, W q x k row-major (ld k), info[0] = 1 if that fallback was
+ * taken, info[1] = rank used.  Returns HBSD_ERR_RR_RANK if the rank is below k.  The
+ * workspace is internal.  Synchronous (reads back info). */
+int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double* theta,
+                       double* W, int* info, void* stream);
+
+/* Steps 10-11: Z(:, 0:k) := Z(:, 0:q) W in place, row by row, for an n x q block Z and a
+ * q x k matrix W (row-major, ld k, device), k <= q. */
+int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream);
+
+/* ---- measurement ------------------------------------------------------------------
+ * Sustained FMA throughput of the SIMT pipes on the current device (which = 0: FP64, 1: FP32),
+ * in FLOP/s (an FMA counts 2), from one timed launch of independent FMA chains on every SM.
+ * The paper has no counterpart; it supplies the ALU peak that the FP64 rooflines divide by.
+ * Synchronous. */
+int hbsd_probe_peak(int which, void* stream, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HBSD_H */

@@ -1,0 +1,955 @@
+// Global preconditioner of LABPSD step 6(a): K = (H - eps_bar S)^{-1} (Eq. globalprecond,
+// Eq. k1p), applied through a sparse factorisation computed once per session (Sec. 4,
+// Eq. ldl: "computed just once and used throughout").  eps_bar lies below the spectrum, so
+// H - eps_bar S is positive definite and the factorisation is a Cholesky L L^T.
+//
+//  * ordering (host): geometric nested dissection of the periodic node grid; the dofs of a
+//    node stay together.  A periodic direction is cut by two planes, an open one by one.
+//    Each dissection-tree node (separator or leaf box) is one supernode.
+//  * symbolic (host): below-diagonal row structure of every supernode, child->parent
+//    extend-add maps, storage offsets.
+//  * numeric (GPU): multifrontal, one tree level at a time; a front is assembled from the
+//    matrix entries and the children's update matrices, then partially factorised by a
+//    blocked right-looking Cholesky (NB x NB diagonal blocks in shared memory, their
+//    inverses kept for the solves).  Only the lower triangle of a front is referenced.
+//  * solve (GPU): forward multifrontal sweep with front vectors (levels bottom-up), backward
+//    sweep gathering the ancestors' solution (levels top-down); within a supernode both are
+//    blocked by NB with the inverted diagonal blocks.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <numeric>
+
+#include "common.h"
+
+namespace hbsd {
+
+namespace {
+
+constexpr int NB = Factor::NB;
+constexpr int LEAF_NODES = 64;
+
+struct SnDev {
+    int64_t first, L_off, Dinv_off, fv_off, struct_off, ea_off, front_off;
+    int ns, nu, child0, child1;
+};
+
+struct NDTree {
+    int g[3];
+    std::vector<std::vector<int32_t>> nodes;   // mesh nodes of each tree node
+    std::vector<std::array<int, 2>> kids;
+    std::vector<int> parent;
+
+    int add(std::vector<int32_t>&& v) {
+        nodes.push_back(std::move(v));
+        kids.push_back({-1, -1});
+        parent.push_back(-1);
+        return (int)nodes.size() - 1;
+    }
+    void box_nodes(const int lo[3], const int hi[3], std::vector<int32_t>& out) const {
+        for (int z = lo[2]; z < hi[2]; ++z)
+            for (int y = lo[1]; y < hi[1]; ++y)
+                for (int x = lo[0]; x < hi[0]; ++x) {
+                    const int xx = ((x % g[0]) + g[0]) % g[0];
+                    const int yy = ((y % g[1]) + g[1]) % g[1];
+                    const int zz = ((z % g[2]) + g[2]) % g[2];
+                    out.push_back(xx + g[0] * (yy + g[1] * zz));
+                }
+    }
+    int build(const int lo[3], const int hi[3], const bool per[3]) {
+        int size[3] = {hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]};
+        if (size[0] <= 0 || size[1] <= 0 || size[2] <= 0) return -1;
+        const int64_t vol = (int64_t)size[0] * size[1] * size[2];
+        if (vol <= LEAF_NODES) {
+            std::vector<int32_t> v;
+            box_nodes(lo, hi, v);
+            return add(std::move(v));
+        }
+        int d = 0;
+        for (int e = 1; e < 3; ++e)
+            if (size[e] > size[d]) d = e;
+        const int mid = lo[d] + size[d] / 2;
+        std::vector<int> planes;
+        int alo[3], ahi[3], blo[3], bhi[3];
+        bool per2[3] = {per[0], per[1], per[2]};
+        for (int e = 0; e < 3; ++e) { alo[e] = blo[e] = lo[e]; ahi[e] = bhi[e] = hi[e]; }
+        if (per[d]) {
+            planes.push_back(lo[d]);
+            if (mid != lo[d]) planes.push_back(mid);
+            alo[d] = lo[d] + 1; ahi[d] = mid;
+            blo[d] = mid + 1; bhi[d] = hi[d];
+            per2[d] = false;
+        } else {
+            planes.push_back(mid);
+            ahi[d] = mid;
+            blo[d] = mid + 1;
+        }
+        const int ca = build(alo, ahi, per2);
+        const int cb = build(blo, bhi, per2);
+        std::vector<int32_t> sep;
+        for (int pl : planes) {
+            int slo[3] = {lo[0], lo[1], lo[2]}, shi[3] = {hi[0], hi[1], hi[2]};
+            slo[d] = pl; shi[d] = pl + 1;
+            box_nodes(slo, shi, sep);
+        }
+        const int id = add(std::move(sep));
+        kids[id] = {ca, cb};
+        if (ca >= 0) parent[ca] = id;
+        if (cb >= 0) parent[cb] = id;
+        return id;
+    }
+};
+
+// ---- numeric factorisation kernels ---------------------------------------------------------
+__global__ void k_zero(double* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = 0.0;
+}
+
+__global__ void k_scatter_entries(const int64_t* __restrict__ pos, const int64_t* __restrict__ src,
+                                  int64_t count, const double* __restrict__ aval, double* __restrict__ F) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        F[pos[i]] = aval[src[i]];
+}
+
+// parent front += child update matrix (lower triangle), jobs = (parent, child) pairs
+__global__ void k_extend_add_matrix(const SnDev* __restrict__ sn, const int* __restrict__ jobs, int njobs,
+                                    const int32_t* __restrict__ ea, double* __restrict__ F) {
+    const int job = blockIdx.y;
+    if (job >= njobs) return;
+    const SnDev p = sn[jobs[2 * job]];
+    const SnDev c = sn[jobs[2 * job + 1]];
+    const int nu = c.nu;
+    const int nfc = c.ns + c.nu, nfp = p.ns + p.nu;
+    const int64_t total = (int64_t)nu * nu;
+    const int32_t* map = ea + c.ea_off;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % nu), j = (int)(idx / nu);
+        if (i < j) continue;
+        const double u = F[c.front_off + (int64_t)(c.ns + j) * nfc + c.ns + i];
+        F[p.front_off + (int64_t)map[j] * nfp + map[i]] += u;
+    }
+}
+
+// Cholesky of the diagonal block [k0, k0+kb) of each front in shared memory, plus its inverse.
+__global__ void __launch_bounds__(256) k_potrf_block(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                     int nids, int k0, double* __restrict__ F,
+                                                     double* __restrict__ Dinv, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto A = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
+    auto X = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * NB * (NB + 1));
+    __shared__ int bad;
+    const SnDev s = sn[ids[blockIdx.x]];
+    if (k0 >= s.ns) return;
+    const int kb = min(NB, s.ns - k0);
+    const int nf = s.ns + s.nu;
+    double* Fb = F + s.front_off + (int64_t)k0 * nf + k0;
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        const int i = t % NB, j = t / NB;
+        A[i][j] = (i < kb && j < kb && i >= j) ? Fb[(int64_t)j * nf + i] : 0.0;
+        X[i][j] = 0.0;
+    }
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int c = 0; c < kb; ++c) {
+        if (threadIdx.x == 0) {
+            const double piv = A[c][c];
+            if (!(piv > 0.0)) { bad = 1; A[c][c] = 1.0; }
+            else A[c][c] = sqrt(piv);
+        }
+        __syncthreads();
+        const double l = A[c][c];
+        for (int i = c + 1 + threadIdx.x; i < kb; i += blockDim.x) A[i][c] /= l;
+        __syncthreads();
+        const int m = kb - c - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            const int i = c + 1 + t % m, j = c + 1 + t / m;
+            if (i >= j) A[i][j] -= A[i][c] * A[j][c];
+        }
+        __syncthreads();
+    }
+    if (bad && threadIdx.x == 0) atomicExch(err, 1);
+    // inverse of the lower-triangular block, one column per thread
+    for (int c = threadIdx.x; c < kb; c += blockDim.x) {
+        X[c][c] = 1.0 / A[c][c];
+        for (int i = c + 1; i < kb; ++i) {
+            double acc = 0.0;
+            for (int t = c; t < i; ++t) acc += A[i][t] * X[t][c];
+            X[i][c] = -acc / A[i][i];
+        }
+    }
+    __syncthreads();
+    double* Db = Dinv + s.Dinv_off + (int64_t)(k0 / NB) * NB * NB;
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) {
+        const int i = t % NB, j = t / NB;
+        if (i < kb && j < kb && i >= j) Fb[(int64_t)j * nf + i] = A[i][j];
+        Db[t] = (i < kb && j < kb) ? X[i][j] : 0.0;  // column-major NB x NB
+    }
+}
+
+// Panel: F[k0+kb : nf, k0 : k0+kb] := F[...] * L_kk^{-T}  (row tiles of 64)
+__global__ void __launch_bounds__(256) k_trsm_panel(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                    int k0, double* __restrict__ F, const double* __restrict__ Dinv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto Ar = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
+    auto Di = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * 64 * (NB + 1));
+    const SnDev s = sn[ids[blockIdx.y]];
+    if (k0 >= s.ns) return;
+    const int kb = min(NB, s.ns - k0);
+    const int nf = s.ns + s.nu;
+    const int r0 = k0 + kb + blockIdx.x * 64;
+    if (r0 >= nf) return;
+    const int rows = min(64, nf - r0);
+    double* Fc = F + s.front_off + (int64_t)k0 * nf;
+    const double* Db = Dinv + s.Dinv_off + (int64_t)(k0 / NB) * NB * NB;
+    for (int t = threadIdx.x; t < 64 * NB; t += blockDim.x) {
+        const int i = t % 64, j = t / 64;
+        Ar[i][j] = (i < rows && j < kb) ? Fc[(int64_t)j * nf + r0 + i] : 0.0;
+    }
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) Di[t % NB][t / NB] = Db[t];
+    __syncthreads();
+    // out[i][c] = sum_{t <= c} A[i][t] * Dinv[c][t]
+    for (int t = threadIdx.x; t < 64 * NB; t += blockDim.x) {
+        const int i = t % 64, c = t / 64;
+        if (i >= rows || c >= kb) continue;
+        double acc = 0.0;
+        for (int u = 0; u <= c; ++u) acc += Ar[i][u] * Di[c][u];
+        Fc[(int64_t)c * nf + r0 + i] = acc;
+    }
+}
+
+// Trailing update F22 -= L21 L21^T over 64 x 64 tiles of the lower triangle.
+__global__ void __launch_bounds__(256) k_syrk_update(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                     int k0, double* __restrict__ F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto Li = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
+    auto Lj = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * 64 * (NB + 1));
+    const SnDev s = sn[ids[blockIdx.y]];
+    if (k0 >= s.ns) return;
+    const int kb = min(NB, s.ns - k0);
+    const int nf = s.ns + s.nu;
+    const int base = k0 + kb;
+    const int m = nf - base;
+    if (m <= 0) return;
+    const int T = (m + 63) / 64;
+    const int x = blockIdx.x;
+    if (x >= T * (T + 1) / 2) return;
+    int ti = (int)((sqrt(8.0 * x + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= x) ++ti;
+    while (ti * (ti + 1) / 2 > x) --ti;
+    const int tj = x - ti * (ti + 1) / 2;
+    const int i0 = base + ti * 64, j0 = base + tj * 64;
+    const double* Fc = F + s.front_off + (int64_t)k0 * nf;
+    for (int t = threadIdx.x; t < 64 * NB; t += blockDim.x) {
+        const int r = t % 64, c = t / 64;
+        Li[r][c] = (i0 + r < nf && c < kb) ? Fc[(int64_t)c * nf + i0 + r] : 0.0;
+        Lj[r][c] = (j0 + r < nf && c < kb) ? Fc[(int64_t)c * nf + j0 + r] : 0.0;
+    }
+    __syncthreads();
+    const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;  // 4 x 4 outputs each
+    double acc[4][4] = {};
+    for (int c = 0; c < kb; ++c) {
+        double a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { a[u] = Li[tr + 16 * u][c]; b[u] = Lj[tc + 16 * u][c]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    double* Fo = F + s.front_off;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + tr + 16 * u, j = j0 + tc + 16 * v;
+            if (i < nf && j < nf && i >= j) Fo[(int64_t)j * nf + i] -= acc[u][v];
+        }
+}
+
+__global__ void k_copy_panels(const SnDev* __restrict__ sn, int nsn, const double* __restrict__ F,
+                              double* __restrict__ L) {
+    const SnDev s = sn[blockIdx.y];
+    const int64_t count = (int64_t)(s.ns + s.nu) * s.ns;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        L[s.L_off + i] = F[s.front_off + i];
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// ---- solve kernels (T = double or float), RHS chunks of 64 columns ------------------------------
+constexpr int RC = 64;  // RHS columns per CTA
+
+// front vectors of a level: rows < ns <- R[perm[first + r]], rows >= ns <- 0
+template <class T>
+__global__ void k_fv_init(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                          const int32_t* __restrict__ perm, const T* __restrict__ R, int64_t ldr, int k,
+                          T* __restrict__ fv, int64_t ldf) {
+    const SnDev s = sn[ids[blockIdx.y]];
+    const int nf = s.ns + s.nu;
+    const int64_t total = (int64_t)nf * k;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / k), j = (int)(idx % k);
+        T v = T(0);
+        if (r < s.ns) v = R[(int64_t)perm[s.first + r] * ldr + j];
+        fv[(s.fv_off + r) * ldf + j] = v;
+    }
+}
+
+// parent front vector += child's below-diagonal part
+template <class T>
+__global__ void k_fv_extend_add(const SnDev* __restrict__ sn, const int* __restrict__ jobs, int njobs,
+                                const int32_t* __restrict__ ea, int k, T* __restrict__ fv, int64_t ldf) {
+    const int job = blockIdx.y;
+    if (job >= njobs) return;
+    const SnDev p = sn[jobs[2 * job]];
+    const SnDev c = sn[jobs[2 * job + 1]];
+    const int64_t total = (int64_t)c.nu * k;
+    const int32_t* map = ea + c.ea_off;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / k), j = (int)(idx % k);
+        fv[(p.fv_off + map[r]) * ldf + j] += fv[(c.fv_off + c.ns + r) * ldf + j];
+    }
+}
+
+// y_blk := Dinv_blk (or Dinv_blk^T) y_blk, block [k0, k0+kb) of every front of the level
+template <class T, bool TRANS>
+__global__ void __launch_bounds__(256) k_solve_diag(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                    int k0, const T* __restrict__ Dinv, int k,
+                                                    T* __restrict__ fv, int64_t ldf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto Y = reinterpret_cast<T(*)[RC + 1]>(smem_raw);
+    auto D = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
+    const SnDev s = sn[ids[blockIdx.y]];
+    if (k0 >= s.ns) return;
+    const int kb = min(NB, s.ns - k0);
+    const int j0 = blockIdx.x * RC;
+    const int kc = min(RC, k - j0);
+    const T* Db = Dinv + s.Dinv_off + (int64_t)(k0 / NB) * NB * NB;
+    T* yb = fv + (s.fv_off + k0) * ldf + j0;
+    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
+        const int r = t / RC, j = t % RC;
+        Y[r][j] = (r < kb && j < kc) ? yb[(int64_t)r * ldf + j] : T(0);
+    }
+    for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) D[t % NB][t / NB] = Db[t];
+    __syncthreads();
+    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
+        const int r = t / RC, j = t % RC;
+        if (r >= kb || j >= kc) continue;
+        T acc = T(0);
+        if (!TRANS) {
+            for (int u = 0; u <= r; ++u) acc = fma(D[r][u], Y[u][j], acc);
+        } else {
+            for (int u = r; u < kb; ++u) acc = fma(D[u][r], Y[u][j], acc);
+        }
+        yb[(int64_t)r * ldf + j] = acc;
+    }
+}
+
+// forward: rows >= k0+kb of each front: fv[row] -= L[row, k0:k0+kb] y_blk   (row tiles of 64)
+template <class T>
+__global__ void __launch_bounds__(256) k_solve_fwd_update(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                          int k0, const T* __restrict__ L, int k,
+                                                          T* __restrict__ fv, int64_t ldf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto Lt = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
+    auto Y = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * 64 * (NB + 1));
+    const SnDev s = sn[ids[blockIdx.y]];
+    if (k0 >= s.ns) return;
+    const int kb = min(NB, s.ns - k0);
+    const int nf = s.ns + s.nu;
+    const int r0 = k0 + kb + blockIdx.x * 64;
+    if (r0 >= nf) return;
+    const int rows = min(64, nf - r0);
+    const int j0 = blockIdx.z * RC;
+    const int kc = min(RC, k - j0);
+    const T* Lc = L + s.L_off + (int64_t)k0 * nf;
+    for (int t = threadIdx.x; t < 64 * NB; t += blockDim.x) {
+        const int i = t % 64, c = t / 64;
+        Lt[i][c] = (i < rows && c < kb) ? Lc[(int64_t)c * nf + r0 + i] : T(0);
+    }
+    const T* yb = fv + (s.fv_off + k0) * ldf + j0;
+    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
+        const int r = t / RC, j = t % RC;
+        Y[r][j] = (r < kb && j < kc) ? yb[(int64_t)r * ldf + j] : T(0);
+    }
+    __syncthreads();
+    T* ob = fv + (s.fv_off + r0) * ldf + j0;
+    for (int t = threadIdx.x; t < 64 * RC; t += blockDim.x) {
+        const int i = t / RC, j = t % RC;
+        if (i >= rows || j >= kc) continue;
+        T acc = T(0);
+        for (int c = 0; c < kb; ++c) acc = fma(Lt[i][c], Y[c][j], acc);
+        ob[(int64_t)i * ldf + j] -= acc;
+    }
+}
+
+// backward, step a: fv[c] -= sum_r L[ns + r][c] x[struct[r]] for columns c of the supernode
+template <class T>
+__global__ void __launch_bounds__(256) k_solve_bwd_gather(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                          const T* __restrict__ L, const int64_t* __restrict__ srows,
+                                                          const T* __restrict__ xp, int64_t ldx, int k,
+                                                          T* __restrict__ fv, int64_t ldf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto Lt = reinterpret_cast<T(*)[65]>(smem_raw);
+    auto Xs = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * 64 * 65);
+    const SnDev s = sn[ids[blockIdx.y]];
+    const int c0 = blockIdx.x * 64;
+    if (c0 >= s.ns || s.nu == 0) return;
+    const int cols = min(64, s.ns - c0);
+    const int nf = s.ns + s.nu;
+    const int j0 = blockIdx.z * RC;
+    const int kc = min(RC, k - j0);
+    const int tc = threadIdx.x % 64, tg = threadIdx.x / 64;  // column c0+tc, RHS j = tg + 4*v
+    T acc[RC / 4];
+#pragma unroll
+    for (int v = 0; v < RC / 4; ++v) acc[v] = T(0);
+    const T* Lc = L + s.L_off;
+    for (int r0 = 0; r0 < s.nu; r0 += 64) {
+        const int rr = min(64, s.nu - r0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) {
+            const int r = t % 64, c = t / 64;
+            Lt[r][c] = (r < rr && c < cols) ? Lc[(int64_t)(c0 + c) * nf + s.ns + r0 + r] : T(0);
+        }
+        for (int t = threadIdx.x; t < 64 * RC; t += blockDim.x) {
+            const int r = t / RC, j = t % RC;
+            Xs[r][j] = (r < rr && j < kc) ? xp[srows[s.struct_off + r0 + r] * ldx + j0 + j] : T(0);
+        }
+        __syncthreads();
+        for (int r = 0; r < rr; ++r) {
+            const T l = Lt[r][tc];
+#pragma unroll
+            for (int v = 0; v < RC / 4; ++v) acc[v] = fma(l, Xs[r][tg + 4 * v], acc[v]);
+        }
+    }
+    if (tc < cols) {
+        T* ob = fv + (s.fv_off + c0 + tc) * ldf + j0;
+#pragma unroll
+        for (int v = 0; v < RC / 4; ++v) {
+            const int j = tg + 4 * v;
+            if (j < kc) ob[j] -= acc[v];
+        }
+    }
+}
+
+// backward, step b: for columns c < k0: fv[c] -= sum_{t < kb} L[k0 + t][c] x_blk[t]
+template <class T>
+__global__ void __launch_bounds__(256) k_solve_bwd_update(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                                                          int k0, const T* __restrict__ L, int k,
+                                                          T* __restrict__ fv, int64_t ldf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto Lt = reinterpret_cast<T(*)[65]>(smem_raw);
+    auto Xs = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * 65);
+    const SnDev s = sn[ids[blockIdx.y]];
+    if (k0 >= s.ns) return;
+    const int c0 = blockIdx.x * 64;
+    if (c0 >= k0) return;
+    const int cols = min(64, k0 - c0);
+    const int kb = min(NB, s.ns - k0);
+    const int nf = s.ns + s.nu;
+    const int j0 = blockIdx.z * RC;
+    const int kc = min(RC, k - j0);
+    const T* Lc = L + s.L_off;
+    for (int t = threadIdx.x; t < NB * 64; t += blockDim.x) {
+        const int r = t % NB, c = t / NB;
+        Lt[r][c] = (r < kb && c < cols) ? Lc[(int64_t)(c0 + c) * nf + k0 + r] : T(0);
+    }
+    const T* xb = fv + (s.fv_off + k0) * ldf + j0;
+    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
+        const int r = t / RC, j = t % RC;
+        Xs[r][j] = (r < kb && j < kc) ? xb[(int64_t)r * ldf + j] : T(0);
+    }
+    __syncthreads();
+    const int tc = threadIdx.x % 64, tg = threadIdx.x / 64;
+    if (tc >= cols) return;
+    T acc[RC / 4];
+#pragma unroll
+    for (int v = 0; v < RC / 4; ++v) acc[v] = T(0);
+    for (int r = 0; r < kb; ++r) {
+        const T l = Lt[r][tc];
+#pragma unroll
+        for (int v = 0; v < RC / 4; ++v) acc[v] = fma(l, Xs[r][tg + 4 * v], acc[v]);
+    }
+    T* ob = fv + (s.fv_off + c0 + tc) * ldf + j0;
+#pragma unroll
+    for (int v = 0; v < RC / 4; ++v) {
+        const int j = tg + 4 * v;
+        if (j < kc) ob[j] -= acc[v];
+    }
+}
+
+// x (permuted) <- front-vector top rows of each supernode of the level
+template <class T>
+__global__ void k_fv_store_x(const SnDev* __restrict__ sn, const int* __restrict__ ids, int k,
+                             const T* __restrict__ fv, int64_t ldf, T* __restrict__ xp, int64_t ldx) {
+    const SnDev s = sn[ids[blockIdx.y]];
+    const int64_t total = (int64_t)s.ns * k;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / k), j = (int)(idx % k);
+        xp[(s.first + r) * ldx + j] = fv[(s.fv_off + r) * ldf + j];
+    }
+}
+
+// P[perm[i]] = -x[i]
+template <class T>
+__global__ void k_unpermute_neg(const int32_t* __restrict__ perm, const T* __restrict__ xp, int64_t ldx,
+                                int64_t n, int k, T* __restrict__ P, int64_t ldp) {
+    const int64_t total = n * k;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / k;
+        const int j = (int)(idx % k);
+        P[(int64_t)perm[i] * ldp + j] = -xp[i * ldx + j];
+    }
+}
+
+// two 64 x 65 tiles of T
+template <class T>
+constexpr size_t tile2_bytes() { return 2 * sizeof(T) * 64 * 65; }
+
+template <class K>
+int allow_smem(K kernel, size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return fail(HBSD_ERR_CUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    return 0;
+}
+
+inline int grid_for(int64_t work, int threads = 256) {
+    return (int)std::min<int64_t>(std::max<int64_t>(1, (work + threads - 1) / threads), 1 << 16);
+}
+
+// Largest row count below the diagonal block [k0, k0+kb) over the fronts of a level, and the
+// largest number of 64 x 64 lower-triangle tiles of the trailing matrix (grids must cover every
+// front of the level, whose ns and nf differ).
+void level_extent(const Factor& f, int h, int k0, int* max_rows, int* max_pairs) {
+    int mr = 0, mp = 0;
+    for (int q : f.levels[h]) {
+        const Supernode& sn = f.sn[q];
+        if (k0 >= sn.ns) continue;
+        const int kb = std::min(NB, sn.ns - k0);
+        const int rem = sn.ns + sn.nu - k0 - kb;
+        mr = std::max(mr, rem);
+        const int T = (rem + 63) / 64;
+        mp = std::max(mp, T * (T + 1) / 2);
+    }
+    *max_rows = mr;
+    *max_pairs = mp;
+}
+
+}  // namespace
+
+int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* aval, const int32_t* dof_node, const int32_t* grid, cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    f.n = n;
+    NDTree T;
+    for (int e = 0; e < 3; ++e) T.g[e] = grid[e];
+    const int64_t nnodes = (int64_t)grid[0] * grid[1] * grid[2];
+    for (int64_t i = 0; i < n; ++i)
+        if (dof_node[i] < 0 || dof_node[i] >= nnodes) return fail(HBSD_ERR_ARG, "dof_node out of range");
+    const int lo[3] = {0, 0, 0}, hi[3] = {grid[0], grid[1], grid[2]};
+    const bool per[3] = {true, true, true};
+    const int root = T.build(lo, hi, per);
+    if (root < 0) return fail(HBSD_ERR_ARG, "empty grid");
+    // dofs of every mesh node
+    std::vector<int64_t> nd_ptr(nnodes + 1, 0);
+    for (int64_t i = 0; i < n; ++i) nd_ptr[dof_node[i] + 1]++;
+    for (int64_t v = 0; v < nnodes; ++v) nd_ptr[v + 1] += nd_ptr[v];
+    std::vector<int32_t> nd_dofs(n);
+    {
+        std::vector<int64_t> fill(nd_ptr.begin(), nd_ptr.end() - 1);
+        for (int64_t i = 0; i < n; ++i) nd_dofs[fill[dof_node[i]]++] = (int32_t)i;
+    }
+    // postorder of the dissection tree -> supernodes (tree nodes without dofs are skipped)
+    std::vector<int> post;
+    {
+        std::vector<std::pair<int, int>> stack{{root, 0}};
+        while (!stack.empty()) {
+            auto& top = stack.back();
+            if (top.second < 2) {
+                int c = T.kids[top.first][top.second++];
+                if (c >= 0) stack.push_back({c, 0});
+            } else {
+                post.push_back(top.first);
+                stack.pop_back();
+            }
+        }
+    }
+    std::vector<int> sn_of_tree(T.nodes.size(), -1);
+    f.h_perm.clear();
+    f.h_perm.reserve(n);
+    f.sn.clear();
+    for (int t : post) {
+        std::vector<int32_t> mesh = T.nodes[t];
+        std::sort(mesh.begin(), mesh.end());
+        Supernode sn{};
+        sn.first = (int64_t)f.h_perm.size();
+        for (int32_t v : mesh)
+            for (int64_t q = nd_ptr[v]; q < nd_ptr[v + 1]; ++q) f.h_perm.push_back(nd_dofs[q]);
+        sn.ns = (int)((int64_t)f.h_perm.size() - sn.first);
+        sn.parent = -1;
+        sn.child[0] = sn.child[1] = -1;
+        if (sn.ns == 0) continue;
+        sn_of_tree[t] = (int)f.sn.size();
+        f.sn.push_back(sn);
+    }
+    if ((int64_t)f.h_perm.size() != n) return fail(HBSD_ERR_ARG, "ordering does not cover every dof");
+    // parent links: nearest ancestor that owns dofs
+    for (int t : post) {
+        const int me = sn_of_tree[t];
+        if (me < 0) continue;
+        int a = T.parent[t];
+        while (a >= 0 && sn_of_tree[a] < 0) a = T.parent[a];
+        if (a >= 0) {
+            const int p = sn_of_tree[a];
+            f.sn[me].parent = p;
+            if (f.sn[p].child[0] < 0) f.sn[p].child[0] = me;
+            else if (f.sn[p].child[1] < 0) f.sn[p].child[1] = me;
+            else return fail(HBSD_ERR_ARG, "dissection tree node with more than two children");
+        }
+    }
+    std::vector<int32_t> iperm(n);
+    for (int64_t i = 0; i < n; ++i) iperm[f.h_perm[i]] = (int32_t)i;
+    // symbolic: below-diagonal structure of each supernode (postorder = index order)
+    const int nsn = (int)f.sn.size();
+    std::vector<std::vector<int64_t>> st_rows(nsn);
+    for (int q = 0; q < nsn; ++q) {
+        Supernode& sn = f.sn[q];
+        const int64_t last = sn.first + sn.ns;
+        std::vector<int64_t> rows;
+        for (int64_t c = sn.first; c < last; ++c) {
+            const int32_t old = f.h_perm[c];
+            for (int64_t e = row_ptr[old]; e < row_ptr[old + 1]; ++e) {
+                const int64_t r = iperm[col_idx[e]];
+                if (r >= last) rows.push_back(r);
+            }
+        }
+        for (int ci = 0; ci < 2; ++ci) {
+            const int c = sn.child[ci];
+            if (c < 0) continue;
+            for (int64_t r : st_rows[c])
+                if (r >= last) rows.push_back(r);
+        }
+        std::sort(rows.begin(), rows.end());
+        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+        sn.nu = (int)rows.size();
+        st_rows[q] = std::move(rows);
+    }
+    // heights
+    int H = 0;
+    for (int q = 0; q < nsn; ++q) {
+        int h = 0;
+        for (int ci = 0; ci < 2; ++ci)
+            if (f.sn[q].child[ci] >= 0) h = std::max(h, f.sn[f.sn[q].child[ci]].level + 1);
+        f.sn[q].level = h;
+        H = std::max(H, h);
+    }
+    f.levels.assign(H + 1, {});
+    for (int q = 0; q < nsn; ++q) f.levels[f.sn[q].level].push_back(q);
+    // offsets (front storage ordered by level so a level is one contiguous range)
+    std::vector<int64_t> front_off(nsn), level_front_begin(H + 2, 0);
+    int64_t fo = 0;
+    f.nnz_L = 0; f.fv_total = 0; f.dinv_total = 0; f.ea_total = 0;
+    f.h_struct.clear();
+    f.max_front = 0; f.max_ns = 0;
+    int64_t L_tot = 0;
+    for (int h = 0; h <= H; ++h) {
+        level_front_begin[h] = fo;
+        for (int q : f.levels[h]) {
+            const int64_t nf = (int64_t)f.sn[q].ns + f.sn[q].nu;
+            front_off[q] = fo;
+            fo += nf * nf;
+        }
+    }
+    level_front_begin[H + 1] = fo;
+    for (int q = 0; q < nsn; ++q) {
+        Supernode& sn = f.sn[q];
+        const int64_t nf = (int64_t)sn.ns + sn.nu;
+        sn.L_off = L_tot;
+        L_tot += nf * sn.ns;
+        f.nnz_L += nf * sn.ns - (int64_t)sn.ns * (sn.ns - 1) / 2;
+        sn.Dinv_off = f.dinv_total;
+        f.dinv_total += (int64_t)ceil_div(sn.ns, NB) * NB * NB;
+        sn.fv_off = f.fv_total;
+        f.fv_total += nf;
+        sn.struct_off = (int64_t)f.h_struct.size();
+        f.h_struct.insert(f.h_struct.end(), st_rows[q].begin(), st_rows[q].end());
+        sn.ea_off = f.ea_total;
+        f.ea_total += sn.nu;
+        f.max_front = std::max<int>(f.max_front, (int)nf);
+        f.max_ns = std::max(f.max_ns, sn.ns);
+    }
+    // extend-add maps: child struct row -> parent front row
+    std::vector<int32_t> ea(std::max<int64_t>(1, f.ea_total));
+    for (int q = 0; q < nsn; ++q) {
+        const Supernode& c = f.sn[q];
+        if (c.parent < 0) continue;
+        const Supernode& p = f.sn[c.parent];
+        const std::vector<int64_t>& prow = st_rows[c.parent];
+        for (int r = 0; r < c.nu; ++r) {
+            const int64_t g = st_rows[q][r];
+            int32_t pos;
+            if (g < p.first + p.ns) {
+                if (g < p.first) return fail(HBSD_ERR_ARG, "symbolic: child row before parent columns");
+                pos = (int32_t)(g - p.first);
+            } else {
+                auto it = std::lower_bound(prow.begin(), prow.end(), g);
+                if (it == prow.end() || *it != g) return fail(HBSD_ERR_ARG, "symbolic: child row missing in parent");
+                pos = (int32_t)(p.ns + (it - prow.begin()));
+            }
+            ea[c.ea_off + r] = pos;
+        }
+    }
+    // matrix entries of each supernode's columns (lower triangle, permuted) -> front positions
+    LevelLists& LL = f.LL;
+    LL.offs.assign(H + 1, 0); LL.counts.assign(H + 1, 0);
+    LL.max_ns.assign(H + 1, 0); LL.max_nf.assign(H + 1, 0); LL.max_nu.assign(H + 1, 0);
+    for (int c = 0; c < 2; ++c) { LL.job_offs[c].assign(H + 1, 0); LL.job_counts[c].assign(H + 1, 0); }
+    LL.entry_offs.assign(H + 2, 0);
+    std::vector<int> ids, jobs;
+    std::vector<int64_t> epos, esrc;
+    for (int h = 0; h <= H; ++h) {
+        LL.offs[h] = (int)ids.size();
+        LL.counts[h] = (int)f.levels[h].size();
+        for (int q : f.levels[h]) {
+            ids.push_back(q);
+            LL.max_ns[h] = std::max(LL.max_ns[h], f.sn[q].ns);
+            LL.max_nu[h] = std::max(LL.max_nu[h], f.sn[q].nu);
+            LL.max_nf[h] = std::max(LL.max_nf[h], f.sn[q].ns + f.sn[q].nu);
+        }
+    }
+    for (int slot = 0; slot < 2; ++slot)
+        for (int h = 0; h <= H; ++h) {
+            LL.job_offs[slot][h] = (int)jobs.size() / 2;
+            for (int q : f.levels[h])
+                if (f.sn[q].child[slot] >= 0) { jobs.push_back(q); jobs.push_back(f.sn[q].child[slot]); }
+            LL.job_counts[slot][h] = (int)jobs.size() / 2 - LL.job_offs[slot][h];
+        }
+    for (int h = 0; h <= H; ++h) {
+        LL.entry_offs[h] = (int64_t)epos.size();
+        for (int q : f.levels[h]) {
+            const Supernode& sn = f.sn[q];
+            const int64_t nf = (int64_t)sn.ns + sn.nu;
+            const int64_t last = sn.first + sn.ns;
+            const std::vector<int64_t>& rows = st_rows[q];
+            for (int64_t c = sn.first; c < last; ++c) {
+                const int32_t old = f.h_perm[c];
+                for (int64_t e = row_ptr[old]; e < row_ptr[old + 1]; ++e) {
+                    const int64_t r = iperm[col_idx[e]];
+                    if (r < c) continue;
+                    int64_t pr;
+                    if (r < last) pr = r - sn.first;
+                    else pr = sn.ns + (std::lower_bound(rows.begin(), rows.end(), r) - rows.begin());
+                    epos.push_back(front_off[q] + (c - sn.first) * nf + pr);
+                    esrc.push_back(e);
+                }
+            }
+        }
+    }
+    LL.entry_offs[H + 1] = (int64_t)epos.size();
+    // ---- device copies ----
+    std::vector<SnDev> sd(nsn);
+    for (int q = 0; q < nsn; ++q) {
+        const Supernode& sn = f.sn[q];
+        sd[q] = SnDev{sn.first, sn.L_off, sn.Dinv_off, sn.fv_off, sn.struct_off, sn.ea_off, front_off[q],
+                      sn.ns, sn.nu, sn.child[0], sn.child[1]};
+    }
+    HBSD_TRY(f.d_sn.alloc(nsn * sizeof(SnDev) / sizeof(int) + 1));
+    HBSD_CUDA(cudaMemcpy(f.d_sn.p, sd.data(), nsn * sizeof(SnDev), cudaMemcpyHostToDevice));
+    HBSD_TRY(f.perm.alloc(n));
+    HBSD_CUDA(cudaMemcpy(f.perm.p, f.h_perm.data(), n * 4, cudaMemcpyHostToDevice));
+    HBSD_TRY(f.d_struct.alloc(std::max<size_t>(1, f.h_struct.size())));
+    if (!f.h_struct.empty())
+        HBSD_CUDA(cudaMemcpy(f.d_struct.p, f.h_struct.data(), f.h_struct.size() * 8, cudaMemcpyHostToDevice));
+    HBSD_TRY(f.ea.alloc(ea.size()));
+    HBSD_CUDA(cudaMemcpy(f.ea.p, ea.data(), ea.size() * 4, cudaMemcpyHostToDevice));
+    HBSD_TRY(LL.ids.alloc(std::max<size_t>(1, ids.size())));
+    HBSD_CUDA(cudaMemcpy(LL.ids.p, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice));
+    HBSD_TRY(LL.jobs.alloc(std::max<size_t>(2, jobs.size())));
+    if (!jobs.empty()) HBSD_CUDA(cudaMemcpy(LL.jobs.p, jobs.data(), jobs.size() * 4, cudaMemcpyHostToDevice));
+    HBSD_TRY(LL.entry_pos.alloc(std::max<size_t>(1, epos.size())));
+    HBSD_TRY(LL.entry_src.alloc(std::max<size_t>(1, esrc.size())));
+    HBSD_CUDA(cudaMemcpy(LL.entry_pos.p, epos.data(), epos.size() * 8, cudaMemcpyHostToDevice));
+    HBSD_CUDA(cudaMemcpy(LL.entry_src.p, esrc.data(), esrc.size() * 8, cudaMemcpyHostToDevice));
+    DBuf<double> d_aval;
+    HBSD_TRY(d_aval.alloc(row_ptr[n]));
+    HBSD_CUDA(cudaMemcpy(d_aval.p, aval, row_ptr[n] * 8, cudaMemcpyHostToDevice));
+    DBuf<double> fronts;
+    HBSD_TRY(fronts.alloc(std::max<int64_t>(1, fo)));
+    HBSD_TRY(f.Dinv.alloc(std::max<int64_t>(1, f.dinv_total)));
+    DBuf<int> err;
+    HBSD_TRY(err.alloc(1));
+    HBSD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    const SnDev* dsn = reinterpret_cast<const SnDev*>(f.d_sn.p);
+    HBSD_TRY(allow_smem(k_potrf_block, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_trsm_panel, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_syrk_update, tile2_bytes<double>()));
+    // ---- numeric factorisation, level by level ----
+    for (int h = 0; h <= H; ++h) {
+        const int64_t fb = level_front_begin[h], fe = level_front_begin[h + 1];
+        k_zero<<<grid_for(fe - fb), 256, 0, st>>>(fronts.p + fb, fe - fb);
+        HBSD_LAUNCHED(s);
+        const int64_t e0 = LL.entry_offs[h], e1 = LL.entry_offs[h + 1];
+        if (e1 > e0) {
+            k_scatter_entries<<<grid_for(e1 - e0), 256, 0, st>>>(LL.entry_pos.p + e0, LL.entry_src.p + e0, e1 - e0,
+                                                                 d_aval.p, fronts.p);
+            HBSD_LAUNCHED(s);
+        }
+        for (int slot = 0; slot < 2; ++slot) {
+            const int nj = LL.job_counts[slot][h];
+            if (nj == 0) continue;
+            int64_t maxw = 0;
+            for (int q : f.levels[h])
+                if (f.sn[q].child[slot] >= 0) maxw = std::max<int64_t>(maxw, (int64_t)f.sn[f.sn[q].child[slot]].nu * f.sn[f.sn[q].child[slot]].nu);
+            dim3 g(std::min(grid_for(maxw), 2048), nj);
+            k_extend_add_matrix<<<g, 256, 0, st>>>(dsn, LL.jobs.p + 2 * LL.job_offs[slot][h], nj, f.ea.p, fronts.p);
+            HBSD_LAUNCHED(s);
+        }
+        const int* lid = LL.ids.p + LL.offs[h];
+        const int cnt = LL.counts[h];
+        for (int k0 = 0; k0 < LL.max_ns[h]; k0 += NB) {
+            k_potrf_block<<<cnt, 256, tile2_bytes<double>(), st>>>(dsn, lid, cnt, k0, fronts.p, f.Dinv.p, err.p);
+            HBSD_LAUNCHED(s);
+            int rem = 0, pairs = 0;
+            level_extent(f, h, k0, &rem, &pairs);
+            if (rem <= 0) continue;
+            dim3 gt(ceil_div(rem, 64), cnt);
+            k_trsm_panel<<<gt, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p, f.Dinv.p);
+            HBSD_LAUNCHED(s);
+            dim3 gs(pairs, cnt);
+            k_syrk_update<<<gs, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p);
+            HBSD_LAUNCHED(s);
+        }
+    }
+    int herr = 0;
+    HBSD_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HBSD_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(HBSD_ERR_NOT_SPD, "factorisation of H - sigma_bar S met a non-positive pivot");
+    HBSD_TRY(f.L.alloc(std::max<int64_t>(1, L_tot)));
+    {
+        int64_t maxp = 1;
+        for (int q = 0; q < nsn; ++q) maxp = std::max<int64_t>(maxp, ((int64_t)f.sn[q].ns + f.sn[q].nu) * f.sn[q].ns);
+        dim3 g(std::min(grid_for(maxp), 1024), nsn);
+        k_copy_panels<<<g, 256, 0, st>>>(dsn, nsn, fronts.p, f.L.p);
+        HBSD_LAUNCHED(s);
+    }
+    HBSD_CUDA(cudaStreamSynchronize(st));
+    fronts.release();
+    auto t1 = std::chrono::steady_clock::now();
+    s->stats.t_factor_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    s->stats.nnz_L = f.nnz_L;
+    s->stats.n_supernodes = nsn;
+    return 0;
+}
+
+int factor_make_fp32(Factor& f, cudaStream_t st) {
+    if (f.L32.p) return 0;
+    HBSD_TRY(f.L32.alloc(f.L.n));
+    HBSD_TRY(f.Dinv32.alloc(f.Dinv.n));
+    k_to_float<<<grid_for(f.L.n), 256, 0, st>>>(f.L.p, f.L32.p, f.L.n);
+    k_to_float<<<grid_for(f.Dinv.n), 256, 0, st>>>(f.Dinv.p, f.Dinv32.p, f.Dinv.n);
+    HBSD_CUDA(cudaPeekAtLastError());
+    return 0;
+}
+
+template <class T> struct FactorData;
+template <> struct FactorData<double> {
+    static const double* L(Factor& f) { return f.L.p; }
+    static const double* D(Factor& f) { return f.Dinv.p; }
+    static DBuf<double>& fv(Factor& f) { return f.fv; }
+    static DBuf<double>& xp(Factor& f) { return f.xp; }
+};
+template <> struct FactorData<float> {
+    static const float* L(Factor& f) { return f.L32.p; }
+    static const float* D(Factor& f) { return f.Dinv32.p; }
+    static DBuf<float>& fv(Factor& f) { return f.fv32; }
+    static DBuf<float>& xp(Factor& f) { return f.xp32; }
+};
+
+template <class T>
+int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, int64_t ldp, cudaStream_t st) {
+    if (k <= 0) return 0;
+    const T* L = FactorData<T>::L(f);
+    const T* D = FactorData<T>::D(f);
+    if (!L || !D) return fail(HBSD_ERR_ARG, "factor_solve: factor not available in this precision");
+    const int64_t ldf = round_up(k, 4);
+    HBSD_TRY(FactorData<T>::fv(f).alloc((size_t)f.fv_total * ldf));
+    HBSD_TRY(FactorData<T>::xp(f).alloc((size_t)f.n * ldf));
+    T* fv = FactorData<T>::fv(f).p;
+    T* xp = FactorData<T>::xp(f).p;
+    LevelLists& LL = f.LL;
+    const SnDev* dsn = reinterpret_cast<const SnDev*>(f.d_sn.p);
+    const int H = (int)f.levels.size() - 1;
+    {
+        static bool attr_set = false;  // per template instantiation
+        if (!attr_set) {
+            HBSD_TRY(allow_smem(k_solve_diag<T, false>, tile2_bytes<T>()));
+            HBSD_TRY(allow_smem(k_solve_diag<T, true>, tile2_bytes<T>()));
+            HBSD_TRY(allow_smem(k_solve_fwd_update<T>, tile2_bytes<T>()));
+            HBSD_TRY(allow_smem(k_solve_bwd_gather<T>, tile2_bytes<T>()));
+            HBSD_TRY(allow_smem(k_solve_bwd_update<T>, tile2_bytes<T>()));
+            attr_set = true;
+        }
+    }
+    const int rchunks = ceil_div(k, RC);
+    // forward sweep
+    for (int h = 0; h <= H; ++h) {
+        const int* lid = LL.ids.p + LL.offs[h];
+        const int cnt = LL.counts[h];
+        dim3 gi(std::min(grid_for((int64_t)LL.max_nf[h] * k), 1024), cnt);
+        k_fv_init<T><<<gi, 256, 0, st>>>(dsn, lid, f.perm.p, R, ldr, k, fv, ldf);
+        HBSD_LAUNCHED(s);
+        for (int slot = 0; slot < 2; ++slot) {
+            const int nj = LL.job_counts[slot][h];
+            if (nj == 0) continue;
+            dim3 g(std::min(grid_for((int64_t)LL.max_nf[h] * k), 1024), nj);
+            k_fv_extend_add<T><<<g, 256, 0, st>>>(dsn, LL.jobs.p + 2 * LL.job_offs[slot][h], nj, f.ea.p, k, fv, ldf);
+            HBSD_LAUNCHED(s);
+        }
+        for (int k0 = 0; k0 < LL.max_ns[h]; k0 += NB) {
+            dim3 gd(rchunks, cnt);
+            k_solve_diag<T, false><<<gd, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, D, k, fv, ldf);
+            HBSD_LAUNCHED(s);
+            int rem = 0, pairs = 0;
+            level_extent(f, h, k0, &rem, &pairs);
+            if (rem <= 0) continue;
+            dim3 gu(ceil_div(rem, 64), cnt, rchunks);
+            k_solve_fwd_update<T><<<gu, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, L, k, fv, ldf);
+            HBSD_LAUNCHED(s);
+        }
+    }
+    // backward sweep
+    for (int h = H; h >= 0; --h) {
+        const int* lid = LL.ids.p + LL.offs[h];
+        const int cnt = LL.counts[h];
+        if (LL.max_nu[h] > 0) {
+            dim3 gg(ceil_div(LL.max_ns[h], 64), cnt, rchunks);
+            k_solve_bwd_gather<T><<<gg, 256, tile2_bytes<T>(), st>>>(dsn, lid, L, f.d_struct.p, xp, ldf, k, fv, ldf);
+            HBSD_LAUNCHED(s);
+        }
+        const int nblk = ceil_div(LL.max_ns[h], NB);
+        for (int b = nblk - 1; b >= 0; --b) {
+            const int k0 = b * NB;
+            dim3 gd(rchunks, cnt);
+            k_solve_diag<T, true><<<gd, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, D, k, fv, ldf);
+            HBSD_LAUNCHED(s);
+            if (k0 == 0) continue;
+            dim3 gu(ceil_div(k0, 64), cnt, rchunks);
+            k_solve_bwd_update<T><<<gu, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, L, k, fv, ldf);
+            HBSD_LAUNCHED(s);
+        }
+        dim3 gs(std::min(grid_for((int64_t)LL.max_ns[h] * k), 1024), cnt);
+        k_fv_store_x<T><<<gs, 256, 0, st>>>(dsn, lid, k, fv, ldf, xp, ldf);
+        HBSD_LAUNCHED(s);
+    }
+    k_unpermute_neg<T><<<grid_for(f.n * k), 256, 0, st>>>(f.perm.p, xp, ldf, f.n, k, P, ldp);
+    HBSD_LAUNCHED(s);
+    return 0;
+}
+
+template int factor_solve<double>(Session*, Factor&, const double*, int64_t, int, double*, int64_t, cudaStream_t);
+template int factor_solve<float>(Session*, Factor&, const float*, int64_t, int, float*, int64_t, cudaStream_t);
+
+}  // namespace hbsd

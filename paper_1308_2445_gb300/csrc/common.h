@@ -1,0 +1,225 @@
+// Internal declarations shared by the translation units of libhbsd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hbsd.h"
+
+namespace hbsd {
+
+// ---- errors -------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define HBSD_CUDA(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return ::hbsd::fail(HBSD_ERR_CUDA, std::string(#call) + ": " +               \
+                                                   cudaGetErrorString(e_));              \
+    } while (0)
+
+#define HBSD_TRY(call)                                                                   \
+    do {                                                                                 \
+        int s_ = (call);                                                                 \
+        if (s_ < 0) return s_;                                                           \
+    } while (0)
+
+#define HBSD_LAUNCHED(h)                                                                 \
+    do {                                                                                 \
+        cudaError_t e_ = cudaPeekAtLastError();                                          \
+        if (e_ != cudaSuccess)                                                           \
+            return ::hbsd::fail(HBSD_ERR_CUDA, std::string("launch: ") +                 \
+                                                   cudaGetErrorString(e_));              \
+        ::hbsd::count_launch(h);                                                         \
+    } while (0)
+
+struct Session;
+void count_launch(Session* s);
+
+// ---- device memory owned by a session ---------------------------------------------------
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    int alloc(size_t count);
+    void release();
+    ~DBuf() { release(); }
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+};
+
+template <class T>
+int DBuf<T>::alloc(size_t count) {
+    if (count <= n && p) return 0;
+    release();
+    if (count == 0) return 0;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        return fail(HBSD_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+    return 0;
+}
+
+template <class T>
+void DBuf<T>::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+}
+
+// ---- SELL-C-sigma matrix with interleaved (h, s) values -----------------------------------
+struct Sell {
+    int C = 8;                  // slice height
+    int sigma = 256;            // sorting window
+    int64_t n = 0, nnz = 0;
+    int64_t n_slices = 0, n_slots = 0, stored = 0;
+    DBuf<int64_t> slice_ptr;    // first entry of each slice
+    DBuf<int32_t> slice_len;    // padded row length of each slice
+    DBuf<int32_t> cols;         // stored column indices, slice-major, then entry-major, then row
+    DBuf<double2> hs;           // (h - sigma0 s, s) per stored entry
+    DBuf<float2> hs32;          // FP32 copy for the mixed-precision path
+    DBuf<int32_t> slot_row;     // original row of each slot (-1 for padding slots)
+    std::vector<int64_t> h_entry_of_csr;  // stored position of each CSR entry (host, for updates)
+};
+
+int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+               const double* hval, const double* sval, double sigma0);
+int sell_update_h(Sell& m, const double* hval, const double* sval, double sigma0);
+
+// Y_h = Hs X, Y_s = S X for k columns; X, Y row-major.
+template <class T>
+int spmm_pair(Session* s, const Sell& m, const T* X, int64_t ldx, int k, T* HX, int64_t ldhx,
+              T* SX, int64_t ldsx, cudaStream_t st);
+// Y(:, j) = (Hs - e_j S) X(:, j)
+template <class T>
+int spmm_shifted(Session* s, const Sell& m, const T* X, int64_t ldx, int k, const T* e, T* Y,
+                 int64_t ldy, cudaStream_t st);
+
+// ---- supernodal Cholesky of H - sigma_bar S ----------------------------------------------
+struct Supernode {
+    int64_t first;       // first column (permuted order)
+    int ns;              // columns
+    int nu;              // rows below the diagonal block
+    int parent;          // -1 for a root
+    int level;           // height: leaves 0
+    int child[2];        // up to two children (-1 none)
+    int64_t struct_off;  // offset of the below-diagonal row list in Factor::h_struct
+    int64_t L_off;       // offset of the (ns+nu) x ns column-major panel in Factor::L
+    int64_t Dinv_off;    // offset of the inverted NB x NB diagonal blocks
+    int64_t ea_off;      // offset of this node's child->parent map (nu entries) in Factor::ea
+    int64_t fv_off;      // offset of this node's front vector (ns+nu rows) in the solve workspace
+};
+
+// per-level work lists of the factor (device copies used by the batched kernels)
+struct LevelLists {
+    std::vector<int> offs;                        // offset of each level's id list in ids
+    std::vector<int> counts;
+    std::vector<int> max_ns, max_nf, max_nu;
+    std::vector<int> job_offs[2], job_counts[2];  // (parent, child) pairs per level per child slot
+    std::vector<int64_t> entry_offs;              // matrix-entry scatter list per level
+    DBuf<int> ids;
+    DBuf<int> jobs;
+    DBuf<int64_t> entry_pos, entry_src;
+};
+
+struct Factor {
+    static constexpr int NB = 64;
+    LevelLists LL;
+    int64_t n = 0;
+    std::vector<Supernode> sn;
+    std::vector<int64_t> h_struct;               // below-diagonal rows of every supernode
+    std::vector<std::vector<int>> levels;        // supernodes by height
+    std::vector<int32_t> h_perm;                 // new -> old
+    int64_t nnz_L = 0, fv_total = 0, dinv_total = 0, ea_total = 0;
+    DBuf<int32_t> perm;                          // new -> old
+    DBuf<int64_t> d_struct;
+    DBuf<int32_t> ea;                            // child row -> parent front row
+    DBuf<double> L;                              // panels
+    DBuf<float> L32;                             // FP32 copy (mixed path)
+    DBuf<double> Dinv;                           // inverted diagonal blocks
+    DBuf<float> Dinv32;
+    DBuf<int> d_sn;                              // packed per-supernode descriptors (see chol.cu)
+    int max_front = 0;
+    int max_ns = 0;
+    // solve workspace
+    DBuf<double> fv;                             // front vectors, fv_total * kmax
+    DBuf<double> xp;                             // permuted solution, n * kmax
+    DBuf<float> fv32, xp32;
+    int kmax = 0;
+};
+
+int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                 const double* aval, const int32_t* dof_node, const int32_t* grid, cudaStream_t st);
+template <class T>
+int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, int64_t ldp,
+                 cudaStream_t st);
+int factor_make_fp32(Factor& f, cudaStream_t st);
+
+// ---- dense helpers -------------------------------------------------------------------
+// column sums over rows of a row-major block: out[j] = sum_i A(i, j) * B(i, j)  (B may be A)
+template <class T>
+int col_dots(Session* s, const T* A, int64_t lda, const T* B, int64_t ldb, int64_t n, int k,
+             double* out, cudaStream_t st);
+int gram2(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1,
+          int q1, const double* H0, int64_t ldh0, const double* H1, int64_t ldh1,
+          const double* S0, int64_t lds0, const double* S1, int64_t lds1, int64_t n, double* HR,
+          double* SR, cudaStream_t st);
+int update2(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
+            int64_t n, const double* W, int k, cudaStream_t st);
+int rayleigh_ritz(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
+                  double* W, int* info_host, cudaStream_t st);
+template <class T>
+int residual(Session* s, const T* PH, int64_t ldh, const T* PS, int64_t lds, const double* E, int m,
+             T* R, int64_t ldr, int64_t n, double* res, double* rnorm, cudaStream_t st);
+template <class T>
+int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double eta, int maxit, T* X,
+                 int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st);
+
+// ---- session -----------------------------------------------------------------------
+struct Session {
+    int64_t n = 0, nnz = 0;
+    hbsd_options opt{};
+    double sigma0 = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Sell A;                     // (Hs, S) pattern
+    Factor F;
+    bool has_factor = false;
+    hbsd_stats stats{};
+    int launches = 0;
+    // CSR kept on host for hbsd_update_H
+    std::vector<double> h_sval;
+    // workspaces (FP64 driver)
+    DBuf<double> ws;            // generic scratch for reductions
+    DBuf<double> rr_ws;         // Rayleigh-Ritz workspace
+    DBuf<int> rr_info;
+    // MINRES workspace (minres.cu)
+    DBuf<double> mr_d;
+    DBuf<float> mr_f;
+    DBuf<double> mr_col;        // per-column recurrence state, reinterpreted in minres.cu
+    DBuf<double> mr_red;
+    DBuf<int> mr_any, mr_steps;
+    // warm-start state
+    DBuf<double> psi_keep;
+    int keep_w = 0;
+    int64_t keep_ld = 0;
+};
+
+// ---- small utilities -----------------------------------------------------------------
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace hbsd
+
+struct hbsd_handle {
+    hbsd::Session s;
+};

@@ -1,0 +1,562 @@
+// LABPSD driver (Sec. 3 outline, steps 1-12, with remarks 1-6) on the GB300 kernels, and the
+// C ABI of include/hbsd.h.  The host runs the outer loop and decides, from the per-column
+// relative residuals read back each iteration, which columns are preconditioned (remark 3)
+// and which are refined locally (remark 4); every block operation runs in the kernels of
+// sell.cu, dense.cu, chol.cu and minres.cu.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+#include "common.h"
+
+namespace hbsd {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+void count_launch(Session* s) {
+    if (s) s->launches++;
+}
+
+// ---- small kernels of the driver ---------------------------------------------------------
+namespace {
+
+inline int grid_for(int64_t work) {
+    return (int)std::min<int64_t>(std::max<int64_t>(1, (work + 255) / 256), 8192);
+}
+
+// R_U(:, j) = PsiH(:, U_j) - PsiS(:, U_j) E_{U_j}  (step 4 restricted to the unconverged columns)
+template <class T>
+__global__ void k_gather_residual(const T* __restrict__ PH, int64_t ldh, const T* __restrict__ PS, int64_t lds,
+                                  const double* __restrict__ E, const int* __restrict__ U, int p, int64_t n,
+                                  T* __restrict__ R, int64_t ldr) {
+    const int64_t total = n * p;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / p;
+        const int j = (int)(idx % p);
+        const int c = U[j];
+        R[i * ldr + j] = PH[i * ldh + c] - PS[i * lds + c] * (T)E[c];
+    }
+}
+
+template <class T>
+__global__ void k_gather_cols(const T* __restrict__ src, int64_t lds, const int* __restrict__ idx, int k, int64_t n,
+                              T* __restrict__ dst, int64_t ldd) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t % k);
+        dst[i * ldd + j] = src[i * lds + idx[j]];
+    }
+}
+
+template <class T>
+__global__ void k_scatter_cols(const T* __restrict__ src, int64_t lds, const int* __restrict__ idx, int k, int64_t n,
+                               T* __restrict__ dst, int64_t ldd) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t % k);
+        dst[i * ldd + idx[j]] = src[i * lds + j];
+    }
+}
+
+template <class T>
+__global__ void k_copy_block(const T* __restrict__ src, int64_t lds, int k, int64_t n, T* __restrict__ dst, int64_t ldd) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t % k);
+        dst[i * ldd + j] = src[i * lds + j];
+    }
+}
+
+__global__ void k_shift_add(const double* __restrict__ E, int k, double sigma0, double* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) out[j] = E[j] + sigma0;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator + Box-Muller
+constexpr uint64_t GOLDEN = 0x9E3779B97F4A7C15ull;
+inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+void seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out) {
+    const uint64_t key = mix64((seed ^ (stream * GOLDEN)) + GOLDEN);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t t = 0; t < count; t += 2) {
+        const uint64_t z1 = mix64(key + (uint64_t)(t + 1) * GOLDEN);
+        const uint64_t z2 = mix64(key + (uint64_t)(t + 2) * GOLDEN);
+        const double u1 = (double)(z1 >> 11) * (1.0 / 9007199254740992.0);
+        const double u2 = (double)(z2 >> 11) * (1.0 / 9007199254740992.0);
+        const double rad = std::sqrt(-2.0 * std::log1p(-u1));
+        out[t] = rad * std::cos(two_pi * u2);
+        if (t + 1 < count) out[t + 1] = rad * std::sin(two_pi * u2);
+    }
+}
+
+}  // namespace
+
+// ---- step timers: CUDA events on the session stream, read back after host syncs ------------------
+struct StepTimer {
+    enum { MATVEC, RESID, PRECOND, LOCAL, GRAM, RR, UPDATE, NCLS };
+    static constexpr int NEV = 32;
+    cudaEvent_t ev[NEV][2];
+    int cls[NEV];
+    int used = 0;
+    double acc[NCLS] = {};
+    bool ok = false;
+    StepTimer() {
+        ok = true;
+        for (int i = 0; i < NEV && ok; ++i)
+            ok = cudaEventCreate(&ev[i][0]) == cudaSuccess && cudaEventCreate(&ev[i][1]) == cudaSuccess;
+    }
+    ~StepTimer() {
+        for (int i = 0; i < NEV; ++i) { cudaEventDestroy(ev[i][0]); cudaEventDestroy(ev[i][1]); }
+    }
+    int begin(int c, cudaStream_t st) {
+        if (!ok) return -1;
+        if (used == NEV) flush();
+        const int i = used++;
+        cls[i] = c;
+        cudaEventRecord(ev[i][0], st);
+        return i;
+    }
+    void end(int i, cudaStream_t st) {
+        if (i >= 0) cudaEventRecord(ev[i][1], st);
+    }
+    void flush() {  // waits for the recorded pairs
+        for (int i = 0; i < used; ++i) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(ev[i][1]) == cudaSuccess && cudaEventElapsedTime(&ms, ev[i][0], ev[i][1]) == cudaSuccess)
+                acc[cls[i]] += ms;
+        }
+        used = 0;
+    }
+};
+
+// ---- per-solve buffers -----------------------------------------------------------------------
+struct SolveBufs {
+    DBuf<double> Psi, PsiH, PsiS, P, PH, PS, RU, Xa, Ra;
+    DBuf<double> E, res, HR, SR, W, theta, shifts, out_lam;
+    DBuf<int> Ulist, Llist, steps;
+};
+
+static int labpsd_fp64(Session* S, int m, double tol, const double* X0, int64_t ldx0, double* lam_dev,
+                       double* X_dev, int64_t ldx, int* iters_out) {
+    cudaStream_t st = S->stream;
+    const hbsd_options& o = S->opt;
+    const int64_t n = S->n;
+    const int m0 = o.m0 >= 0 ? o.m0 : std::max(3, (m + 9) / 10);
+    const int w = m + m0;
+    if (m < 1 || w > n) return fail(HBSD_ERR_ARG, "nev + m0 must lie in [1, n]");
+    const int64_t ldw = round_up(w, 2), ldp = round_up(std::max(m, 1), 2);
+    const int qmax = w + m;
+    SolveBufs B;
+    HBSD_TRY(B.Psi.alloc(n * ldw)); HBSD_TRY(B.PsiH.alloc(n * ldw)); HBSD_TRY(B.PsiS.alloc(n * ldw));
+    HBSD_TRY(B.P.alloc(n * ldp)); HBSD_TRY(B.PH.alloc(n * ldp)); HBSD_TRY(B.PS.alloc(n * ldp));
+    HBSD_TRY(B.RU.alloc(n * ldp)); HBSD_TRY(B.Xa.alloc(n * ldp)); HBSD_TRY(B.Ra.alloc(n * ldp));
+    HBSD_TRY(B.E.alloc(w)); HBSD_TRY(B.res.alloc(m)); HBSD_TRY(B.theta.alloc(w));
+    HBSD_TRY(B.HR.alloc((size_t)qmax * qmax)); HBSD_TRY(B.SR.alloc((size_t)qmax * qmax));
+    HBSD_TRY(B.W.alloc((size_t)qmax * w)); HBSD_TRY(B.shifts.alloc(m));
+    HBSD_TRY(B.Ulist.alloc(m)); HBSD_TRY(B.Llist.alloc(m)); HBSD_TRY(B.steps.alloc(m));
+    {   // scratch of the reductions and the Gram partials, sized once (no reallocation mid-solve)
+        const int tiles = ceil_div(qmax, 32);
+        HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + (size_t)304 * 2 * qmax + 1024));
+        HBSD_TRY(S->rr_ws.alloc((size_t)4 * qmax * qmax + 3 * qmax + 64));
+        HBSD_TRY(S->rr_info.alloc(4));
+    }
+    hbsd_stats& stt = S->stats;
+    stt.iters = stt.iters_fp64 = 0;
+    stt.minres_steps = stt.precond_cols = stt.local_cols = 0;
+    stt.rr_fallbacks = 0;
+    stt.matvec_cols = stt.minres_spmm_cols = 0;
+    stt.precond_calls = 0;
+    StepTimer tm;
+    int ti;
+    // steps 1-3 on a cold start: Rayleigh-Ritz on span(X0), then Psi_H, Psi_S
+    k_copy_block<double><<<grid_for(n * w), 256, 0, st>>>(X0, ldx0, w, n, B.Psi.p, ldw);
+    HBSD_LAUNCHED(S);
+    ti = tm.begin(StepTimer::MATVEC, st);
+    HBSD_TRY(spmm_pair<double>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+    tm.end(ti, st);
+    stt.matvec_cols += w;
+    ti = tm.begin(StepTimer::GRAM, st);
+    HBSD_TRY(gram2(S, B.Psi.p, ldw, w, nullptr, 0, 0, B.PsiH.p, ldw, nullptr, 0, B.PsiS.p, ldw, nullptr, 0, n,
+                   B.HR.p, B.SR.p, st));
+    tm.end(ti, st);
+    int info[2];
+    ti = tm.begin(StepTimer::RR, st);
+    HBSD_TRY(rayleigh_ritz(S, B.HR.p, B.SR.p, w, w, B.theta.p, B.W.p, info, st));
+    tm.end(ti, st);
+    stt.rr_fallbacks += info[0];
+    ti = tm.begin(StepTimer::UPDATE, st);
+    HBSD_TRY(update2(S, B.Psi.p, ldw, w, nullptr, 0, 0, n, B.W.p, w, st));
+    HBSD_TRY(update2(S, B.PsiH.p, ldw, w, nullptr, 0, 0, n, B.W.p, w, st));
+    HBSD_TRY(update2(S, B.PsiS.p, ldw, w, nullptr, 0, 0, n, B.W.p, w, st));
+    tm.end(ti, st);
+    std::vector<double> E(w), Eprev, res(m);
+    HBSD_CUDA(cudaMemcpyAsync(B.E.p, B.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
+    HBSD_CUDA(cudaMemcpyAsync(E.data(), B.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
+    int iters = 0;
+    bool converged = false;
+    const bool hybrid = o.precond == HBSD_PRECOND_HYBRID;
+    std::vector<int> U, Lpos;
+    std::vector<double> shifts;
+    for (;;) {
+        // steps 4-5
+        ti = tm.begin(StepTimer::RESID, st);
+        HBSD_TRY(residual<double>(S, B.PsiH.p, ldw, B.PsiS.p, ldw, B.E.p, m, nullptr, 0, n, B.res.p, nullptr, st));
+        tm.end(ti, st);
+        HBSD_CUDA(cudaMemcpyAsync(res.data(), B.res.p, m * 8, cudaMemcpyDeviceToHost, st));
+        HBSD_CUDA(cudaStreamSynchronize(st));
+        double rmax = 0.0;
+        for (double r : res) rmax = std::max(rmax, r);
+        stt.res_max = rmax;
+        if (rmax <= tol) { converged = true; break; }
+        if (iters >= o.max_outer) break;
+        // step 6: unconverged columns (remark 3), localized among them (remark 4)
+        U.clear(); Lpos.clear(); shifts.clear();
+        for (int i = 0; i < m; ++i)
+            if (res[i] > tol) U.push_back(i);
+        const int p = (int)U.size();
+        if (hybrid && !Eprev.empty()) {
+            for (int j = 0; j < p; ++j) {
+                const int i = U[j];
+                if (res[i] <= o.tau1 && std::fabs(E[i] - Eprev[i]) <= o.tau2 * std::fabs(Eprev[i])) {
+                    Lpos.push_back(j);
+                    shifts.push_back(E[i]);
+                }
+            }
+        }
+        const int a = (int)Lpos.size();
+        HBSD_CUDA(cudaMemcpyAsync(B.Ulist.p, U.data(), p * sizeof(int), cudaMemcpyHostToDevice, st));
+        ti = tm.begin(StepTimer::RESID, st);
+        k_gather_residual<double><<<grid_for(n * p), 256, 0, st>>>(B.PsiH.p, ldw, B.PsiS.p, ldw, B.E.p, B.Ulist.p, p,
+                                                                  n, B.RU.p, ldp);
+        HBSD_LAUNCHED(S);
+        tm.end(ti, st);
+        ti = tm.begin(StepTimer::PRECOND, st);
+        HBSD_TRY(factor_solve<double>(S, S->F, B.RU.p, ldp, p, B.P.p, ldp, st));   // 6(a)
+        tm.end(ti, st);
+        stt.precond_cols += p;
+        stt.precond_calls += 1;
+        if (a > 0) {                                                                 // 6(b)
+            ti = tm.begin(StepTimer::LOCAL, st);
+            HBSD_CUDA(cudaMemcpyAsync(B.Llist.p, Lpos.data(), a * sizeof(int), cudaMemcpyHostToDevice, st));
+            HBSD_CUDA(cudaMemcpyAsync(B.shifts.p, shifts.data(), a * 8, cudaMemcpyHostToDevice, st));
+            k_gather_cols<double><<<grid_for(n * a), 256, 0, st>>>(B.P.p, ldp, B.Llist.p, a, n, B.Xa.p, ldp);
+            HBSD_LAUNCHED(S);
+            k_gather_cols<double><<<grid_for(n * a), 256, 0, st>>>(B.RU.p, ldp, B.Llist.p, a, n, B.Ra.p, ldp);
+            HBSD_LAUNCHED(S);
+            int64_t msteps = 0;
+            HBSD_TRY(minres_batch<double>(S, B.Ra.p, ldp, B.shifts.p, a, o.eta, o.max_minres, B.Xa.p, ldp, B.steps.p,
+                                          &msteps, st));
+            k_scatter_cols<double><<<grid_for(n * a), 256, 0, st>>>(B.Xa.p, ldp, B.Llist.p, a, n, B.P.p, ldp);
+            HBSD_LAUNCHED(S);
+            tm.end(ti, st);
+            stt.minres_steps += msteps;
+            stt.local_cols += a;
+        }
+        // step 7
+        ti = tm.begin(StepTimer::MATVEC, st);
+        HBSD_TRY(spmm_pair<double>(S, S->A, B.P.p, ldp, p, B.PH.p, ldp, B.PS.p, ldp, st));
+        tm.end(ti, st);
+        stt.matvec_cols += p;
+        // step 8
+        const int q = w + p;
+        ti = tm.begin(StepTimer::GRAM, st);
+        HBSD_TRY(gram2(S, B.Psi.p, ldw, w, B.P.p, ldp, p, B.PsiH.p, ldw, B.PH.p, ldp, B.PsiS.p, ldw, B.PS.p, ldp, n,
+                       B.HR.p, B.SR.p, st));
+        tm.end(ti, st);
+        // step 9
+        ti = tm.begin(StepTimer::RR, st);
+        HBSD_TRY(rayleigh_ritz(S, B.HR.p, B.SR.p, q, w, B.theta.p, B.W.p, info, st));
+        tm.end(ti, st);
+        stt.rr_fallbacks += info[0];
+        // steps 10-11
+        ti = tm.begin(StepTimer::UPDATE, st);
+        HBSD_TRY(update2(S, B.Psi.p, ldw, w, B.P.p, ldp, p, n, B.W.p, w, st));
+        HBSD_TRY(update2(S, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, B.W.p, w, st));
+        HBSD_TRY(update2(S, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, B.W.p, w, st));
+        tm.end(ti, st);
+        Eprev = E;
+        HBSD_CUDA(cudaMemcpyAsync(B.E.p, B.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
+        HBSD_CUDA(cudaMemcpyAsync(E.data(), B.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
+        ++iters;
+    }
+    stt.iters = iters;
+    stt.iters_fp64 = iters;
+    tm.flush();
+    stt.t_matvec_ms = tm.acc[StepTimer::MATVEC];
+    stt.t_resid_ms = tm.acc[StepTimer::RESID];
+    stt.t_precond_ms = tm.acc[StepTimer::PRECOND];
+    stt.t_local_ms = tm.acc[StepTimer::LOCAL];
+    stt.t_gram_ms = tm.acc[StepTimer::GRAM];
+    stt.t_rr_ms = tm.acc[StepTimer::RR];
+    stt.t_update_ms = tm.acc[StepTimer::UPDATE];
+    if (lam_dev) {
+        k_shift_add<<<ceil_div(m, 128), 128, 0, st>>>(B.E.p, m, S->sigma0, lam_dev);
+        HBSD_LAUNCHED(S);
+    }
+    if (X_dev) {
+        k_copy_block<double><<<grid_for(n * m), 256, 0, st>>>(B.Psi.p, ldw, m, n, X_dev, ldx);
+        HBSD_LAUNCHED(S);
+    }
+    // keep the block for a warm start
+    HBSD_TRY(S->psi_keep.alloc(n * ldw));
+    HBSD_CUDA(cudaMemcpyAsync(S->psi_keep.p, B.Psi.p, n * ldw * 8, cudaMemcpyDeviceToDevice, st));
+    S->keep_w = w;
+    S->keep_ld = ldw;
+    HBSD_CUDA(cudaStreamSynchronize(st));
+    if (iters_out) *iters_out = iters;
+    return converged ? HBSD_OK : HBSD_NOT_CONVERGED;
+}
+
+}  // namespace hbsd
+
+using namespace hbsd;
+
+// ---- C ABI ------------------------------------------------------------------------------
+extern "C" {
+
+void hbsd_options_default(hbsd_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->sigma_bar = std::numeric_limits<double>::quiet_NaN();
+    opt->sigma0 = std::numeric_limits<double>::quiet_NaN();
+    opt->m0 = -1;
+    opt->tau1 = 0.1;
+    opt->tau2 = 0.1;
+    opt->eta = 0.25;
+    opt->max_minres = 20;
+    opt->max_outer = 1000;
+    opt->precision = HBSD_PRECISION_FP64;
+    opt->precond = HBSD_PRECOND_HYBRID;
+    opt->seed = 1;
+}
+
+const char* hbsd_status_string(int status) {
+    switch (status) {
+        case HBSD_OK: return "ok";
+        case HBSD_NOT_CONVERGED: return "not converged";
+        case HBSD_BUSY: return "busy";
+        case HBSD_ERR_ARG: return "invalid argument";
+        case HBSD_ERR_OOM: return "out of device memory";
+        case HBSD_ERR_NOT_SPD: return "H - sigma_bar S is not positive definite";
+        case HBSD_ERR_RR_RANK: return "search space rank too small";
+        case HBSD_ERR_TIMEOUT: return "device wait timed out";
+        case HBSD_ERR_CUDA: return "CUDA error";
+        case HBSD_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* hbsd_last_error(void) { return g_last_error.c_str(); }
+
+int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* lb, const hbsd_options* opt,
+                void* stream, hbsd_handle** out) {
+    if (!out) return fail(HBSD_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!H || !Sm || !lb || !opt) return fail(HBSD_ERR_ARG, "H, S, local blocks and options are required");
+    if (H->is_complex || Sm->is_complex) return fail(HBSD_ERR_UNSUPPORTED, "complex Hermitian input is not built yet");
+    if (H->n <= 0 || H->n != Sm->n || H->nnz != Sm->nnz || H->nnz != H->row_ptr[H->n])
+        return fail(HBSD_ERR_ARG, "H and S must have the same n and nnz");
+    if (!H->row_ptr || !H->col_idx || !H->val || !Sm->val || !Sm->row_ptr || !Sm->col_idx)
+        return fail(HBSD_ERR_ARG, "NULL CSR array");
+    if (std::memcmp(H->row_ptr, Sm->row_ptr, (H->n + 1) * 8) != 0 ||
+        std::memcmp(H->col_idx, Sm->col_idx, H->nnz * 4) != 0)
+        return fail(HBSD_ERR_ARG, "H and S must share one sparsity pattern");
+    for (int64_t e = 0; e < H->nnz; ++e)
+        if (H->col_idx[e] < 0 || H->col_idx[e] >= H->n) return fail(HBSD_ERR_ARG, "column index out of range");
+    if (!std::isfinite(opt->sigma_bar)) return fail(HBSD_ERR_ARG, "sigma_bar must be set");
+    if (!lb->dof_node || lb->grid[0] <= 0 || lb->grid[1] <= 0 || lb->grid[2] <= 0)
+        return fail(HBSD_ERR_ARG, "local blocks need dof_node and a positive grid");
+    hbsd_handle* h = new hbsd_handle();
+    Session* S = &h->s;
+    S->n = H->n;
+    S->nnz = H->nnz;
+    S->opt = *opt;
+    S->sigma0 = std::isnan(opt->sigma0) ? opt->sigma_bar : opt->sigma0;
+    if (stream) {
+        S->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreate(&S->stream) != cudaSuccess) {  // blocking: ordered with the legacy default stream
+            delete h;
+            return fail(HBSD_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        S->own_stream = true;
+    }
+    int rc = sell_build(S->A, S->n, H->row_ptr, H->col_idx, H->val, Sm->val, S->sigma0);
+    if (rc < 0) { hbsd_destroy(h); return rc; }
+    S->h_sval.assign(Sm->val, Sm->val + S->nnz);
+    std::vector<double> aval(S->nnz);
+    for (int64_t e = 0; e < S->nnz; ++e) aval[e] = H->val[e] - opt->sigma_bar * Sm->val[e];
+    rc = factor_build(S, S->F, S->n, H->row_ptr, H->col_idx, aval.data(), lb->dof_node, lb->grid, S->stream);
+    if (rc < 0) { std::string keep = g_last_error; hbsd_destroy(h); g_last_error = keep; return rc; }
+    S->has_factor = true;
+    *out = h;
+    return HBSD_OK;
+}
+
+int hbsd_update_H(hbsd_handle* h, const double* H_val) {
+    if (!h || !H_val) return fail(HBSD_ERR_ARG, "NULL argument");
+    return sell_update_h(h->s.A, H_val, h->s.h_sval.data(), h->s.sigma0);
+}
+
+void hbsd_destroy(hbsd_handle* h) {
+    if (!h) return;
+    if (h->s.stream) cudaStreamSynchronize(h->s.stream);
+    if (h->s.own_stream && h->s.stream) cudaStreamDestroy(h->s.stream);
+    delete h;
+}
+
+int64_t hbsd_n(const hbsd_handle* h) { return h ? h->s.n : -1; }
+double hbsd_sigma0(const hbsd_handle* h) { return h ? h->s.sigma0 : 0.0; }
+void hbsd_get_stats(const hbsd_handle* h, hbsd_stats* st) {
+    if (h && st) *st = h->s.stats;
+}
+
+static int m0_of(const Session& S, int nev) { return S.opt.m0 >= 0 ? S.opt.m0 : std::max(3, (nev + 9) / 10); }
+
+int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0, double* lambda_dev,
+                      double* X_dev, int64_t ldx, int* iters, hbsd_stats* st) {
+    if (!h) return fail(HBSD_ERR_ARG, "NULL handle");
+    Session* S = &h->s;
+    if (nev < 1 || !(tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
+    const int w = nev + m0_of(*S, nev);
+    if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
+    if (S->opt.precision != HBSD_PRECISION_FP64) return fail(HBSD_ERR_UNSUPPORTED, "precision mode not built yet");
+    DBuf<double> x0buf;
+    if (!X0_dev) {
+        std::vector<double> hx((size_t)S->n * w);
+        seed_normals(S->opt.seed, 2, (int64_t)hx.size(), hx.data());
+        HBSD_TRY(x0buf.alloc(hx.size()));
+        HBSD_CUDA(cudaMemcpy(x0buf.p, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice));
+        X0_dev = x0buf.p;
+        ldx0 = w;
+    } else if (ldx0 < w) {
+        return fail(HBSD_ERR_ARG, "ldx0 < nev + m0");
+    }
+    S->launches = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = labpsd_fp64(S, nev, tol, X0_dev, ldx0, lambda_dev, X_dev, ldx, iters);
+    auto t1 = std::chrono::steady_clock::now();
+    S->stats.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    S->stats.gpu_launches = S->launches;
+    if (st) *st = S->stats;
+    return rc;
+}
+
+int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm, double* lambda, double* X, int* iters,
+               hbsd_stats* st) {
+    if (!h || !lambda) return fail(HBSD_ERR_ARG, "NULL handle or lambda");
+    Session* S = &h->s;
+    if (nev < 1) return fail(HBSD_ERR_ARG, "nev >= 1 required");
+    const int w = nev + m0_of(*S, nev);
+    if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
+    DBuf<double> x0, lam, xo;
+    const double* x0p = nullptr;
+    int64_t ld0 = w;
+    if (warm) {
+        if (X0) return fail(HBSD_ERR_ARG, "warm start takes X0 = NULL");
+        if (!S->psi_keep.p || S->keep_w != w) return fail(HBSD_ERR_ARG, "no previous block of this width to warm-start from");
+        x0p = S->psi_keep.p;
+        ld0 = S->keep_ld;
+    } else if (X0) {
+        HBSD_TRY(x0.alloc((size_t)S->n * w));
+        HBSD_CUDA(cudaMemcpyAsync(x0.p, X0, (size_t)S->n * w * 8, cudaMemcpyHostToDevice, S->stream));
+        x0p = x0.p;
+    }
+    HBSD_TRY(lam.alloc(nev));
+    if (X) HBSD_TRY(xo.alloc((size_t)S->n * nev));
+    DBuf<double> keep_copy;
+    if (warm) {  // the solve overwrites psi_keep; start from a copy
+        HBSD_TRY(keep_copy.alloc(S->psi_keep.n));
+        HBSD_CUDA(cudaMemcpyAsync(keep_copy.p, S->psi_keep.p, S->psi_keep.n * 8, cudaMemcpyDeviceToDevice, S->stream));
+        x0p = keep_copy.p;
+    }
+    int rc = hbsd_solve_device(h, nev, tol, x0p, ld0, lam.p, X ? xo.p : nullptr, nev, iters, st);
+    if (rc < 0) return rc;
+    HBSD_CUDA(cudaMemcpy(lambda, lam.p, nev * 8, cudaMemcpyDeviceToHost));
+    if (X) HBSD_CUDA(cudaMemcpy(X, xo.p, (size_t)S->n * nev * 8, cudaMemcpyDeviceToHost));
+    return rc;
+}
+
+// ---- step-level entry points ---------------------------------------------------------------
+int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx, double* SX,
+                   int64_t ldsx) {
+    if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    return spmm_pair<double>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+}
+
+int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e, double* Y, int64_t ldy) {
+    if (!h || !X || !e || !Y || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    return spmm_shifted<double>(&h->s, h->s.A, X, ldx, k, e, Y, ldy, h->s.stream);
+}
+
+int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double* PsiS, int64_t lds, const double* E,
+                  int m, double* R, int64_t ldr, double* res) {
+    if (!h || !PsiH || !PsiS || !E || !res || m <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    Session* S = &h->s;
+    HBSD_TRY(S->ws.alloc((size_t)304 * 2 * m + 64));
+    return residual<double>(S, PsiH, ldh, PsiS, lds, E, m, R, ldr, S->n, res, nullptr, S->stream);
+}
+
+int hbsd_precond_apply(hbsd_handle* h, const double* R, int64_t ldr, int k, double* P, int64_t ldp) {
+    if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    return factor_solve<double>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream);
+}
+
+int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k, double eta, int max_minres,
+                double* P, int64_t ldp, int* steps) {
+    if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    Session* S = &h->s;
+    HBSD_TRY(S->ws.alloc((size_t)304 * 2 * std::max(k, 1) + 64));
+    return minres_batch<double>(S, R, ldr, e, k, eta, max_minres, P, ldp, steps, nullptr, S->stream);
+}
+
+// Step-level calls without a session run on a temporary one that only carries scratch.
+static Session* scratch_session() {
+    static thread_local Session* s = nullptr;
+    if (!s) s = new Session();
+    return s;
+}
+
+int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs, int64_t n,
+              int q, double* HR, double* SR, void* stream) {
+    if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    Session* S = scratch_session();
+    const int tiles = ceil_div(q, 32);
+    HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + 1024));
+    return gram2(S, Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR, SR,
+                 (cudaStream_t)stream);
+}
+
+int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double* theta, double* W, int* info,
+                       void* stream) {
+    if (!HR || !SR || !theta || !W) return fail(HBSD_ERR_ARG, "bad arguments");
+    Session* S = scratch_session();
+    int hinfo[2] = {0, 0};
+    int rc = rayleigh_ritz(S, HR, SR, q, k, theta, W, hinfo, (cudaStream_t)stream);
+    if (info) {
+        int tmp[2] = {hinfo[0], hinfo[1]};
+        cudaError_t e = cudaMemcpy(info, tmp, sizeof(tmp), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(HBSD_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return rc;
+}
+
+int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
+    if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
+    return update2(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
+}
+
+}  // extern "C"

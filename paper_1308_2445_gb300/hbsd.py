@@ -1,0 +1,271 @@
+"""Python binding of libhbsd (include/hbsd.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  If libhbsd.so is missing or cannot be loaded
+this module raises; there is no CPU fallback.  Device buffers may be torch CUDA tensors (their
+data_ptr() is passed) or raw integer device addresses.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhbsd.so")
+
+HBSD_OK = 0
+HBSD_NOT_CONVERGED = 1
+HBSD_BUSY = 2
+HBSD_ERR_ARG = -1
+HBSD_ERR_OOM = -2
+HBSD_ERR_NOT_SPD = -3
+HBSD_ERR_RR_RANK = -4
+HBSD_ERR_TIMEOUT = -5
+HBSD_ERR_CUDA = -6
+HBSD_ERR_UNSUPPORTED = -7
+
+PRECISION_FP64 = 0
+PRECISION_MIXED = 1
+PRECOND_HYBRID = 0
+PRECOND_GLOBAL = 1
+
+
+class hbsd_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.POINTER(C.c_int64)),
+                ("col_idx", C.POINTER(C.c_int32)), ("val", C.POINTER(C.c_double)), ("is_complex", C.c_int)]
+
+
+class hbsd_local_blocks(C.Structure):
+    _fields_ = [("dof_node", C.POINTER(C.c_int32)), ("dof_cluster", C.POINTER(C.c_int32)),
+                ("grid", C.c_int32 * 3)]
+
+
+class hbsd_options(C.Structure):
+    _fields_ = [("sigma_bar", C.c_double), ("sigma0", C.c_double), ("m0", C.c_int), ("tau1", C.c_double),
+                ("tau2", C.c_double), ("eta", C.c_double), ("max_minres", C.c_int), ("max_outer", C.c_int),
+                ("precision", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64)]
+
+
+class hbsd_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("iters_fp64", C.c_int), ("minres_steps", C.c_int64),
+                ("precond_cols", C.c_int64), ("local_cols", C.c_int64), ("rr_fallbacks", C.c_int),
+                ("res_max", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("nnz_L", C.c_int64), ("n_supernodes", C.c_int), ("gpu_launches", C.c_int),
+                ("t_matvec_ms", C.c_double), ("t_resid_ms", C.c_double), ("t_precond_ms", C.c_double),
+                ("t_local_ms", C.c_double), ("t_gram_ms", C.c_double), ("t_rr_ms", C.c_double),
+                ("t_update_ms", C.c_double), ("matvec_cols", C.c_int64), ("minres_spmm_cols", C.c_int64),
+                ("precond_calls", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_SIGS = {
+    "hbsd_options_default": (None, [C.POINTER(hbsd_options)]),
+    "hbsd_create": (C.c_int, [C.POINTER(hbsd_csr), C.POINTER(hbsd_csr), C.POINTER(hbsd_local_blocks),
+                              C.POINTER(hbsd_options), _P, C.POINTER(_P)]),
+    "hbsd_update_H": (C.c_int, [_P, _D]),
+    "hbsd_solve": (C.c_int, [_P, C.c_int, C.c_double, _D, C.c_int, _D, _D, C.POINTER(C.c_int),
+                             C.POINTER(hbsd_stats)]),
+    "hbsd_solve_device": (C.c_int, [_P, C.c_int, C.c_double, _P, C.c_int64, _P, _P, C.c_int64,
+                                    C.POINTER(C.c_int), C.POINTER(hbsd_stats)]),
+    "hbsd_destroy": (None, [_P]),
+    "hbsd_status_string": (C.c_char_p, [C.c_int]),
+    "hbsd_last_error": (C.c_char_p, []),
+    "hbsd_n": (C.c_int64, [_P]),
+    "hbsd_sigma0": (C.c_double, [_P]),
+    "hbsd_get_stats": (None, [_P, C.POINTER(hbsd_stats)]),
+    "hbsd_spmm_pair": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
+    "hbsd_spmm_shifted": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, C.c_int64]),
+    "hbsd_residual": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int, _P, C.c_int64, _P]),
+    "hbsd_precond_apply": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64]),
+    "hbsd_minres": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, C.c_double, C.c_int, _P, C.c_int64, _P]),
+    "hbsd_gram": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int, _P, _P, _P]),
+    "hbsd_rayleigh_ritz": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
+    "hbsd_update": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int, _P]),
+    "hbsd_probe_peak": (C.c_int, [C.c_int, _P, C.POINTER(C.c_double)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libhbsd.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing; build it with __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+class HbsdError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = lib().hbsd_last_error().decode(errors="replace")
+        st = lib().hbsd_status_string(code).decode()
+        super().__init__(f"{where}: {st} ({code}): {msg}")
+
+
+def check(code, where):
+    if code < 0:
+        raise HbsdError(code, where)
+    return code
+
+
+def ptr(x):
+    """Device address of a torch tensor (or an int)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def ld(t):
+    """Leading dimension (row stride, elements) of a 2-D row-major torch tensor."""
+    return int(t.stride(0))
+
+
+def options_default(**kw) -> hbsd_options:
+    o = hbsd_options()
+    lib().hbsd_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Session:
+    """A solver session (hbsd_create ... hbsd_destroy) over one (H, S) pair."""
+
+    def __init__(self, n, row_ptr, col_idx, h_val, s_val, dof_node, grid, sigma_bar, stream=None, **opts):
+        self._keep = []
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+        hv = np.ascontiguousarray(h_val, dtype=np.float64)
+        sv = np.ascontiguousarray(s_val, dtype=np.float64)
+        dn = np.ascontiguousarray(dof_node, dtype=np.int32)
+        self._keep += [rp, ci, hv, sv, dn]
+        self.n = int(n)
+        H = hbsd_csr(self.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                     ci.ctypes.data_as(C.POINTER(C.c_int32)), hv.ctypes.data_as(_D), 0)
+        S = hbsd_csr(self.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                     ci.ctypes.data_as(C.POINTER(C.c_int32)), sv.ctypes.data_as(_D), 0)
+        lb = hbsd_local_blocks(dn.ctypes.data_as(C.POINTER(C.c_int32)), None, (C.c_int32 * 3)(*grid))
+        self.opts = options_default(sigma_bar=float(sigma_bar), **opts)
+        h = C.c_void_p()
+        check(lib().hbsd_create(C.byref(H), C.byref(S), C.byref(lb), C.byref(self.opts),
+                                C.c_void_p(stream) if stream else None, C.byref(h)), "hbsd_create")
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, p, stream=None, **opts):
+        return cls(p.n, p.row_ptr, p.col_idx, p.h_val, p.s_val, p.dof_node, p.grid, p.eps_bar, stream=stream, **opts)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hbsd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def sigma0(self):
+        return lib().hbsd_sigma0(self.h)
+
+    def stats(self):
+        st = hbsd_stats()
+        lib().hbsd_get_stats(self.h, C.byref(st))
+        return st.as_dict()
+
+    def m0(self, nev):
+        return self.opts.m0 if self.opts.m0 >= 0 else max(3, -(-nev // 10))
+
+    def update_H(self, h_val):
+        hv = np.ascontiguousarray(h_val, dtype=np.float64)
+        check(lib().hbsd_update_H(self.h, hv.ctypes.data_as(_D)), "hbsd_update_H")
+
+    def solve(self, nev, tol, X0=None, warm=False, want_vectors=True):
+        """hbsd_solve with host arrays: returns (lambda, X, iters, status, stats)."""
+        w = nev + self.m0(nev)
+        x0p = None
+        if X0 is not None:
+            X0 = np.ascontiguousarray(X0, dtype=np.float64)
+            if X0.shape != (self.n, w):
+                raise ValueError(f"X0 must be {self.n} x {w}")
+            x0p = X0.ctypes.data_as(_D)
+        lam = np.empty(nev)
+        X = np.empty((self.n, nev)) if want_vectors else None
+        it = C.c_int(0)
+        st = hbsd_stats()
+        rc = check(lib().hbsd_solve(self.h, nev, tol, x0p, int(bool(warm)), lam.ctypes.data_as(_D),
+                                    X.ctypes.data_as(_D) if X is not None else None, C.byref(it), C.byref(st)),
+                   "hbsd_solve")
+        return lam, X, it.value, rc, st.as_dict()
+
+    def solve_device(self, nev, tol, X0, lam, X=None):
+        it = C.c_int(0)
+        st = hbsd_stats()
+        rc = check(lib().hbsd_solve_device(self.h, nev, tol, ptr(X0), ld(X0) if X0 is not None else 0, ptr(lam),
+                                           ptr(X), ld(X) if X is not None else 0, C.byref(it), C.byref(st)),
+                   "hbsd_solve_device")
+        return it.value, rc, st.as_dict()
+
+    # ---- step-level calls on torch CUDA tensors (row-major, float64) ----
+    def spmm_pair(self, X, HX, SX):
+        check(lib().hbsd_spmm_pair(self.h, ptr(X), ld(X), X.shape[1], ptr(HX), ld(HX), ptr(SX), ld(SX)),
+              "hbsd_spmm_pair")
+
+    def spmm_shifted(self, X, e, Y):
+        check(lib().hbsd_spmm_shifted(self.h, ptr(X), ld(X), X.shape[1], ptr(e), ptr(Y), ld(Y)), "hbsd_spmm_shifted")
+
+    def residual(self, PsiH, PsiS, E, m, R, res):
+        check(lib().hbsd_residual(self.h, ptr(PsiH), ld(PsiH), ptr(PsiS), ld(PsiS), ptr(E), m, ptr(R),
+                                  ld(R) if R is not None else 0, ptr(res)), "hbsd_residual")
+
+    def precond_apply(self, R, P):
+        check(lib().hbsd_precond_apply(self.h, ptr(R), ld(R), R.shape[1], ptr(P), ld(P)), "hbsd_precond_apply")
+
+    def minres(self, R, e, P, eta, max_minres, steps):
+        check(lib().hbsd_minres(self.h, ptr(R), ld(R), ptr(e), R.shape[1], eta, max_minres, ptr(P), ld(P),
+                                ptr(steps)), "hbsd_minres")
+
+
+def gram(Z, ZH, ZS, HR, SR, stream=0):
+    check(lib().hbsd_gram(ptr(Z), ld(Z), ptr(ZH), ld(ZH), ptr(ZS), ld(ZS), Z.shape[0], Z.shape[1], ptr(HR), ptr(SR),
+                          C.c_void_p(stream) if stream else None), "hbsd_gram")
+
+
+def rayleigh_ritz(HR, SR, k, theta, W, info, stream=0):
+    return check(lib().hbsd_rayleigh_ritz(ptr(HR), ptr(SR), HR.shape[0], k, ptr(theta), ptr(W), ptr(info),
+                                          C.c_void_p(stream) if stream else None), "hbsd_rayleigh_ritz")
+
+
+def update(Z, W, k, stream=0):
+    check(lib().hbsd_update(ptr(Z), ld(Z), Z.shape[0], W.shape[0], ptr(W), k, C.c_void_p(stream) if stream else None),
+          "hbsd_update")
+
+
+def probe_peak(which, stream=0):
+    """Measured FMA FLOP/s of the FP64 (which=0) or FP32 (which=1) SIMT pipes."""
+    out = C.c_double(0.0)
+    check(lib().hbsd_probe_peak(which, C.c_void_p(stream) if stream else None, C.byref(out)), "hbsd_probe_peak")
+    return out.value

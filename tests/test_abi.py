@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads without a GPU, and exports every symbol include/hbsd.h declares."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hbsd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hbsd_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1308_2445_gb300 import build_lib, hbsd
+    if not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    return hbsd.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("hbsd_create", "hbsd_solve", "hbsd_destroy", "hbsd_update_H", "hbsd_status_string",
+                 "hbsd_spmm_pair", "hbsd_precond_apply", "hbsd_minres", "hbsd_gram", "hbsd_rayleigh_ritz",
+                 "hbsd_update", "hbsd_residual"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(lib):
+    from paper_1308_2445_gb300 import hbsd
+    assert set(_declared()) <= set(hbsd.exported_symbols())
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_1308_2445_gb300 import hbsd
+    assert lib.hbsd_status_string(0) == b"ok"
+    assert lib.hbsd_status_string(-3).startswith(b"H - sigma_bar S")
+    o = hbsd.options_default()
+    assert (o.tau1, o.tau2, o.eta, o.max_minres, o.max_outer, o.m0) == (0.1, 0.1, 0.25, 20, 1000, -1)
+
+
+def test_create_rejects_bad_input_without_gpu(lib):
+    # argument validation happens before any CUDA call
+    from paper_1308_2445_gb300 import hbsd
+    import ctypes as C
+    h = C.c_void_p()
+    rc = lib.hbsd_create(None, None, None, None, None, C.byref(h))
+    assert rc == hbsd.HBSD_ERR_ARG
+    assert b"required" in lib.hbsd_last_error()
