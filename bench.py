@@ -232,8 +232,10 @@ def main():
         e2e_t.append(time.perf_counter() - ta)
         if rc2 == 0 and st2["res_max"] <= TOL:
             e2e_conv += nev
-    e2e = {"value": e2e_conv / sum(e2e_t) * ws, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d),
-           "d2h_bytes_per_step": int(d2h), "t_create_s": statistics.mean(e2e_t) - st2["t_solve_ms"] * 1e-3}
+    e2e = None
+    if e2e_t:
+        e2e = {"value": e2e_conv / sum(e2e_t) * ws, "unit": "eigenpairs/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "t_create_s": statistics.mean(e2e_t) - st2["t_solve_ms"] * 1e-3}
 
     # ---- roofline of the dominant step class (device time from the solve's CUDA events) ----
     peak64 = hbsd.probe_peak(0, stream.cuda_stream)

@@ -194,6 +194,22 @@ int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, i
 int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
               int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream);
 
+/* Allocation-free form of hbsd_gram, for callers that must not allocate device memory:
+ * a serving loop whose per-request path may not call cudaMalloc / cudaFree (both can
+ * synchronise the whole device and stall the requests already in flight), or a host whose
+ * memory pool owns all device memory up front.  It computes exactly what hbsd_gram computes,
+ * but its scratch is a file-scope device array of 2^21 doubles (16 MiB) that every device which
+ * loads the library holds until the process exits; the paper has no counterpart.  Sizes:
+ * q <= 1024 (2 q^2 scratch doubles per row chunk); a larger q returns HBSD_ERR_ARG.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current, so make that first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller; each call overwrites every scratch element it reads, so nothing
+ * carries over from the previous call.  Asynchronous on stream; no allocation, no free. */
+int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh,
+                      const double* ZS, int64_t ldzs, int64_t n, int q, double* HR, double* SR,
+                      void* stream);
+
 /* Step 9: lowest k eigenpairs of H_R W = S_R W Theta (q x q inputs row-major, ld q, device).
  * Diagonal scaling D = diag(S_R)^{-1/2}, Cholesky of D S_R D, symmetric eigensolve of
  * L^{-1} D H_R D L^{-T}; if the Cholesky breaks down or a pivot is below 1e-14 the

@@ -173,6 +173,8 @@ int gram2(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, i
           int q1, const double* H0, int64_t ldh0, const double* H1, int64_t ldh1,
           const double* S0, int64_t lds0, const double* S1, int64_t lds1, int64_t n, double* HR,
           double* SR, cudaStream_t st);
+int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
+                 int64_t n, int q, double* HR, double* SR, cudaStream_t st);
 int update2(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
             int64_t n, const double* W, int k, cudaStream_t st);
 int rayleigh_ritz(Session* s, const double* HR, const double* SR, int q, int k, double* theta,

@@ -7,6 +7,7 @@
 // (16-byte aligned) buffers.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "common.h"
 
@@ -240,6 +241,59 @@ int gram2(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, i
     const int64_t qq = (int64_t)q * q;
     k_gram_final<<<ceil_div(qq, 256), 256, 0, st>>>(s->ws.p, nch, q, HR, SR);
     HBSD_LAUNCHED(s);
+    return 0;
+}
+
+// ---- allocation-free Gram ---------------------------------------------------------------
+// Scratch for hbsd_gram_noalloc: a file-scope device array, so the call needs no cudaMalloc.
+// Every device that loads the library holds it (16 MiB) until the process exits.
+constexpr size_t GRAM_STATIC_DOUBLES = size_t(1) << 21;
+static __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
+
+// Device address of g_gram_static on the current device, looked up once per device.  In host
+// code the symbol names a host-side stand-in, not device memory, so kernels must be given this
+// address instead.
+static int gram_static_address(double** out) {
+    static std::mutex mu;
+    static double* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(HBSD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return fail(HBSD_ERR_ARG, "device ordinal beyond 63");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_gram_static);
+        if (e != cudaSuccess)
+            return fail(HBSD_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        addr[dev] = static_cast<double*>(p);
+    }
+    *out = addr[dev];
+    return 0;
+}
+
+int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
+                 int64_t n, int q, double* HR, double* SR, cudaStream_t st) {
+    if (q <= 0 || n <= 0) return fail(HBSD_ERR_ARG, "gram_noalloc: need n > 0 and q > 0");
+    const size_t per_chunk = (size_t)2 * q * q;
+    if (per_chunk > GRAM_STATIC_DOUBLES)
+        return fail(HBSD_ERR_ARG, "gram_noalloc: q = " + std::to_string(q) +
+                                      " exceeds the static scratch (2 q^2 <= 2^21 doubles, q <= 1024)");
+    double* scratch = nullptr;
+    HBSD_TRY(gram_static_address(&scratch));
+    const int tiles = ceil_div(q, 32);
+    int nch = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, ceil_div(1216, tiles * tiles)));
+    nch = (int)std::min<size_t>((size_t)nch, GRAM_STATIC_DOUBLES / per_chunk);
+    const int64_t rpc = (n + nch - 1) / nch;
+    nch = (int)((n + rpc - 1) / rpc);
+    // every partial element read by k_gram_final is written by k_gram_partial: nothing to clear
+    Seg2 A{Z, ldz, q, nullptr, 0}, AH{ZH, ldzh, q, nullptr, 0}, AS{ZS, ldzs, q, nullptr, 0};
+    dim3 grid(tiles * tiles, nch);
+    k_gram_partial<<<grid, 256, 0, st>>>(A, AH, AS, q, n, rpc, tiles, scratch);
+    HBSD_LAUNCHED(nullptr);
+    const int64_t qq = (int64_t)q * q;
+    k_gram_final<<<ceil_div(qq, 256), 256, 0, st>>>(scratch, nch, q, HR, SR);
+    HBSD_LAUNCHED(nullptr);
     return 0;
 }
 

@@ -540,6 +540,12 @@ int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, cons
                  (cudaStream_t)stream);
 }
 
+int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
+                      int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream) {
+    if (!Z || !ZH || !ZS || !HR || !SR) return fail(HBSD_ERR_ARG, "bad arguments");
+    return gram_noalloc(Z, ldz, ZH, ldzh, ZS, ldzs, n, q, HR, SR, (cudaStream_t)stream);
+}
+
 int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double* theta, double* W, int* info,
                        void* stream) {
     if (!HR || !SR || !theta || !W) return fail(HBSD_ERR_ARG, "bad arguments");
