@@ -172,6 +172,16 @@ int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k,
 int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e,
                       double* Y, int64_t ldy);
 
+/* FP32 forms used by the mixed precision (HBSD_PRECISION_MIXED) phase.  They act on the
+ * diagonally scaled pencil (D Hs D, D S D), D = diag(S)^{-1/2} (hbsd_dscale returns D, host,
+ * n doubles): hbsd_spmm_pair_f32 gives (D Hs D) X and (D S D) X; hbsd_precond_apply_f32 gives
+ * P = -(D (H - sigma_bar S) D)^{-1} R from the FP32 copy of the factor panels.  Blocks are
+ * row-major FP32 with ld a multiple of 4 and 16-byte aligned pointers. */
+int hbsd_spmm_pair_f32(hbsd_handle* h, const float* X, int64_t ldx, int k, float* HX, int64_t ldhx,
+                       float* SX, int64_t ldsx);
+int hbsd_precond_apply_f32(hbsd_handle* h, const float* R, int64_t ldr, int k, float* P, int64_t ldp);
+int hbsd_dscale(const hbsd_handle* h, double* d_host);
+
 /* Steps 4-5 (Eq. res1): for j < m, r_j = PsiH(:,j) - PsiS(:,j) E_j and
  * res[j] = ||r_j|| / ||PsiH(:,j)|| (device outputs: R n x m with ldr, res m doubles). */
 int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double* PsiS,
@@ -223,6 +233,15 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
 /* Steps 10-11: Z(:, 0:k) := Z(:, 0:q) W in place, row by row, for an n x q block Z and a
  * q x k matrix W (row-major, ld k, device), k <= q. */
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream);
+
+/* The start-block generator used when hbsd_solve gets X0 = NULL (host only, no GPU needed):
+ * count standard normals from SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based
+ * generator (draw t = mix(key + (t+1) * 0x9E3779B97F4A7C15), key = mix((seed ^ stream *
+ * 0x9E3779B97F4A7C15) + 0x9E3779B97F4A7C15)), uniforms from the top 53 bits, Box-Muller on
+ * consecutive pairs.  hbsd_solve uses stream 2 and the options' seed; entry (i, j) of the
+ * n x (nev + m0) block is draw i * (nev + m0) + j.  The paper has no counterpart (its start
+ * vectors come from the previous SCF step, remark 1). */
+int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out);
 
 /* ---- measurement ------------------------------------------------------------------
  * Sustained FMA throughput of the SIMT pipes on the current device (which = 0: FP64, 1: FP32),

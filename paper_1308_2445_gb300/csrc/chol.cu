@@ -279,217 +279,240 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, 
         b[i] = (float)a[i];
 }
 
-// ---- solve kernels (T = double or float), RHS chunks of 64 columns ------------------------------
-constexpr int RC = 64;  // RHS columns per CTA
+// ---- explicit panels G = [L11^{-1}; -L21 L11^{-1}] (factor time) ----------------------------------
+// Running the blocked forward substitution of a supernode on the right-hand side [I; 0] yields
+// L11^{-1} in the first ns rows and -L21 L11^{-1} below, so that the per-iteration solves become
+// products with G only:  forward  [y; u] = G f_top + [0; f_bot],   backward  x = G^T [y; x_struct].
+// G has the shape and column-major layout of the L panel (nf x ns, ld nf).
 
-// front vectors of a level: rows < ns <- R[perm[first + r]], rows >= ns <- 0
-template <class T>
-__global__ void k_fv_init(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                          const int32_t* __restrict__ perm, const T* __restrict__ R, int64_t ldr, int k,
-                          T* __restrict__ fv, int64_t ldf) {
+__global__ void k_g_init(const SnDev* __restrict__ sn, const int* __restrict__ ids, double* __restrict__ G) {
     const SnDev s = sn[ids[blockIdx.y]];
     const int nf = s.ns + s.nu;
-    const int64_t total = (int64_t)nf * k;
+    const int64_t total = (int64_t)nf * s.ns;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / k), j = (int)(idx % k);
-        T v = T(0);
-        if (r < s.ns) v = R[(int64_t)perm[s.first + r] * ldr + j];
-        fv[(s.fv_off + r) * ldf + j] = v;
+        const int r = (int)(idx % nf), c = (int)(idx / nf);
+        G[s.L_off + idx] = (r == c) ? 1.0 : 0.0;
     }
 }
 
-// parent front vector += child's below-diagonal part
-template <class T>
-__global__ void k_fv_extend_add(const SnDev* __restrict__ sn, const int* __restrict__ jobs, int njobs,
-                                const int32_t* __restrict__ ea, int k, T* __restrict__ fv, int64_t ldf) {
-    const int job = blockIdx.y;
-    if (job >= njobs) return;
-    const SnDev p = sn[jobs[2 * job]];
-    const SnDev c = sn[jobs[2 * job + 1]];
-    const int64_t total = (int64_t)c.nu * k;
-    const int32_t* map = ea + c.ea_off;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / k), j = (int)(idx % k);
-        fv[(p.fv_off + map[r]) * ldf + j] += fv[(c.fv_off + c.ns + r) * ldf + j];
-    }
-}
-
-// y_blk := Dinv_blk (or Dinv_blk^T) y_blk, block [k0, k0+kb) of every front of the level
-template <class T, bool TRANS>
-__global__ void __launch_bounds__(256) k_solve_diag(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                                                    int k0, const T* __restrict__ Dinv, int k,
-                                                    T* __restrict__ fv, int64_t ldf) {
+// block row [k0, k0+kb) of G, columns [0, k0+kb):  G_blk := Dinv_blk G_blk   (column chunks of 64)
+__global__ void __launch_bounds__(256) k_g_diag(const SnDev* __restrict__ sn, const int* __restrict__ ids, int k0,
+                                                const double* __restrict__ Dinv, double* __restrict__ G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto Y = reinterpret_cast<T(*)[RC + 1]>(smem_raw);
-    auto D = reinterpret_cast<T(*)[NB + 1]>(smem_raw + sizeof(T) * NB * (RC + 1));
+    auto Y = reinterpret_cast<double(*)[65]>(smem_raw);
+    auto D = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * NB * 65);
     const SnDev s = sn[ids[blockIdx.y]];
     if (k0 >= s.ns) return;
     const int kb = min(NB, s.ns - k0);
-    const int j0 = blockIdx.x * RC;
-    const int kc = min(RC, k - j0);
-    const T* Db = Dinv + s.Dinv_off + (int64_t)(k0 / NB) * NB * NB;
-    T* yb = fv + (s.fv_off + k0) * ldf + j0;
-    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
-        const int r = t / RC, j = t % RC;
-        Y[r][j] = (r < kb && j < kc) ? yb[(int64_t)r * ldf + j] : T(0);
+    const int ncols = k0 + kb;
+    const int c0 = blockIdx.x * 64;
+    if (c0 >= ncols) return;
+    const int cc = min(64, ncols - c0);
+    const int nf = s.ns + s.nu;
+    double* Gc = G + s.L_off;
+    const double* Db = Dinv + s.Dinv_off + (int64_t)(k0 / NB) * NB * NB;
+    for (int t = threadIdx.x; t < NB * 64; t += blockDim.x) {
+        const int r = t % NB, j = t / NB;
+        Y[r][j] = (r < kb && j < cc) ? Gc[(int64_t)(c0 + j) * nf + k0 + r] : 0.0;
     }
     for (int t = threadIdx.x; t < NB * NB; t += blockDim.x) D[t % NB][t / NB] = Db[t];
     __syncthreads();
-    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
-        const int r = t / RC, j = t % RC;
-        if (r >= kb || j >= kc) continue;
-        T acc = T(0);
-        if (!TRANS) {
-            for (int u = 0; u <= r; ++u) acc = fma(D[r][u], Y[u][j], acc);
-        } else {
-            for (int u = r; u < kb; ++u) acc = fma(D[u][r], Y[u][j], acc);
-        }
-        yb[(int64_t)r * ldf + j] = acc;
+    for (int t = threadIdx.x; t < NB * 64; t += blockDim.x) {
+        const int r = t % NB, j = t / NB;
+        if (r >= kb || j >= cc) continue;
+        double acc = 0.0;
+        for (int u = 0; u <= r; ++u) acc = fma(D[r][u], Y[u][j], acc);
+        Gc[(int64_t)(c0 + j) * nf + k0 + r] = acc;
     }
 }
 
-// forward: rows >= k0+kb of each front: fv[row] -= L[row, k0:k0+kb] y_blk   (row tiles of 64)
-template <class T>
-__global__ void __launch_bounds__(256) k_solve_fwd_update(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                                                          int k0, const T* __restrict__ L, int k,
-                                                          T* __restrict__ fv, int64_t ldf) {
+// rows >= k0+kb, columns [0, k0+kb):  G -= L[:, k0:k0+kb] G_blk   (64 x 64 tiles)
+__global__ void __launch_bounds__(256) k_g_update(const SnDev* __restrict__ sn, const int* __restrict__ ids, int k0,
+                                                  const double* __restrict__ L, double* __restrict__ G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto Lt = reinterpret_cast<T(*)[NB + 1]>(smem_raw);
-    auto Y = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * 64 * (NB + 1));
-    const SnDev s = sn[ids[blockIdx.y]];
+    auto Lt = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
+    auto Yt = reinterpret_cast<double(*)[65]>(smem_raw + sizeof(double) * 64 * (NB + 1));
+    const SnDev s = sn[ids[blockIdx.z]];
     if (k0 >= s.ns) return;
     const int kb = min(NB, s.ns - k0);
     const int nf = s.ns + s.nu;
     const int r0 = k0 + kb + blockIdx.x * 64;
-    if (r0 >= nf) return;
-    const int rows = min(64, nf - r0);
-    const int j0 = blockIdx.z * RC;
-    const int kc = min(RC, k - j0);
-    const T* Lc = L + s.L_off + (int64_t)k0 * nf;
+    const int c0 = blockIdx.y * 64;
+    if (r0 >= nf || c0 >= k0 + kb) return;
+    const int rows = min(64, nf - r0), cols = min(64, k0 + kb - c0);
+    const double* Lc = L + s.L_off;
+    double* Gc = G + s.L_off;
     for (int t = threadIdx.x; t < 64 * NB; t += blockDim.x) {
         const int i = t % 64, c = t / 64;
-        Lt[i][c] = (i < rows && c < kb) ? Lc[(int64_t)c * nf + r0 + i] : T(0);
+        Lt[i][c] = (i < rows && c < kb) ? Lc[(int64_t)(k0 + c) * nf + r0 + i] : 0.0;
     }
-    const T* yb = fv + (s.fv_off + k0) * ldf + j0;
-    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
-        const int r = t / RC, j = t % RC;
-        Y[r][j] = (r < kb && j < kc) ? yb[(int64_t)r * ldf + j] : T(0);
-    }
-    __syncthreads();
-    T* ob = fv + (s.fv_off + r0) * ldf + j0;
-    for (int t = threadIdx.x; t < 64 * RC; t += blockDim.x) {
-        const int i = t / RC, j = t % RC;
-        if (i >= rows || j >= kc) continue;
-        T acc = T(0);
-        for (int c = 0; c < kb; ++c) acc = fma(Lt[i][c], Y[c][j], acc);
-        ob[(int64_t)i * ldf + j] -= acc;
-    }
-}
-
-// backward, step a: fv[c] -= sum_r L[ns + r][c] x[struct[r]] for columns c of the supernode
-template <class T>
-__global__ void __launch_bounds__(256) k_solve_bwd_gather(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                                                          const T* __restrict__ L, const int64_t* __restrict__ srows,
-                                                          const T* __restrict__ xp, int64_t ldx, int k,
-                                                          T* __restrict__ fv, int64_t ldf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto Lt = reinterpret_cast<T(*)[65]>(smem_raw);
-    auto Xs = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * 64 * 65);
-    const SnDev s = sn[ids[blockIdx.y]];
-    const int c0 = blockIdx.x * 64;
-    if (c0 >= s.ns || s.nu == 0) return;
-    const int cols = min(64, s.ns - c0);
-    const int nf = s.ns + s.nu;
-    const int j0 = blockIdx.z * RC;
-    const int kc = min(RC, k - j0);
-    const int tc = threadIdx.x % 64, tg = threadIdx.x / 64;  // column c0+tc, RHS j = tg + 4*v
-    T acc[RC / 4];
-#pragma unroll
-    for (int v = 0; v < RC / 4; ++v) acc[v] = T(0);
-    const T* Lc = L + s.L_off;
-    for (int r0 = 0; r0 < s.nu; r0 += 64) {
-        const int rr = min(64, s.nu - r0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < 64 * 64; t += blockDim.x) {
-            const int r = t % 64, c = t / 64;
-            Lt[r][c] = (r < rr && c < cols) ? Lc[(int64_t)(c0 + c) * nf + s.ns + r0 + r] : T(0);
-        }
-        for (int t = threadIdx.x; t < 64 * RC; t += blockDim.x) {
-            const int r = t / RC, j = t % RC;
-            Xs[r][j] = (r < rr && j < kc) ? xp[srows[s.struct_off + r0 + r] * ldx + j0 + j] : T(0);
-        }
-        __syncthreads();
-        for (int r = 0; r < rr; ++r) {
-            const T l = Lt[r][tc];
-#pragma unroll
-            for (int v = 0; v < RC / 4; ++v) acc[v] = fma(l, Xs[r][tg + 4 * v], acc[v]);
-        }
-    }
-    if (tc < cols) {
-        T* ob = fv + (s.fv_off + c0 + tc) * ldf + j0;
-#pragma unroll
-        for (int v = 0; v < RC / 4; ++v) {
-            const int j = tg + 4 * v;
-            if (j < kc) ob[j] -= acc[v];
-        }
-    }
-}
-
-// backward, step b: for columns c < k0: fv[c] -= sum_{t < kb} L[k0 + t][c] x_blk[t]
-template <class T>
-__global__ void __launch_bounds__(256) k_solve_bwd_update(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                                                          int k0, const T* __restrict__ L, int k,
-                                                          T* __restrict__ fv, int64_t ldf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto Lt = reinterpret_cast<T(*)[65]>(smem_raw);
-    auto Xs = reinterpret_cast<T(*)[RC + 1]>(smem_raw + sizeof(T) * NB * 65);
-    const SnDev s = sn[ids[blockIdx.y]];
-    if (k0 >= s.ns) return;
-    const int c0 = blockIdx.x * 64;
-    if (c0 >= k0) return;
-    const int cols = min(64, k0 - c0);
-    const int kb = min(NB, s.ns - k0);
-    const int nf = s.ns + s.nu;
-    const int j0 = blockIdx.z * RC;
-    const int kc = min(RC, k - j0);
-    const T* Lc = L + s.L_off;
     for (int t = threadIdx.x; t < NB * 64; t += blockDim.x) {
-        const int r = t % NB, c = t / NB;
-        Lt[r][c] = (r < kb && c < cols) ? Lc[(int64_t)(c0 + c) * nf + k0 + r] : T(0);
-    }
-    const T* xb = fv + (s.fv_off + k0) * ldf + j0;
-    for (int t = threadIdx.x; t < NB * RC; t += blockDim.x) {
-        const int r = t / RC, j = t % RC;
-        Xs[r][j] = (r < kb && j < kc) ? xb[(int64_t)r * ldf + j] : T(0);
+        const int r = t % NB, j = t / NB;
+        Yt[r][j] = (r < kb && j < cols) ? Gc[(int64_t)(c0 + j) * nf + k0 + r] : 0.0;
     }
     __syncthreads();
-    const int tc = threadIdx.x % 64, tg = threadIdx.x / 64;
-    if (tc >= cols) return;
-    T acc[RC / 4];
+    const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;
+    double acc[4][4] = {};
+    for (int c = 0; c < kb; ++c) {
+        double a[4], b[4];
 #pragma unroll
-    for (int v = 0; v < RC / 4; ++v) acc[v] = T(0);
-    for (int r = 0; r < kb; ++r) {
-        const T l = Lt[r][tc];
+        for (int u = 0; u < 4; ++u) { a[u] = Lt[tr + 16 * u][c]; b[u] = Yt[c][tc + 16 * u]; }
 #pragma unroll
-        for (int v = 0; v < RC / 4; ++v) acc[v] = fma(l, Xs[r][tg + 4 * v], acc[v]);
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
     }
-    T* ob = fv + (s.fv_off + c0 + tc) * ldf + j0;
 #pragma unroll
-    for (int v = 0; v < RC / 4; ++v) {
-        const int j = tg + 4 * v;
-        if (j < kc) ob[j] -= acc[v];
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = tr + 16 * u, j = tc + 16 * v;
+            if (i < rows && j < cols) Gc[(int64_t)(c0 + j) * nf + r0 + i] -= acc[u][v];
+        }
+}
+
+// ---- per-iteration solve kernels (T = double or float) ---------------------------------------
+// Forward: front vector f (nf rows) <- [R(perm) rows of the supernode; 0] + the children's
+// bottom parts (each front row has at most one source row per child; src = -1 for none).
+template <class T>
+__global__ void k_fwd_assemble(const SnDev* __restrict__ sn, const int* __restrict__ ids,
+                               const int32_t* __restrict__ perm, const int2* __restrict__ src,
+                               const T* __restrict__ R, int64_t ldr, int p, T* __restrict__ fv, int64_t ldf) {
+    const SnDev s = sn[ids[blockIdx.y]];
+    const int nf = s.ns + s.nu;
+    const int64_t total = (int64_t)nf * p;
+    const SnDev* c0 = s.child0 >= 0 ? sn + s.child0 : nullptr;
+    const SnDev* c1 = s.child1 >= 0 ? sn + s.child1 : nullptr;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / p), j = (int)(idx % p);
+        T v = (r < s.ns) ? R[(int64_t)perm[s.first + r] * ldr + j] : T(0);
+        const int2 sr = src[s.fv_off + r];
+        if (sr.x >= 0) v += fv[(c0->fv_off + c0->ns + sr.x) * ldf + j];
+        if (sr.y >= 0) v += fv[(c1->fv_off + c1->ns + sr.y) * ldf + j];
+        fv[(s.fv_off + r) * ldf + j] = v;
     }
 }
 
-// x (permuted) <- front-vector top rows of each supernode of the level
-template <class T>
-__global__ void k_fv_store_x(const SnDev* __restrict__ sn, const int* __restrict__ ids, int k,
-                             const T* __restrict__ fv, int64_t ldf, T* __restrict__ xp, int64_t ldx) {
-    const SnDev s = sn[ids[blockIdx.y]];
-    const int64_t total = (int64_t)s.ns * k;
+// One tile of a split-K product with G.  FWD: out rows [t0, t0+64) of nf, reduction over G
+// columns [k0, k1) against f_top.  BWD: out columns [t0, t0+64) of ns, reduction over G rows
+// [k0, k1) against z = [y; x(struct)].  Unsplit items write the result; split items write a
+// partial that k_*_reduce sums in split order (deterministic).
+struct SolveItem {
+    int sn, t0, k0, k1, split, nsplit;
+    int64_t part_row;   // first partial row of this supernode's split block (level-relative)
+};
+
+template <class T, int RC, bool BWD>
+__global__ void __launch_bounds__(256) k_solve_gemm(const SnDev* __restrict__ sn, const SolveItem* __restrict__ items,
+                                                    const T* __restrict__ G, const int64_t* __restrict__ srows,
+                                                    int p, T* __restrict__ fv, int64_t ldf,
+                                                    T* __restrict__ Y, T* __restrict__ X, int64_t ldx,
+                                                    T* __restrict__ part) {
+    __shared__ T Gt[32][65];
+    __shared__ T Zt[32][RC + 1];
+    const SolveItem it = items[blockIdx.x];
+    const SnDev s = sn[it.sn];
+    const int nf = s.ns + s.nu;
+    const int j0 = blockIdx.y * RC;
+    const int kc = min(RC, p - j0);
+    const int nout = BWD ? s.ns : nf;
+    constexpr int CPT = RC / 16;         // columns per thread
+    const int tr = threadIdx.x % 16, tc = threadIdx.x / 16;
+    T acc[4][CPT];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) acc[u][v] = T(0);
+    const T* Gs = G + s.L_off;
+    for (int kk = it.k0; kk < it.k1; kk += 32) {
+        if (!BWD) {
+            for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
+                const int i = t % 64, q = t / 64;   // coalesced over output rows
+                const int row = it.t0 + i, k = kk + q;
+                Gt[q][i] = (row < nf && k < it.k1) ? Gs[(int64_t)k * nf + row] : T(0);
+            }
+            for (int t = threadIdx.x; t < 32 * RC; t += blockDim.x) {
+                const int q = t / RC, j = t % RC;
+                const int k = kk + q;
+                Zt[q][j] = (k < it.k1 && j < kc) ? fv[(s.fv_off + k) * ldf + j0 + j] : T(0);
+            }
+        } else {
+            for (int t = threadIdx.x; t < 32 * 64; t += blockDim.x) {
+                const int q = t % 32, i = t / 32;   // coalesced over G rows
+                const int col = it.t0 + i, r = kk + q;
+                Gt[q][i] = (col < s.ns && r < it.k1) ? Gs[(int64_t)col * nf + r] : T(0);
+            }
+            for (int t = threadIdx.x; t < 32 * RC; t += blockDim.x) {
+                const int q = t / RC, j = t % RC;
+                const int r = kk + q;
+                T z = T(0);
+                if (r < it.k1 && j < kc)
+                    z = (r < s.ns) ? Y[(s.first + r) * ldx + j0 + j] : X[srows[s.struct_off + r - s.ns] * ldx + j0 + j];
+                Zt[q][j] = z;
+            }
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            T a[4], b[CPT];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = Gt[q][tr + 16 * u];
+#pragma unroll
+            for (int v = 0; v < CPT; ++v) b[v] = Zt[q][tc + 16 * v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < CPT; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int o = it.t0 + tr + 16 * u;
+        if (o >= nout) continue;
+#pragma unroll
+        for (int v = 0; v < CPT; ++v) {
+            const int j = tc + 16 * v;
+            if (j >= kc) continue;
+            if (it.nsplit > 1) {
+                part[(it.part_row + (int64_t)it.split * nout + o) * ldf + j0 + j] = acc[u][v];
+            } else if (BWD) {
+                X[(s.first + o) * ldx + j0 + j] = acc[u][v];
+            } else if (o < s.ns) {
+                Y[(s.first + o) * ldx + j0 + j] = acc[u][v];
+            } else {
+                fv[(s.fv_off + o) * ldf + j0 + j] += acc[u][v];
+            }
+        }
+    }
+}
+
+// Sum the split partials of the supernodes listed in items (one item per (supernode, tile)),
+// in split order, skipping the splits whose tiles were empty (see solve_items()).
+template <class T, bool BWD>
+__global__ void k_solve_reduce(const SnDev* __restrict__ sn, const SolveItem* __restrict__ items, int p,
+                               const T* __restrict__ part, int64_t ldf, T* __restrict__ fv, T* __restrict__ Y,
+                               T* __restrict__ X, int64_t ldx, int KS) {
+    const SolveItem it = items[blockIdx.y];
+    const SnDev s = sn[it.sn];
+    const int nf = s.ns + s.nu;
+    const int nout = BWD ? s.ns : nf;
+    const int64_t total = (int64_t)64 * p;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(idx / k), j = (int)(idx % k);
-        xp[(s.first + r) * ldx + j] = fv[(s.fv_off + r) * ldf + j];
+        const int o = it.t0 + (int)(idx / p), j = (int)(idx % p);
+        if (o >= nout) continue;
+        T acc = T(0);
+        for (int sp = 0; sp < it.nsplit; ++sp) {
+            const int k0 = sp * KS;
+            bool empty;
+            if (BWD) empty = (k0 + KS <= it.t0);                               // rows all above the tile
+            else empty = (it.t0 + 64 <= s.ns) && (k0 > it.t0 + 63);            // columns all right of the tile
+            if (empty) continue;
+            acc += part[(it.part_row + (int64_t)sp * nout + o) * ldf + j];
+        }
+        if (BWD) X[(s.first + o) * ldx + j] = acc;
+        else if (o < s.ns) Y[(s.first + o) * ldx + j] = acc;
+        else fv[(s.fv_off + o) * ldf + j] += acc;
     }
 }
 
@@ -505,6 +528,10 @@ __global__ void k_unpermute_neg(const int32_t* __restrict__ perm, const T* __res
     }
 }
 
+inline int grid_for(int64_t work, int threads = 256) {
+    return (int)std::min<int64_t>(std::max<int64_t>(1, (work + threads - 1) / threads), 1 << 16);
+}
+
 // two 64 x 65 tiles of T
 template <class T>
 constexpr size_t tile2_bytes() { return 2 * sizeof(T) * 64 * 65; }
@@ -516,8 +543,32 @@ int allow_smem(K kernel, size_t bytes) {
     return 0;
 }
 
-inline int grid_for(int64_t work, int threads = 256) {
-    return (int)std::min<int64_t>(std::max<int64_t>(1, (work + threads - 1) / threads), 1 << 16);
+// Split-K chunk of the solve products (columns of G forward, rows of G backward)
+constexpr int SOLVE_KS = 128;
+
+// Work items of one sweep of one level (see k_solve_gemm); partial rows are level-relative.
+void solve_items(const Factor& f, int h, bool bwd, std::vector<SolveItem>& items, std::vector<SolveItem>& red,
+                 int64_t* part_rows) {
+    int64_t pr = 0;
+    for (int q : f.levels[h]) {
+        const Supernode& sn = f.sn[q];
+        const int nf = sn.ns + sn.nu;
+        const int nout = bwd ? sn.ns : nf;
+        const int klen = bwd ? nf : sn.ns;
+        const int nsplit = std::max(1, ceil_div(klen, SOLVE_KS));
+        const int64_t base = pr;
+        if (nsplit > 1) pr += (int64_t)nsplit * nout;
+        for (int t0 = 0; t0 < nout; t0 += 64) {
+            for (int sp = 0; sp < nsplit; ++sp) {
+                const int k0 = sp * SOLVE_KS, k1 = std::min(klen, k0 + SOLVE_KS);
+                const bool empty = bwd ? (k1 <= t0) : (t0 + 64 <= sn.ns && k0 > t0 + 63);
+                if (empty) continue;
+                items.push_back(SolveItem{q, t0, k0, k1, sp, nsplit, base});
+            }
+            if (nsplit > 1) red.push_back(SolveItem{q, t0, 0, klen, 0, nsplit, base});
+        }
+    }
+    *part_rows = pr;
 }
 
 // Largest row count below the diagonal block [k0, k0+kb) over the fronts of a level, and the
@@ -837,6 +888,75 @@ int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const
     }
     HBSD_CUDA(cudaStreamSynchronize(st));
     fronts.release();
+    // explicit panels G = [L11^{-1}; -L21 L11^{-1}]: forward substitution on [I; 0], level-batched
+    HBSD_TRY(f.G.alloc(std::max<int64_t>(1, L_tot)));
+    HBSD_TRY(allow_smem(k_g_diag, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_g_update, tile2_bytes<double>()));
+    for (int h = 0; h <= H; ++h) {
+        const int* lid = LL.ids.p + LL.offs[h];
+        const int cnt = LL.counts[h];
+        int64_t maxp = 1;
+        for (int q : f.levels[h]) maxp = std::max<int64_t>(maxp, ((int64_t)f.sn[q].ns + f.sn[q].nu) * f.sn[q].ns);
+        dim3 gi(std::min(grid_for(maxp), 1024), cnt);
+        k_g_init<<<gi, 256, 0, st>>>(dsn, lid, f.G.p);
+        HBSD_LAUNCHED(s);
+        for (int k0 = 0; k0 < LL.max_ns[h]; k0 += NB) {
+            const int ncols = k0 + std::min(NB, LL.max_ns[h] - k0);
+            dim3 gd(ceil_div(ncols, 64), cnt);
+            k_g_diag<<<gd, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, f.Dinv.p, f.G.p);
+            HBSD_LAUNCHED(s);
+            int rem = 0, pairs = 0;
+            level_extent(f, h, k0, &rem, &pairs);
+            if (rem <= 0) continue;
+            dim3 gu(ceil_div(rem, 64), ceil_div(ncols, 64), cnt);
+            k_g_update<<<gu, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, f.L.p, f.G.p);
+            HBSD_LAUNCHED(s);
+        }
+    }
+    // extend-add sources of every front row (pull form of the solve's extend-add)
+    {
+        std::vector<int2> src(std::max<int64_t>(1, f.fv_total), make_int2(-1, -1));
+        for (int q = 0; q < nsn; ++q) {
+            const Supernode& c = f.sn[q];
+            if (c.parent < 0) continue;
+            const Supernode& pa = f.sn[c.parent];
+            const int slot = (pa.child[0] == q) ? 0 : 1;
+            for (int r = 0; r < c.nu; ++r) {
+                int2& e = src[pa.fv_off + ea[c.ea_off + r]];
+                if (slot == 0) e.x = r; else e.y = r;
+            }
+        }
+        HBSD_TRY(f.src.alloc(src.size()));
+        HBSD_CUDA(cudaMemcpy(f.src.p, src.data(), src.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+    // solve work lists
+    {
+        f.sweep.assign(2 * (H + 1), {});
+        std::vector<SolveItem> all_items, all_red;
+        f.part_rows = 0;
+        for (int h = 0; h <= H; ++h)
+            for (int b = 0; b < 2; ++b) {
+                std::vector<SolveItem> items, red;
+                int64_t pr = 0;
+                solve_items(f, h, b == 1, items, red, &pr);
+                Factor::Sweep& sw = f.sweep[2 * h + b];
+                sw.item_off = (int)all_items.size();
+                sw.n_items = (int)items.size();
+                sw.red_off = (int)all_red.size();
+                sw.n_red = (int)red.size();
+                all_items.insert(all_items.end(), items.begin(), items.end());
+                all_red.insert(all_red.end(), red.begin(), red.end());
+                f.part_rows = std::max(f.part_rows, pr);
+            }
+        const size_t isz = sizeof(SolveItem);
+        HBSD_TRY(f.items.alloc((std::max<size_t>(1, all_items.size()) * isz + 7) / 8));
+        HBSD_TRY(f.red_items.alloc((std::max<size_t>(1, all_red.size()) * isz + 7) / 8));
+        if (!all_items.empty())
+            HBSD_CUDA(cudaMemcpy(f.items.p, all_items.data(), all_items.size() * isz, cudaMemcpyHostToDevice));
+        if (!all_red.empty())
+            HBSD_CUDA(cudaMemcpy(f.red_items.p, all_red.data(), all_red.size() * isz, cudaMemcpyHostToDevice));
+    }
+    HBSD_CUDA(cudaStreamSynchronize(st));
     auto t1 = std::chrono::steady_clock::now();
     s->stats.t_factor_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     s->stats.nnz_L = f.nnz_L;
@@ -844,107 +964,99 @@ int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const
     return 0;
 }
 
-int factor_make_fp32(Factor& f, cudaStream_t st) {
-    if (f.L32.p) return 0;
-    HBSD_TRY(f.L32.alloc(f.L.n));
-    HBSD_TRY(f.Dinv32.alloc(f.Dinv.n));
-    k_to_float<<<grid_for(f.L.n), 256, 0, st>>>(f.L.p, f.L32.p, f.L.n);
-    k_to_float<<<grid_for(f.Dinv.n), 256, 0, st>>>(f.Dinv.p, f.Dinv32.p, f.Dinv.n);
+// FP32 panels of the diagonally scaled matrix D A D (D in the permuted order): with
+// L^ = D L, the panel G^ = [L11^{-1} D_s^{-1}; D_u M21 D_s^{-1}], i.e. column c divided by the
+// scale of the supernode's c-th dof and rows below the diagonal block multiplied by theirs.
+__global__ void k_g_to_float_scaled(const SnDev* __restrict__ sn, const double* __restrict__ G,
+                                    const int32_t* __restrict__ perm, const int64_t* __restrict__ srows,
+                                    const double* __restrict__ d, float* __restrict__ G32) {
+    const SnDev s = sn[blockIdx.y];
+    const int nf = s.ns + s.nu;
+    const int64_t total = (int64_t)nf * s.ns;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx % nf), c = (int)(idx / nf);
+        const double rho = (r < s.ns) ? 1.0 : d[perm[srows[s.struct_off + r - s.ns]]];
+        G32[s.L_off + idx] = (float)(rho * G[s.L_off + idx] / d[perm[s.first + c]]);
+    }
+}
+
+int factor_make_fp32(Factor& f, const double* dscale, cudaStream_t st) {
+    if (f.G32.p) return 0;
+    HBSD_TRY(f.G32.alloc(f.G.n));
+    const int nsn = (int)f.sn.size();
+    int64_t maxp = 1;
+    for (int q = 0; q < nsn; ++q) maxp = std::max<int64_t>(maxp, ((int64_t)f.sn[q].ns + f.sn[q].nu) * f.sn[q].ns);
+    dim3 g(std::min(grid_for(maxp), 1024), nsn);
+    k_g_to_float_scaled<<<g, 256, 0, st>>>(reinterpret_cast<const SnDev*>(f.d_sn.p), f.G.p, f.perm.p, f.d_struct.p,
+                                           dscale, f.G32.p);
     HBSD_CUDA(cudaPeekAtLastError());
     return 0;
 }
 
 template <class T> struct FactorData;
 template <> struct FactorData<double> {
-    static const double* L(Factor& f) { return f.L.p; }
-    static const double* D(Factor& f) { return f.Dinv.p; }
-    static DBuf<double>& fv(Factor& f) { return f.fv; }
-    static DBuf<double>& xp(Factor& f) { return f.xp; }
+    static const double* G(Factor& f) { return f.G.p; }
+    static DBuf<double>& ws(Factor& f) { return f.sws; }
 };
 template <> struct FactorData<float> {
-    static const float* L(Factor& f) { return f.L32.p; }
-    static const float* D(Factor& f) { return f.Dinv32.p; }
-    static DBuf<float>& fv(Factor& f) { return f.fv32; }
-    static DBuf<float>& xp(Factor& f) { return f.xp32; }
+    static const float* G(Factor& f) { return f.G32.p; }
+    static DBuf<float>& ws(Factor& f) { return f.sws32; }
 };
 
+// P = -(L L^T)^{-1} R for a k-column block: forward sweep (levels bottom-up), backward sweep
+// (levels top-down), each level one split-K product with G plus, for split supernodes, one
+// deterministic reduction.
 template <class T>
 int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, int64_t ldp, cudaStream_t st) {
     if (k <= 0) return 0;
-    const T* L = FactorData<T>::L(f);
-    const T* D = FactorData<T>::D(f);
-    if (!L || !D) return fail(HBSD_ERR_ARG, "factor_solve: factor not available in this precision");
-    const int64_t ldf = round_up(k, 4);
-    HBSD_TRY(FactorData<T>::fv(f).alloc((size_t)f.fv_total * ldf));
-    HBSD_TRY(FactorData<T>::xp(f).alloc((size_t)f.n * ldf));
-    T* fv = FactorData<T>::fv(f).p;
-    T* xp = FactorData<T>::xp(f).p;
+    const T* G = FactorData<T>::G(f);
+    if (!G) return fail(HBSD_ERR_ARG, "factor_solve: factor not available in this precision");
+    const int64_t ld = round_up(k, 4);
+    // workspace: front vectors | y | x | split partials
+    const int64_t rows = f.fv_total + 2 * f.n + f.part_rows;
+    HBSD_TRY(FactorData<T>::ws(f).alloc((size_t)rows * ld));
+    T* fv = FactorData<T>::ws(f).p;
+    T* Y = fv + f.fv_total * ld;
+    T* X = Y + f.n * ld;
+    T* part = X + f.n * ld;
     LevelLists& LL = f.LL;
     const SnDev* dsn = reinterpret_cast<const SnDev*>(f.d_sn.p);
+    const SolveItem* items = reinterpret_cast<const SolveItem*>(f.items.p);
+    const SolveItem* red = reinterpret_cast<const SolveItem*>(f.red_items.p);
     const int H = (int)f.levels.size() - 1;
-    {
-        static bool attr_set = false;  // per template instantiation
-        if (!attr_set) {
-            HBSD_TRY(allow_smem(k_solve_diag<T, false>, tile2_bytes<T>()));
-            HBSD_TRY(allow_smem(k_solve_diag<T, true>, tile2_bytes<T>()));
-            HBSD_TRY(allow_smem(k_solve_fwd_update<T>, tile2_bytes<T>()));
-            HBSD_TRY(allow_smem(k_solve_bwd_gather<T>, tile2_bytes<T>()));
-            HBSD_TRY(allow_smem(k_solve_bwd_update<T>, tile2_bytes<T>()));
-            attr_set = true;
+    const bool narrow = k <= 16;
+    const int rc = narrow ? 16 : 64;
+    const int rchunks = ceil_div(k, rc);
+    auto gemm = [&](int h, bool bwd) -> int {
+        const Factor::Sweep& sw = f.sweep[2 * h + (bwd ? 1 : 0)];
+        if (sw.n_items > 0) {
+            dim3 g(sw.n_items, rchunks);
+            const SolveItem* it = items + sw.item_off;
+            if (bwd) {
+                if (narrow) k_solve_gemm<T, 16, true><<<g, 256, 0, st>>>(dsn, it, G, f.d_struct.p, k, fv, ld, Y, X, ld, part);
+                else k_solve_gemm<T, 64, true><<<g, 256, 0, st>>>(dsn, it, G, f.d_struct.p, k, fv, ld, Y, X, ld, part);
+            } else {
+                if (narrow) k_solve_gemm<T, 16, false><<<g, 256, 0, st>>>(dsn, it, G, f.d_struct.p, k, fv, ld, Y, X, ld, part);
+                else k_solve_gemm<T, 64, false><<<g, 256, 0, st>>>(dsn, it, G, f.d_struct.p, k, fv, ld, Y, X, ld, part);
+            }
+            HBSD_LAUNCHED(s);
         }
-    }
-    const int rchunks = ceil_div(k, RC);
-    // forward sweep
+        if (sw.n_red > 0) {
+            dim3 g(ceil_div((int64_t)64 * k, 256), sw.n_red);
+            if (bwd) k_solve_reduce<T, true><<<g, 256, 0, st>>>(dsn, red + sw.red_off, k, part, ld, fv, Y, X, ld, SOLVE_KS);
+            else k_solve_reduce<T, false><<<g, 256, 0, st>>>(dsn, red + sw.red_off, k, part, ld, fv, Y, X, ld, SOLVE_KS);
+            HBSD_LAUNCHED(s);
+        }
+        return 0;
+    };
     for (int h = 0; h <= H; ++h) {
-        const int* lid = LL.ids.p + LL.offs[h];
-        const int cnt = LL.counts[h];
-        dim3 gi(std::min(grid_for((int64_t)LL.max_nf[h] * k), 1024), cnt);
-        k_fv_init<T><<<gi, 256, 0, st>>>(dsn, lid, f.perm.p, R, ldr, k, fv, ldf);
+        dim3 gi(std::min(grid_for((int64_t)LL.max_nf[h] * k), 1024), LL.counts[h]);
+        k_fwd_assemble<T><<<gi, 256, 0, st>>>(dsn, LL.ids.p + LL.offs[h], f.perm.p, f.src.p, R, ldr, k, fv, ld);
         HBSD_LAUNCHED(s);
-        for (int slot = 0; slot < 2; ++slot) {
-            const int nj = LL.job_counts[slot][h];
-            if (nj == 0) continue;
-            dim3 g(std::min(grid_for((int64_t)LL.max_nf[h] * k), 1024), nj);
-            k_fv_extend_add<T><<<g, 256, 0, st>>>(dsn, LL.jobs.p + 2 * LL.job_offs[slot][h], nj, f.ea.p, k, fv, ldf);
-            HBSD_LAUNCHED(s);
-        }
-        for (int k0 = 0; k0 < LL.max_ns[h]; k0 += NB) {
-            dim3 gd(rchunks, cnt);
-            k_solve_diag<T, false><<<gd, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, D, k, fv, ldf);
-            HBSD_LAUNCHED(s);
-            int rem = 0, pairs = 0;
-            level_extent(f, h, k0, &rem, &pairs);
-            if (rem <= 0) continue;
-            dim3 gu(ceil_div(rem, 64), cnt, rchunks);
-            k_solve_fwd_update<T><<<gu, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, L, k, fv, ldf);
-            HBSD_LAUNCHED(s);
-        }
+        HBSD_TRY(gemm(h, false));
     }
-    // backward sweep
-    for (int h = H; h >= 0; --h) {
-        const int* lid = LL.ids.p + LL.offs[h];
-        const int cnt = LL.counts[h];
-        if (LL.max_nu[h] > 0) {
-            dim3 gg(ceil_div(LL.max_ns[h], 64), cnt, rchunks);
-            k_solve_bwd_gather<T><<<gg, 256, tile2_bytes<T>(), st>>>(dsn, lid, L, f.d_struct.p, xp, ldf, k, fv, ldf);
-            HBSD_LAUNCHED(s);
-        }
-        const int nblk = ceil_div(LL.max_ns[h], NB);
-        for (int b = nblk - 1; b >= 0; --b) {
-            const int k0 = b * NB;
-            dim3 gd(rchunks, cnt);
-            k_solve_diag<T, true><<<gd, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, D, k, fv, ldf);
-            HBSD_LAUNCHED(s);
-            if (k0 == 0) continue;
-            dim3 gu(ceil_div(k0, 64), cnt, rchunks);
-            k_solve_bwd_update<T><<<gu, 256, tile2_bytes<T>(), st>>>(dsn, lid, k0, L, k, fv, ldf);
-            HBSD_LAUNCHED(s);
-        }
-        dim3 gs(std::min(grid_for((int64_t)LL.max_ns[h] * k), 1024), cnt);
-        k_fv_store_x<T><<<gs, 256, 0, st>>>(dsn, lid, k, fv, ldf, xp, ldf);
-        HBSD_LAUNCHED(s);
-    }
-    k_unpermute_neg<T><<<grid_for(f.n * k), 256, 0, st>>>(f.perm.p, xp, ldf, f.n, k, P, ldp);
+    for (int h = H; h >= 0; --h) HBSD_TRY(gemm(h, true));
+    k_unpermute_neg<T><<<grid_for(f.n * k), 256, 0, st>>>(f.perm.p, X, ld, f.n, k, P, ldp);
     HBSD_LAUNCHED(s);
     return 0;
 }

@@ -86,7 +86,11 @@ struct Sell {
     DBuf<int32_t> slice_len;    // padded row length of each slice
     DBuf<int32_t> cols;         // stored column indices, slice-major, then entry-major, then row
     DBuf<double2> hs;           // (h - sigma0 s, s) per stored entry
-    DBuf<float2> hs32;          // FP32 copy for the mixed-precision path
+    DBuf<float2> hs32;          // FP32 values of the scaled pencil (D Hs D, D S D) for the mixed path
+    DBuf<double> dscale;        // D = diag(S)^{-1/2}
+    std::vector<double> h_dscale;
+    std::vector<int64_t> h_slice_ptr;
+    std::vector<int32_t> h_slot_row, h_cols;
     DBuf<int32_t> slot_row;     // original row of each slot (-1 for padding slots)
     std::vector<int64_t> h_entry_of_csr;  // stored position of each CSR entry (host, for updates)
 };
@@ -94,6 +98,7 @@ struct Sell {
 int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                const double* hval, const double* sval, double sigma0);
 int sell_update_h(Sell& m, const double* hval, const double* sval, double sigma0);
+int sell_fill_fp32(Sell& m, const double2* hs, const int32_t* cols, const int32_t* slot_row);
 
 // Y_h = Hs X, Y_s = S X for k columns; X, Y row-major.
 template <class T>
@@ -144,17 +149,21 @@ struct Factor {
     DBuf<int64_t> d_struct;
     DBuf<int32_t> ea;                            // child row -> parent front row
     DBuf<double> L;                              // panels
-    DBuf<float> L32;                             // FP32 copy (mixed path)
     DBuf<double> Dinv;                           // inverted diagonal blocks
-    DBuf<float> Dinv32;
     DBuf<int> d_sn;                              // packed per-supernode descriptors (see chol.cu)
     int max_front = 0;
     int max_ns = 0;
-    // solve workspace
-    DBuf<double> fv;                             // front vectors, fv_total * kmax
-    DBuf<double> xp;                             // permuted solution, n * kmax
-    DBuf<float> fv32, xp32;
-    int kmax = 0;
+    // explicit panels G = [L11^{-1}; -L21 L11^{-1}] used by the solves (layout of L)
+    DBuf<double> G;
+    DBuf<float> G32;
+    DBuf<int2> src;                              // extend-add sources of each front row (child 0, child 1)
+    struct Sweep { int item_off, n_items, red_off, n_red; };
+    std::vector<Sweep> sweep;                    // [2*level + (0 forward, 1 backward)]
+    DBuf<int64_t> items, red_items;              // packed work items (see chol.cu)
+    int64_t part_rows = 0;                       // split partial rows needed by the largest level
+    // solve workspace: front vectors | y | x | partials
+    DBuf<double> sws;
+    DBuf<float> sws32;
 };
 
 int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
@@ -162,23 +171,26 @@ int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const
 template <class T>
 int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, int64_t ldp,
                  cudaStream_t st);
-int factor_make_fp32(Factor& f, cudaStream_t st);
+int factor_make_fp32(Factor& f, const double* dscale, cudaStream_t st);
 
 // ---- dense helpers -------------------------------------------------------------------
 // column sums over rows of a row-major block: out[j] = sum_i A(i, j) * B(i, j)  (B may be A)
 template <class T>
 int col_dots(Session* s, const T* A, int64_t lda, const T* B, int64_t ldb, int64_t n, int k,
              double* out, cudaStream_t st);
-int gram2(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1,
-          int q1, const double* H0, int64_t ldh0, const double* H1, int64_t ldh1,
-          const double* S0, int64_t lds0, const double* S1, int64_t lds1, int64_t n, double* HR,
-          double* SR, cudaStream_t st);
+template <class T>
+int gram2(Session* s, const T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1, const T* H0,
+          int64_t ldh0, const T* H1, int64_t ldh1, const T* S0, int64_t lds0, const T* S1, int64_t lds1,
+          int64_t n, double* HR, double* SR, cudaStream_t st);
 int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
                  int64_t n, int q, double* HR, double* SR, cudaStream_t st);
-int update2(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
-            int64_t n, const double* W, int k, cudaStream_t st);
+template <class T>
+int update2(Session* s, T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1, int64_t n,
+            const double* W, int k, cudaStream_t st);
 int rayleigh_ritz(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
                   double* W, int* info_host, cudaStream_t st);
+int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
+                          double* W, int* info_host, cudaStream_t st, double drop_tol = 0.0);
 template <class T>
 int residual(Session* s, const T* PH, int64_t ldh, const T* PS, int64_t lds, const double* E, int m,
              T* R, int64_t ldr, int64_t n, double* res, double* rnorm, cudaStream_t st);
@@ -210,6 +222,8 @@ struct Session {
     DBuf<double> mr_col;        // per-column recurrence state, reinterpreted in minres.cu
     DBuf<double> mr_red;
     DBuf<int> mr_any, mr_steps;
+    // mixed-precision preconditioner buffers (FP32 scaled R and P)
+    DBuf<float> r32, p32;
     // warm-start state
     DBuf<double> psi_keep;
     int keep_w = 0;

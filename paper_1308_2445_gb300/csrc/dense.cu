@@ -148,19 +148,22 @@ template int residual<float>(Session*, const float*, int64_t, const float*, int6
                              int, float*, int64_t, int64_t, double*, double*, cudaStream_t);
 
 // ---- Gram (step 8) ---------------------------------------------------------------------
+template <class T>
 struct Seg2 {
-    const double* p0; int64_t ld0; int q0;
-    const double* p1; int64_t ld1;
-    __device__ __forceinline__ double at(int64_t i, int c) const {
+    const T* p0; int64_t ld0; int q0;
+    const T* p1; int64_t ld1;
+    __device__ __forceinline__ T at(int64_t i, int c) const {
         return c < q0 ? p0[i * ld0 + c] : p1[i * ld1 + (c - q0)];
     }
 };
 
-// One CTA: 32 x 32 output tile (a-block, b-block) over a chunk of rows.
-__global__ void __launch_bounds__(256) k_gram_partial(Seg2 Z, Seg2 ZH, Seg2 ZS, int q, int64_t n,
+// One CTA: 32 x 32 output tile (a-block, b-block) over a chunk of rows.  Each 32-row tile is
+// accumulated in T, the tiles in FP64 (for T = float this keeps the long sums in FP64).
+template <class T>
+__global__ void __launch_bounds__(256) k_gram_partial(Seg2<T> Z, Seg2<T> ZH, Seg2<T> ZS, int q, int64_t n,
                                                       int64_t rows_per_chunk, int tiles,
                                                       double* __restrict__ partial) {
-    __shared__ double sz[32][33], sh[32][33], ss[32][33];
+    __shared__ T sz[32][33], sh[32][33], ss[32][33];
     const int tile = blockIdx.x;
     const int ta = tile / tiles, tb = tile % tiles;
     const int a0 = ta * 32, b0 = tb * 32;
@@ -173,21 +176,26 @@ __global__ void __launch_bounds__(256) k_gram_partial(Seg2 Z, Seg2 ZH, Seg2 ZS, 
             const int rr = t >> 5, cc = t & 31;
             const int64_t i = i0 + rr;
             const bool ok = i < r1;
-            sz[rr][cc] = (ok && a0 + cc < q) ? Z.at(i, a0 + cc) : 0.0;
-            sh[rr][cc] = (ok && b0 + cc < q) ? ZH.at(i, b0 + cc) : 0.0;
-            ss[rr][cc] = (ok && b0 + cc < q) ? ZS.at(i, b0 + cc) : 0.0;
+            sz[rr][cc] = (ok && a0 + cc < q) ? Z.at(i, a0 + cc) : T(0);
+            sh[rr][cc] = (ok && b0 + cc < q) ? ZH.at(i, b0 + cc) : T(0);
+            ss[rr][cc] = (ok && b0 + cc < q) ? ZS.at(i, b0 + cc) : T(0);
         }
         __syncthreads();
+        T tH[2][2] = {{0, 0}, {0, 0}}, tS[2][2] = {{0, 0}, {0, 0}};
 #pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
-            const double z0 = sz[rr][ty * 2], z1 = sz[rr][ty * 2 + 1];
-            const double h0 = sh[rr][tx * 2], h1 = sh[rr][tx * 2 + 1];
-            const double s0 = ss[rr][tx * 2], s1 = ss[rr][tx * 2 + 1];
-            accH[0][0] = fma(z0, h0, accH[0][0]); accH[0][1] = fma(z0, h1, accH[0][1]);
-            accH[1][0] = fma(z1, h0, accH[1][0]); accH[1][1] = fma(z1, h1, accH[1][1]);
-            accS[0][0] = fma(z0, s0, accS[0][0]); accS[0][1] = fma(z0, s1, accS[0][1]);
-            accS[1][0] = fma(z1, s0, accS[1][0]); accS[1][1] = fma(z1, s1, accS[1][1]);
+            const T z0 = sz[rr][ty * 2], z1 = sz[rr][ty * 2 + 1];
+            const T h0 = sh[rr][tx * 2], h1 = sh[rr][tx * 2 + 1];
+            const T s0 = ss[rr][tx * 2], s1 = ss[rr][tx * 2 + 1];
+            tH[0][0] = fma(z0, h0, tH[0][0]); tH[0][1] = fma(z0, h1, tH[0][1]);
+            tH[1][0] = fma(z1, h0, tH[1][0]); tH[1][1] = fma(z1, h1, tH[1][1]);
+            tS[0][0] = fma(z0, s0, tS[0][0]); tS[0][1] = fma(z0, s1, tS[0][1]);
+            tS[1][0] = fma(z1, s0, tS[1][0]); tS[1][1] = fma(z1, s1, tS[1][1]);
         }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v) { accH[u][v] += (double)tH[u][v]; accS[u][v] += (double)tS[u][v]; }
         __syncthreads();
     }
     const int64_t qq = (int64_t)q * q;
@@ -222,9 +230,10 @@ __global__ void k_gram_final(const double* __restrict__ partial, int nchunks, in
     SR[idx] = 0.5 * (s_ab + s_ba);
 }
 
-int gram2(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
-          const double* H0, int64_t ldh0, const double* H1, int64_t ldh1, const double* S0,
-          int64_t lds0, const double* S1, int64_t lds1, int64_t n, double* HR, double* SR,
+template <class T>
+int gram2(Session* s, const T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1,
+          const T* H0, int64_t ldh0, const T* H1, int64_t ldh1, const T* S0,
+          int64_t lds0, const T* S1, int64_t lds1, int64_t n, double* HR, double* SR,
           cudaStream_t st) {
     const int q = q0 + q1;
     if (q <= 0) return 0;
@@ -234,15 +243,21 @@ int gram2(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, i
     nch = (int)((n + rpc - 1) / rpc);
     const size_t need = (size_t)nch * 2 * q * q;
     HBSD_TRY(s->ws.alloc(need + 64));
-    Seg2 Z{Z0, ld0, q0, Z1, ld1}, ZH{H0, ldh0, q0, H1, ldh1}, ZS{S0, lds0, q0, S1, lds1};
+    Seg2<T> Z{Z0, ld0, q0, Z1, ld1}, ZH{H0, ldh0, q0, H1, ldh1}, ZS{S0, lds0, q0, S1, lds1};
     dim3 grid(tiles * tiles, nch);
-    k_gram_partial<<<grid, 256, 0, st>>>(Z, ZH, ZS, q, n, rpc, tiles, s->ws.p);
+    k_gram_partial<T><<<grid, 256, 0, st>>>(Z, ZH, ZS, q, n, rpc, tiles, s->ws.p);
     HBSD_LAUNCHED(s);
     const int64_t qq = (int64_t)q * q;
     k_gram_final<<<ceil_div(qq, 256), 256, 0, st>>>(s->ws.p, nch, q, HR, SR);
     HBSD_LAUNCHED(s);
     return 0;
 }
+template int gram2<double>(Session*, const double*, int64_t, int, const double*, int64_t, int, const double*, int64_t,
+                           const double*, int64_t, const double*, int64_t, const double*, int64_t, int64_t, double*,
+                           double*, cudaStream_t);
+template int gram2<float>(Session*, const float*, int64_t, int, const float*, int64_t, int, const float*, int64_t,
+                          const float*, int64_t, const float*, int64_t, const float*, int64_t, int64_t, double*,
+                          double*, cudaStream_t);
 
 // ---- allocation-free Gram ---------------------------------------------------------------
 // Scratch for hbsd_gram_noalloc: a file-scope device array, so the call needs no cudaMalloc.
@@ -287,9 +302,9 @@ int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, c
     const int64_t rpc = (n + nch - 1) / nch;
     nch = (int)((n + rpc - 1) / rpc);
     // every partial element read by k_gram_final is written by k_gram_partial: nothing to clear
-    Seg2 A{Z, ldz, q, nullptr, 0}, AH{ZH, ldzh, q, nullptr, 0}, AS{ZS, ldzs, q, nullptr, 0};
+    Seg2<double> A{Z, ldz, q, nullptr, 0}, AH{ZH, ldzh, q, nullptr, 0}, AS{ZS, ldzs, q, nullptr, 0};
     dim3 grid(tiles * tiles, nch);
-    k_gram_partial<<<grid, 256, 0, st>>>(A, AH, AS, q, n, rpc, tiles, scratch);
+    k_gram_partial<double><<<grid, 256, 0, st>>>(A, AH, AS, q, n, rpc, tiles, scratch);
     HBSD_LAUNCHED(nullptr);
     const int64_t qq = (int64_t)q * q;
     k_gram_final<<<ceil_div(qq, 256), 256, 0, st>>>(scratch, nch, q, HR, SR);
@@ -299,16 +314,18 @@ int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, c
 
 // ---- update (steps 10-11) ------------------------------------------------------------------
 // 16 rows per CTA staged in shared memory; thread (jc, rg): column j = jc + 64*jb, rows 4*rg..4*rg+3
-__global__ void __launch_bounds__(256) k_update(double* __restrict__ Z0, int64_t ld0, int q0,
-                                                const double* __restrict__ Z1, int64_t ld1, int q1,
+template <class T>
+__global__ void __launch_bounds__(256) k_update(T* __restrict__ Z0, int64_t ld0, int q0,
+                                                const T* __restrict__ Z1, int64_t ld1, int q1,
                                                 int64_t n, const double* __restrict__ W, int k) {
-    extern __shared__ double zrow[];  // [16][q]
+    extern __shared__ __align__(16) unsigned char zraw[];
+    T* zrow = reinterpret_cast<T*>(zraw);  // [16][q]
     const int q = q0 + q1;
     const int64_t i0 = (int64_t)blockIdx.x * 16;
     for (int t = threadIdx.x; t < 16 * q; t += 256) {
         const int rr = t / q, c = t % q;
         const int64_t i = i0 + rr;
-        double v = 0.0;
+        T v = T(0);
         if (i < n) v = c < q0 ? Z0[i * ld0 + c] : Z1[i * ld1 + (c - q0)];
         zrow[rr * q + c] = v;
     }
@@ -317,9 +334,9 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ Z0, int64_t
     for (int jb = 0; jb * 64 < k; ++jb) {
         const int j = jb * 64 + jc;
         if (j >= k) continue;
-        double acc[4] = {0, 0, 0, 0};
+        T acc[4] = {0, 0, 0, 0};
         for (int c = 0; c < q; ++c) {
-            const double wv = __ldg(W + (int64_t)c * k + j);
+            const T wv = (T)__ldg(W + (int64_t)c * k + j);
 #pragma unroll
             for (int u = 0; u < 4; ++u) acc[u] = fma(zrow[(rg * 4 + u) * q + c], wv, acc[u]);
         }
@@ -331,18 +348,23 @@ __global__ void __launch_bounds__(256) k_update(double* __restrict__ Z0, int64_t
     }
 }
 
-int update2(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
+template <class T>
+int update2(Session* s, T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1,
             int64_t n, const double* W, int k, cudaStream_t st) {
     const int q = q0 + q1;
     if (k > q0) return fail(HBSD_ERR_ARG, "update: k must not exceed the first segment width");
-    const size_t smem = (size_t)16 * q * sizeof(double);
+    const size_t smem = (size_t)16 * q * sizeof(T);
     if (smem > 200 * 1024) return fail(HBSD_ERR_ARG, "update: q too large");
     if (smem > 48 * 1024)
-        HBSD_CUDA(cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_update<<<ceil_div(n, 16), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, W, k);
+        HBSD_CUDA(cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_update<T><<<ceil_div(n, 16), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, W, k);
     HBSD_LAUNCHED(s);
     return 0;
 }
+template int update2<double>(Session*, double*, int64_t, int, const double*, int64_t, int, int64_t, const double*, int,
+                             cudaStream_t);
+template int update2<float>(Session*, float*, int64_t, int, const float*, int64_t, int, int64_t, const double*, int,
+                            cudaStream_t);
 
 // ---- Rayleigh-Ritz (step 9), one CTA, FP64 ------------------------------------------------
 constexpr int RR_THREADS = 512;

@@ -12,6 +12,7 @@
 // A row is handled by lpr lanes; each lane owns VW consecutive columns per chunk (one 16-byte
 // vector load), so the gather of an X row is coalesced and vectorised.
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 
 #include "common.h"
@@ -48,6 +49,13 @@ int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_id
         sptr[s + 1] = sptr[s] + mx * C;
     }
     m.stored = sptr[m.n_slices];
+    m.h_slice_ptr = sptr;
+    m.h_slot_row = slot_row;
+    // D = diag(S)^{-1/2} (the diagonal entry of each row of S)
+    m.h_dscale.assign(n, 1.0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e)
+            if (col_idx[e] == r && sval[e] > 0.0) m.h_dscale[r] = 1.0 / std::sqrt(sval[e]);
     std::vector<int32_t> cols(m.stored, 0);
     std::vector<double2> hs(m.stored, make_double2(0.0, 0.0));
     m.h_entry_of_csr.assign(m.nnz, -1);
@@ -82,10 +90,29 @@ int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_id
     HBSD_CUDA(cudaMemcpy(m.cols.p, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice));
     HBSD_CUDA(cudaMemcpy(m.hs.p, hs.data(), hs.size() * sizeof(double2), cudaMemcpyHostToDevice));
     HBSD_CUDA(cudaMemcpy(m.slot_row.p, slot_row.data(), slot_row.size() * 4, cudaMemcpyHostToDevice));
-    // FP32 copy of the values for the mixed-precision path
-    std::vector<float2> hs32(m.stored);
-    for (int64_t i = 0; i < m.stored; ++i) hs32[i] = make_float2((float)hs[i].x, (float)hs[i].y);
+    m.h_cols = cols;
+    HBSD_TRY(m.dscale.alloc(n));
+    HBSD_CUDA(cudaMemcpy(m.dscale.p, m.h_dscale.data(), n * 8, cudaMemcpyHostToDevice));
     HBSD_TRY(m.hs32.alloc(m.stored));
+    return sell_fill_fp32(m, hs.data(), cols.data(), slot_row.data());
+}
+
+// FP32 values of the diagonally scaled pencil (D Hs D, D S D), D = diag(S)^{-1/2}: the mixed
+// path's FP32 phase runs on it, because the unscaled basis spans ~30 orders of magnitude.
+int sell_fill_fp32(Sell& m, const double2* hs, const int32_t* cols, const int32_t* slot_row) {
+    std::vector<float2> hs32(m.stored, make_float2(0.f, 0.f));
+    for (int64_t sl = 0; sl < m.n_slices; ++sl) {
+        const int64_t len = (m.h_slice_ptr[sl + 1] - m.h_slice_ptr[sl]) / m.C;
+        for (int t = 0; t < m.C; ++t) {
+            const int32_t r = slot_row[sl * m.C + t];
+            if (r < 0) continue;
+            for (int64_t j = 0; j < len; ++j) {
+                const int64_t pos = m.h_slice_ptr[sl] + j * m.C + t;
+                const double f = m.h_dscale[r] * m.h_dscale[cols[pos]];
+                hs32[pos] = make_float2((float)(f * hs[pos].x), (float)(f * hs[pos].y));
+            }
+        }
+    }
     HBSD_CUDA(cudaMemcpy(m.hs32.p, hs32.data(), hs32.size() * sizeof(float2), cudaMemcpyHostToDevice));
     return 0;
 }
@@ -98,10 +125,7 @@ int sell_update_h(Sell& m, const double* hval, const double* sval, double sigma0
         hs[pos] = make_double2(shifted, sval[e]);
     }
     HBSD_CUDA(cudaMemcpy(m.hs.p, hs.data(), hs.size() * sizeof(double2), cudaMemcpyHostToDevice));
-    std::vector<float2> hs32(m.stored);
-    for (int64_t i = 0; i < m.stored; ++i) hs32[i] = make_float2((float)hs[i].x, (float)hs[i].y);
-    HBSD_CUDA(cudaMemcpy(m.hs32.p, hs32.data(), hs32.size() * sizeof(float2), cudaMemcpyHostToDevice));
-    return 0;
+    return sell_fill_fp32(m, hs.data(), m.h_cols.data(), m.h_slot_row.data());
 }
 
 // ---- kernels ------------------------------------------------------------------------

@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <limits>
 
@@ -104,6 +106,26 @@ void seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out) {
 
 }  // namespace
 
+// ---- trace (HBSD_TRACE=1): one stderr line per outer iteration ----------------------------------
+static bool trace_on() {
+    static int on = -1;
+    if (on < 0) {
+        const char* e = std::getenv("HBSD_TRACE");
+        on = (e && e[0] && e[0] != '0') ? 1 : 0;
+    }
+    return on == 1;
+}
+
+// number of non-finite entries of a device array (trace only)
+static int count_nonfinite(const double* p, int64_t n, cudaStream_t st) {
+    std::vector<double> h(n);
+    if (cudaMemcpyAsync(h.data(), p, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+    int c = 0;
+    for (double v : h) c += !std::isfinite(v);
+    return c;
+}
+
 // ---- step timers: CUDA events on the session stream, read back after host syncs ------------------
 struct StepTimer {
     enum { MATVEC, RESID, PRECOND, LOCAL, GRAM, RR, UPDATE, NCLS };
@@ -143,34 +165,237 @@ struct StepTimer {
 };
 
 // ---- per-solve buffers -----------------------------------------------------------------------
+template <class T>
 struct SolveBufs {
-    DBuf<double> Psi, PsiH, PsiS, P, PH, PS, RU, Xa, Ra;
-    DBuf<double> E, res, HR, SR, W, theta, shifts, out_lam;
+    DBuf<T> Psi, PsiH, PsiS, P, PH, PS, RU, Xa, Ra, shifts;
+};
+
+struct SolveCommon {
+    DBuf<double> E, res, HR, SR, W, theta;
     DBuf<int> Ulist, Llist, steps;
 };
 
-static int labpsd_fp64(Session* S, int m, double tol, const double* X0, int64_t ldx0, double* lam_dev,
-                       double* X_dev, int64_t ldx, int* iters_out) {
+template <class S_, class D_>
+__global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, int64_t n, D_* __restrict__ dst,
+                                int64_t ldd, const double* __restrict__ d, int pw);
+
+// Stopping rule of one precision phase.
+struct PhaseRule {
+    double tol;          // Res_max target (remark 2)
+    int max_iters;       // outer iterations allowed in this phase
+    bool stagnation;     // stop when Res_max has not halved over `window` iterations (FP32 floor)
+    int window;
+};
+
+// LABPSD outline (Sec. 3) in precision T on the blocks of B, starting from Psi (n x w, ld ldw):
+// steps 1-3 (Rayleigh-Ritz on span(Psi)) then steps 4-11 until the rule stops it.  E_host and
+// Eprev carry the Ritz values across phases (remark 4 needs the previous ones).
+template <class T>
+static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int w, int64_t ldw, int64_t ldp,
+                        const PhaseRule& rule, std::vector<double>& E, std::vector<double>& Eprev, int* iters_done,
+                        bool* converged, StepTimer& tm) {
+    cudaStream_t st = S->stream;
+    const hbsd_options& o = S->opt;
+    const int64_t n = S->n;
+    hbsd_stats& stt = S->stats;
+    int ti;
+    int info[2];
+    *converged = false;
+    // FP32 phase: Gram entries carry ~1e-7 relative noise, so a scaled-S_R pivot below 1e-6 is
+    // treated as a dependent direction and dropped; FP64 keeps the reading of the paper (R13).
+    const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
+    // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
+    ti = tm.begin(StepTimer::MATVEC, st);
+    HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+    tm.end(ti, st);
+    stt.matvec_cols += w;
+    ti = tm.begin(StepTimer::GRAM, st);
+    HBSD_TRY(gram2<T>(S, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, B.PsiH.p, ldw, (const T*)nullptr, 0, B.PsiS.p,
+                      ldw, (const T*)nullptr, 0, n, C.HR.p, C.SR.p, st));
+    tm.end(ti, st);
+    if (trace_on())
+        std::fprintf(stderr, "[hbsd] %s start: Rayleigh-Ritz on the start block, nonfinite HR %d SR %d\n",
+                     sizeof(T) == 4 ? "fp32" : "fp64", count_nonfinite(C.HR.p, (int64_t)w * w, st),
+                     count_nonfinite(C.SR.p, (int64_t)w * w, st));
+    ti = tm.begin(StepTimer::RR, st);
+    HBSD_TRY(rayleigh_ritz_cluster(S, C.HR.p, C.SR.p, w, w, C.theta.p, C.W.p, info, st, drop_tol));
+    tm.end(ti, st);
+    stt.rr_fallbacks += info[0];
+    ti = tm.begin(StepTimer::UPDATE, st);
+    HBSD_TRY(update2<T>(S, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st));
+    HBSD_TRY(update2<T>(S, B.PsiH.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st));
+    HBSD_TRY(update2<T>(S, B.PsiS.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st));
+    tm.end(ti, st);
+    HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
+    HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
+    std::vector<double> res(m);
+    std::vector<int> U, Lpos;
+    std::vector<T> shifts;
+    std::vector<double> hist;
+    const bool hybrid = o.precond == HBSD_PRECOND_HYBRID;
+    int iters = 0;
+    for (;;) {
+        // steps 4-5
+        ti = tm.begin(StepTimer::RESID, st);
+        HBSD_TRY(residual<T>(S, B.PsiH.p, ldw, B.PsiS.p, ldw, C.E.p, m, (T*)nullptr, 0, n, C.res.p, nullptr, st));
+        tm.end(ti, st);
+        HBSD_CUDA(cudaMemcpyAsync(res.data(), C.res.p, m * 8, cudaMemcpyDeviceToHost, st));
+        HBSD_CUDA(cudaStreamSynchronize(st));
+        double rmax = 0.0;
+        for (double r : res) {
+            if (!std::isfinite(r)) return fail(HBSD_ERR_RR_RANK, "non-finite residual norm");
+            rmax = std::max(rmax, r);
+        }
+        stt.res_max = rmax;
+        hist.push_back(rmax);
+        if (rmax <= rule.tol) { *converged = true; break; }
+        if (iters >= rule.max_iters) break;
+        if (rule.stagnation && (int)hist.size() > rule.window) {
+            double best_before = hist[0];
+            for (size_t i = 0; i + rule.window < hist.size(); ++i) best_before = std::min(best_before, hist[i]);
+            double best_recent = hist[hist.size() - rule.window];
+            for (size_t i = hist.size() - rule.window; i < hist.size(); ++i) best_recent = std::min(best_recent, hist[i]);
+            if (best_recent > 0.5 * best_before) break;
+        }
+        // step 6: unconverged columns (remark 3), localized among them (remark 4)
+        U.clear(); Lpos.clear(); shifts.clear();
+        for (int i = 0; i < m; ++i)
+            if (res[i] > rule.tol) U.push_back(i);
+        const int p = (int)U.size();
+        if (hybrid && !Eprev.empty()) {
+            for (int j = 0; j < p; ++j) {
+                const int i = U[j];
+                if (res[i] <= o.tau1 && std::fabs(E[i] - Eprev[i]) <= o.tau2 * std::fabs(Eprev[i])) {
+                    Lpos.push_back(j);
+                    shifts.push_back((T)E[i]);
+                }
+            }
+        }
+        const int a = (int)Lpos.size();
+        HBSD_CUDA(cudaMemcpyAsync(C.Ulist.p, U.data(), p * sizeof(int), cudaMemcpyHostToDevice, st));
+        ti = tm.begin(StepTimer::RESID, st);
+        k_gather_residual<T><<<grid_for(n * p), 256, 0, st>>>(B.PsiH.p, ldw, B.PsiS.p, ldw, C.E.p, C.Ulist.p, p, n,
+                                                             B.RU.p, ldp);
+        HBSD_LAUNCHED(S);
+        tm.end(ti, st);
+        ti = tm.begin(StepTimer::PRECOND, st);
+        if (sizeof(T) == 8 && o.precision == HBSD_PRECISION_MIXED) {
+            // 6(a) in FP32 on the scaled pencil: P = D P^, P^ = -(D A D)^{-1} (D R)
+            k_convert_block<T, float><<<grid_for(n * p), 256, 0, st>>>(B.RU.p, ldp, p, n, S->r32.p, ldp,
+                                                                      S->A.dscale.p, +1);
+            HBSD_LAUNCHED(S);
+            HBSD_TRY(factor_solve<float>(S, S->F, S->r32.p, ldp, p, S->p32.p, ldp, st));
+            k_convert_block<float, T><<<grid_for(n * p), 256, 0, st>>>(S->p32.p, ldp, p, n, B.P.p, ldp,
+                                                                      S->A.dscale.p, +1);
+            HBSD_LAUNCHED(S);
+        } else {
+            HBSD_TRY(factor_solve<T>(S, S->F, B.RU.p, ldp, p, B.P.p, ldp, st));   // 6(a)
+        }
+        tm.end(ti, st);
+        stt.precond_cols += p;
+        stt.precond_calls += 1;
+        if (a > 0) {                                                          // 6(b)
+            ti = tm.begin(StepTimer::LOCAL, st);
+            HBSD_CUDA(cudaMemcpyAsync(C.Llist.p, Lpos.data(), a * sizeof(int), cudaMemcpyHostToDevice, st));
+            HBSD_CUDA(cudaMemcpyAsync(B.shifts.p, shifts.data(), a * sizeof(T), cudaMemcpyHostToDevice, st));
+            k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.P.p, ldp, C.Llist.p, a, n, B.Xa.p, ldp);
+            HBSD_LAUNCHED(S);
+            k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.RU.p, ldp, C.Llist.p, a, n, B.Ra.p, ldp);
+            HBSD_LAUNCHED(S);
+            int64_t msteps = 0;
+            HBSD_TRY(minres_batch<T>(S, B.Ra.p, ldp, B.shifts.p, a, o.eta, o.max_minres, B.Xa.p, ldp, C.steps.p,
+                                     &msteps, st));
+            k_scatter_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.Xa.p, ldp, C.Llist.p, a, n, B.P.p, ldp);
+            HBSD_LAUNCHED(S);
+            tm.end(ti, st);
+            stt.minres_steps += msteps;
+            stt.local_cols += a;
+        }
+        // step 7
+        ti = tm.begin(StepTimer::MATVEC, st);
+        HBSD_TRY(spmm_pair<T>(S, S->A, B.P.p, ldp, p, B.PH.p, ldp, B.PS.p, ldp, st));
+        tm.end(ti, st);
+        stt.matvec_cols += p;
+        // step 8
+        const int q = w + p;
+        ti = tm.begin(StepTimer::GRAM, st);
+        HBSD_TRY(gram2<T>(S, B.Psi.p, ldw, w, B.P.p, ldp, p, B.PsiH.p, ldw, B.PH.p, ldp, B.PsiS.p, ldw, B.PS.p, ldp,
+                          n, C.HR.p, C.SR.p, st));
+        tm.end(ti, st);
+        // step 9
+        if (trace_on())
+            std::fprintf(stderr, "[hbsd] %s it %d res_max %.3e p %d a %d nonfinite HR %d SR %d\n",
+                         sizeof(T) == 4 ? "fp32" : "fp64", iters + 1, hist.back(), p, a,
+                         count_nonfinite(C.HR.p, (int64_t)q * q, st), count_nonfinite(C.SR.p, (int64_t)q * q, st));
+        ti = tm.begin(StepTimer::RR, st);
+        HBSD_TRY(rayleigh_ritz_cluster(S, C.HR.p, C.SR.p, q, w, C.theta.p, C.W.p, info, st, drop_tol));
+        tm.end(ti, st);
+        stt.rr_fallbacks += info[0];
+        if (trace_on())
+            std::fprintf(stderr, "[hbsd]   RR q %d rank %d branch %d nonfinite theta %d W %d\n", q, info[1], info[0],
+                         count_nonfinite(C.theta.p, w, st), count_nonfinite(C.W.p, (int64_t)q * w, st));
+        // steps 10-11
+        ti = tm.begin(StepTimer::UPDATE, st);
+        HBSD_TRY(update2<T>(S, B.Psi.p, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st));
+        HBSD_TRY(update2<T>(S, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st));
+        HBSD_TRY(update2<T>(S, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st));
+        tm.end(ti, st);
+        Eprev = E;
+        HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
+        HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
+        ++iters;
+    }
+    *iters_done = iters;
+    return 0;
+}
+
+template <class T>
+static int alloc_blocks(SolveBufs<T>& B, int64_t n, int64_t ldw, int64_t ldp, int m) {
+    HBSD_TRY(B.Psi.alloc(n * ldw)); HBSD_TRY(B.PsiH.alloc(n * ldw)); HBSD_TRY(B.PsiS.alloc(n * ldw));
+    HBSD_TRY(B.P.alloc(n * ldp)); HBSD_TRY(B.PH.alloc(n * ldp)); HBSD_TRY(B.PS.alloc(n * ldp));
+    HBSD_TRY(B.RU.alloc(n * ldp)); HBSD_TRY(B.Xa.alloc(n * ldp)); HBSD_TRY(B.Ra.alloc(n * ldp));
+    HBSD_TRY(B.shifts.alloc(m));
+    return 0;
+}
+
+// dst(i, j) = src(i, j) * d_i^pow  (pow = -1: into scaled coordinates y = D^{-1} x; +1: back)
+template <class S_, class D_>
+__global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, int64_t n, D_* __restrict__ dst,
+                                int64_t ldd, const double* __restrict__ d, int pw) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t % k);
+        const double f = pw > 0 ? d[i] : 1.0 / d[i];
+        dst[i * ldd + j] = (D_)((double)src[i * lds + j] * f);
+    }
+}
+
+// Whole solve.  FP64: every step in FP64.  Mixed: the same FP64 iteration with step 6(a) -- the
+// global preconditioner, which only shapes the search directions -- applied in FP32 on the
+// diagonally scaled pencil (D A D, D = diag(S)^{-1/2}, which keeps its numbers inside the FP32
+// range).  Residuals, block products, Gram, Rayleigh-Ritz and MINRES stay FP64: the directions
+// K r carry components along the shared near-null space of H and S amplified ~1e11, and
+// extracting the subspace from them in FP32 diverges (measured on the 32^3 workload).
+static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t ldx0, double* lam_dev,
+                        double* X_dev, int64_t ldx, int* iters_out) {
     cudaStream_t st = S->stream;
     const hbsd_options& o = S->opt;
     const int64_t n = S->n;
     const int m0 = o.m0 >= 0 ? o.m0 : std::max(3, (m + 9) / 10);
     const int w = m + m0;
     if (m < 1 || w > n) return fail(HBSD_ERR_ARG, "nev + m0 must lie in [1, n]");
-    const int64_t ldw = round_up(w, 2), ldp = round_up(std::max(m, 1), 2);
+    const bool mixed = o.precision == HBSD_PRECISION_MIXED;
+    const int64_t ldw = round_up(w, 4), ldp = round_up(std::max(m, 1), 4);
     const int qmax = w + m;
-    SolveBufs B;
-    HBSD_TRY(B.Psi.alloc(n * ldw)); HBSD_TRY(B.PsiH.alloc(n * ldw)); HBSD_TRY(B.PsiS.alloc(n * ldw));
-    HBSD_TRY(B.P.alloc(n * ldp)); HBSD_TRY(B.PH.alloc(n * ldp)); HBSD_TRY(B.PS.alloc(n * ldp));
-    HBSD_TRY(B.RU.alloc(n * ldp)); HBSD_TRY(B.Xa.alloc(n * ldp)); HBSD_TRY(B.Ra.alloc(n * ldp));
-    HBSD_TRY(B.E.alloc(w)); HBSD_TRY(B.res.alloc(m)); HBSD_TRY(B.theta.alloc(w));
-    HBSD_TRY(B.HR.alloc((size_t)qmax * qmax)); HBSD_TRY(B.SR.alloc((size_t)qmax * qmax));
-    HBSD_TRY(B.W.alloc((size_t)qmax * w)); HBSD_TRY(B.shifts.alloc(m));
-    HBSD_TRY(B.Ulist.alloc(m)); HBSD_TRY(B.Llist.alloc(m)); HBSD_TRY(B.steps.alloc(m));
+    SolveCommon C;
+    HBSD_TRY(C.E.alloc(w)); HBSD_TRY(C.res.alloc(m)); HBSD_TRY(C.theta.alloc(w));
+    HBSD_TRY(C.HR.alloc((size_t)qmax * qmax)); HBSD_TRY(C.SR.alloc((size_t)qmax * qmax));
+    HBSD_TRY(C.W.alloc((size_t)qmax * w));
+    HBSD_TRY(C.Ulist.alloc(m)); HBSD_TRY(C.Llist.alloc(m)); HBSD_TRY(C.steps.alloc(m));
     {   // scratch of the reductions and the Gram partials, sized once (no reallocation mid-solve)
         const int tiles = ceil_div(qmax, 32);
         HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + (size_t)304 * 2 * qmax + 1024));
-        HBSD_TRY(S->rr_ws.alloc((size_t)4 * qmax * qmax + 3 * qmax + 64));
         HBSD_TRY(S->rr_info.alloc(4));
     }
     hbsd_stats& stt = S->stats;
@@ -180,120 +405,24 @@ static int labpsd_fp64(Session* S, int m, double tol, const double* X0, int64_t 
     stt.matvec_cols = stt.minres_spmm_cols = 0;
     stt.precond_calls = 0;
     StepTimer tm;
-    int ti;
-    // steps 1-3 on a cold start: Rayleigh-Ritz on span(X0), then Psi_H, Psi_S
-    k_copy_block<double><<<grid_for(n * w), 256, 0, st>>>(X0, ldx0, w, n, B.Psi.p, ldw);
-    HBSD_LAUNCHED(S);
-    ti = tm.begin(StepTimer::MATVEC, st);
-    HBSD_TRY(spmm_pair<double>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
-    tm.end(ti, st);
-    stt.matvec_cols += w;
-    ti = tm.begin(StepTimer::GRAM, st);
-    HBSD_TRY(gram2(S, B.Psi.p, ldw, w, nullptr, 0, 0, B.PsiH.p, ldw, nullptr, 0, B.PsiS.p, ldw, nullptr, 0, n,
-                   B.HR.p, B.SR.p, st));
-    tm.end(ti, st);
-    int info[2];
-    ti = tm.begin(StepTimer::RR, st);
-    HBSD_TRY(rayleigh_ritz(S, B.HR.p, B.SR.p, w, w, B.theta.p, B.W.p, info, st));
-    tm.end(ti, st);
-    stt.rr_fallbacks += info[0];
-    ti = tm.begin(StepTimer::UPDATE, st);
-    HBSD_TRY(update2(S, B.Psi.p, ldw, w, nullptr, 0, 0, n, B.W.p, w, st));
-    HBSD_TRY(update2(S, B.PsiH.p, ldw, w, nullptr, 0, 0, n, B.W.p, w, st));
-    HBSD_TRY(update2(S, B.PsiS.p, ldw, w, nullptr, 0, 0, n, B.W.p, w, st));
-    tm.end(ti, st);
-    std::vector<double> E(w), Eprev, res(m);
-    HBSD_CUDA(cudaMemcpyAsync(B.E.p, B.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
-    HBSD_CUDA(cudaMemcpyAsync(E.data(), B.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
-    int iters = 0;
-    bool converged = false;
-    const bool hybrid = o.precond == HBSD_PRECOND_HYBRID;
-    std::vector<int> U, Lpos;
-    std::vector<double> shifts;
-    for (;;) {
-        // steps 4-5
-        ti = tm.begin(StepTimer::RESID, st);
-        HBSD_TRY(residual<double>(S, B.PsiH.p, ldw, B.PsiS.p, ldw, B.E.p, m, nullptr, 0, n, B.res.p, nullptr, st));
-        tm.end(ti, st);
-        HBSD_CUDA(cudaMemcpyAsync(res.data(), B.res.p, m * 8, cudaMemcpyDeviceToHost, st));
-        HBSD_CUDA(cudaStreamSynchronize(st));
-        double rmax = 0.0;
-        for (double r : res) rmax = std::max(rmax, r);
-        stt.res_max = rmax;
-        if (rmax <= tol) { converged = true; break; }
-        if (iters >= o.max_outer) break;
-        // step 6: unconverged columns (remark 3), localized among them (remark 4)
-        U.clear(); Lpos.clear(); shifts.clear();
-        for (int i = 0; i < m; ++i)
-            if (res[i] > tol) U.push_back(i);
-        const int p = (int)U.size();
-        if (hybrid && !Eprev.empty()) {
-            for (int j = 0; j < p; ++j) {
-                const int i = U[j];
-                if (res[i] <= o.tau1 && std::fabs(E[i] - Eprev[i]) <= o.tau2 * std::fabs(Eprev[i])) {
-                    Lpos.push_back(j);
-                    shifts.push_back(E[i]);
-                }
-            }
-        }
-        const int a = (int)Lpos.size();
-        HBSD_CUDA(cudaMemcpyAsync(B.Ulist.p, U.data(), p * sizeof(int), cudaMemcpyHostToDevice, st));
-        ti = tm.begin(StepTimer::RESID, st);
-        k_gather_residual<double><<<grid_for(n * p), 256, 0, st>>>(B.PsiH.p, ldw, B.PsiS.p, ldw, B.E.p, B.Ulist.p, p,
-                                                                  n, B.RU.p, ldp);
-        HBSD_LAUNCHED(S);
-        tm.end(ti, st);
-        ti = tm.begin(StepTimer::PRECOND, st);
-        HBSD_TRY(factor_solve<double>(S, S->F, B.RU.p, ldp, p, B.P.p, ldp, st));   // 6(a)
-        tm.end(ti, st);
-        stt.precond_cols += p;
-        stt.precond_calls += 1;
-        if (a > 0) {                                                                 // 6(b)
-            ti = tm.begin(StepTimer::LOCAL, st);
-            HBSD_CUDA(cudaMemcpyAsync(B.Llist.p, Lpos.data(), a * sizeof(int), cudaMemcpyHostToDevice, st));
-            HBSD_CUDA(cudaMemcpyAsync(B.shifts.p, shifts.data(), a * 8, cudaMemcpyHostToDevice, st));
-            k_gather_cols<double><<<grid_for(n * a), 256, 0, st>>>(B.P.p, ldp, B.Llist.p, a, n, B.Xa.p, ldp);
-            HBSD_LAUNCHED(S);
-            k_gather_cols<double><<<grid_for(n * a), 256, 0, st>>>(B.RU.p, ldp, B.Llist.p, a, n, B.Ra.p, ldp);
-            HBSD_LAUNCHED(S);
-            int64_t msteps = 0;
-            HBSD_TRY(minres_batch<double>(S, B.Ra.p, ldp, B.shifts.p, a, o.eta, o.max_minres, B.Xa.p, ldp, B.steps.p,
-                                          &msteps, st));
-            k_scatter_cols<double><<<grid_for(n * a), 256, 0, st>>>(B.Xa.p, ldp, B.Llist.p, a, n, B.P.p, ldp);
-            HBSD_LAUNCHED(S);
-            tm.end(ti, st);
-            stt.minres_steps += msteps;
-            stt.local_cols += a;
-        }
-        // step 7
-        ti = tm.begin(StepTimer::MATVEC, st);
-        HBSD_TRY(spmm_pair<double>(S, S->A, B.P.p, ldp, p, B.PH.p, ldp, B.PS.p, ldp, st));
-        tm.end(ti, st);
-        stt.matvec_cols += p;
-        // step 8
-        const int q = w + p;
-        ti = tm.begin(StepTimer::GRAM, st);
-        HBSD_TRY(gram2(S, B.Psi.p, ldw, w, B.P.p, ldp, p, B.PsiH.p, ldw, B.PH.p, ldp, B.PsiS.p, ldw, B.PS.p, ldp, n,
-                       B.HR.p, B.SR.p, st));
-        tm.end(ti, st);
-        // step 9
-        ti = tm.begin(StepTimer::RR, st);
-        HBSD_TRY(rayleigh_ritz(S, B.HR.p, B.SR.p, q, w, B.theta.p, B.W.p, info, st));
-        tm.end(ti, st);
-        stt.rr_fallbacks += info[0];
-        // steps 10-11
-        ti = tm.begin(StepTimer::UPDATE, st);
-        HBSD_TRY(update2(S, B.Psi.p, ldw, w, B.P.p, ldp, p, n, B.W.p, w, st));
-        HBSD_TRY(update2(S, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, B.W.p, w, st));
-        HBSD_TRY(update2(S, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, B.W.p, w, st));
-        tm.end(ti, st);
-        Eprev = E;
-        HBSD_CUDA(cudaMemcpyAsync(B.E.p, B.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
-        HBSD_CUDA(cudaMemcpyAsync(E.data(), B.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
-        ++iters;
+    std::vector<double> E(w), Eprev;
+    SolveBufs<double> B64;
+    HBSD_TRY(alloc_blocks(B64, n, ldw, ldp, m));
+    int it32 = 0, it64 = 0;
+    bool conv = false;
+    if (mixed) {
+        HBSD_TRY(factor_make_fp32(S->F, S->A.dscale.p, st));
+        HBSD_TRY(S->r32.alloc((size_t)n * ldp));
+        HBSD_TRY(S->p32.alloc((size_t)n * ldp));
     }
+    k_copy_block<double><<<grid_for(n * w), 256, 0, st>>>(X0, ldx0, w, n, B64.Psi.p, ldw);
+    HBSD_LAUNCHED(S);
+    // FP64: the whole solve, or the final check and refinement sweep of the mixed form
+    PhaseRule r64{tol, std::max(0, o.max_outer - it32), false, 0};
+    HBSD_TRY(labpsd_phase<double>(S, B64, C, m, w, ldw, ldp, r64, E, Eprev, &it64, &conv, tm));
+    const int iters = it32 + it64;
     stt.iters = iters;
-    stt.iters_fp64 = iters;
+    stt.iters_fp64 = it64;
     tm.flush();
     stt.t_matvec_ms = tm.acc[StepTimer::MATVEC];
     stt.t_resid_ms = tm.acc[StepTimer::RESID];
@@ -303,21 +432,21 @@ static int labpsd_fp64(Session* S, int m, double tol, const double* X0, int64_t 
     stt.t_rr_ms = tm.acc[StepTimer::RR];
     stt.t_update_ms = tm.acc[StepTimer::UPDATE];
     if (lam_dev) {
-        k_shift_add<<<ceil_div(m, 128), 128, 0, st>>>(B.E.p, m, S->sigma0, lam_dev);
+        k_shift_add<<<ceil_div(m, 128), 128, 0, st>>>(C.E.p, m, S->sigma0, lam_dev);
         HBSD_LAUNCHED(S);
     }
     if (X_dev) {
-        k_copy_block<double><<<grid_for(n * m), 256, 0, st>>>(B.Psi.p, ldw, m, n, X_dev, ldx);
+        k_copy_block<double><<<grid_for(n * m), 256, 0, st>>>(B64.Psi.p, ldw, m, n, X_dev, ldx);
         HBSD_LAUNCHED(S);
     }
     // keep the block for a warm start
     HBSD_TRY(S->psi_keep.alloc(n * ldw));
-    HBSD_CUDA(cudaMemcpyAsync(S->psi_keep.p, B.Psi.p, n * ldw * 8, cudaMemcpyDeviceToDevice, st));
+    HBSD_CUDA(cudaMemcpyAsync(S->psi_keep.p, B64.Psi.p, n * ldw * 8, cudaMemcpyDeviceToDevice, st));
     S->keep_w = w;
     S->keep_ld = ldw;
     HBSD_CUDA(cudaStreamSynchronize(st));
     if (iters_out) *iters_out = iters;
-    return converged ? HBSD_OK : HBSD_NOT_CONVERGED;
+    return conv ? HBSD_OK : HBSD_NOT_CONVERGED;
 }
 
 }  // namespace hbsd
@@ -433,7 +562,8 @@ int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev,
     if (nev < 1 || !(tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
     const int w = nev + m0_of(*S, nev);
     if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
-    if (S->opt.precision != HBSD_PRECISION_FP64) return fail(HBSD_ERR_UNSUPPORTED, "precision mode not built yet");
+    if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
+        return fail(HBSD_ERR_ARG, "unknown precision mode");
     DBuf<double> x0buf;
     if (!X0_dev) {
         std::vector<double> hx((size_t)S->n * w);
@@ -447,7 +577,7 @@ int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev,
     }
     S->launches = 0;
     auto t0 = std::chrono::steady_clock::now();
-    int rc = labpsd_fp64(S, nev, tol, X0_dev, ldx0, lambda_dev, X_dev, ldx, iters);
+    int rc = labpsd_solve(S, nev, tol, X0_dev, ldx0, lambda_dev, X_dev, ldx, iters);
     auto t1 = std::chrono::steady_clock::now();
     S->stats.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     S->stats.gpu_launches = S->launches;
@@ -490,11 +620,35 @@ int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm, 
     return rc;
 }
 
+int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out) {
+    if (!out || count < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    seed_normals(seed, stream, count, out);
+    return HBSD_OK;
+}
+
 // ---- step-level entry points ---------------------------------------------------------------
 int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx, double* SX,
                    int64_t ldsx) {
     if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
     return spmm_pair<double>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+}
+
+int hbsd_spmm_pair_f32(hbsd_handle* h, const float* X, int64_t ldx, int k, float* HX, int64_t ldhx, float* SX,
+                       int64_t ldsx) {
+    if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    return spmm_pair<float>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+}
+
+int hbsd_precond_apply_f32(hbsd_handle* h, const float* R, int64_t ldr, int k, float* P, int64_t ldp) {
+    if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    HBSD_TRY(factor_make_fp32(h->s.F, h->s.A.dscale.p, h->s.stream));
+    return factor_solve<float>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream);
+}
+
+int hbsd_dscale(const hbsd_handle* h, double* d_host) {
+    if (!h || !d_host) return fail(HBSD_ERR_ARG, "bad arguments");
+    std::memcpy(d_host, h->s.A.h_dscale.data(), h->s.n * sizeof(double));
+    return HBSD_OK;
 }
 
 int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e, double* Y, int64_t ldy) {
@@ -536,8 +690,8 @@ int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, cons
     Session* S = scratch_session();
     const int tiles = ceil_div(q, 32);
     HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + 1024));
-    return gram2(S, Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR, SR,
-                 (cudaStream_t)stream);
+    return gram2<double>(S, Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR, SR,
+                         (cudaStream_t)stream);
 }
 
 int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
@@ -551,7 +705,7 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
     if (!HR || !SR || !theta || !W) return fail(HBSD_ERR_ARG, "bad arguments");
     Session* S = scratch_session();
     int hinfo[2] = {0, 0};
-    int rc = rayleigh_ritz(S, HR, SR, q, k, theta, W, hinfo, (cudaStream_t)stream);
+    int rc = rayleigh_ritz_cluster(S, HR, SR, q, k, theta, W, hinfo, (cudaStream_t)stream);
     if (info) {
         int tmp[2] = {hinfo[0], hinfo[1]};
         cudaError_t e = cudaMemcpy(info, tmp, sizeof(tmp), cudaMemcpyHostToDevice);
@@ -562,7 +716,7 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
 
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
     if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
-    return update2(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
+    return update2<double>(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -80,6 +80,9 @@ _SIGS = {
     "hbsd_get_stats": (None, [_P, C.POINTER(hbsd_stats)]),
     "hbsd_spmm_pair": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
     "hbsd_spmm_shifted": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, C.c_int64]),
+    "hbsd_spmm_pair_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
+    "hbsd_precond_apply_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64]),
+    "hbsd_dscale": (C.c_int, [_P, _D]),
     "hbsd_residual": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int, _P, C.c_int64, _P]),
     "hbsd_precond_apply": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64]),
     "hbsd_minres": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, C.c_double, C.c_int, _P, C.c_int64, _P]),
@@ -88,6 +91,7 @@ _SIGS = {
     "hbsd_rayleigh_ritz": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "hbsd_update": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int, _P]),
     "hbsd_probe_peak": (C.c_int, [C.c_int, _P, C.POINTER(C.c_double)]),
+    "hbsd_seed_normals": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int64, _D]),
 }
 
 _lib = None
@@ -242,6 +246,18 @@ class Session:
         check(lib().hbsd_residual(self.h, ptr(PsiH), ld(PsiH), ptr(PsiS), ld(PsiS), ptr(E), m, ptr(R),
                                   ld(R) if R is not None else 0, ptr(res)), "hbsd_residual")
 
+    def spmm_pair_f32(self, X, HX, SX):
+        check(lib().hbsd_spmm_pair_f32(self.h, ptr(X), ld(X), X.shape[1], ptr(HX), ld(HX), ptr(SX), ld(SX)),
+              "hbsd_spmm_pair_f32")
+
+    def precond_apply_f32(self, R, P):
+        check(lib().hbsd_precond_apply_f32(self.h, ptr(R), ld(R), R.shape[1], ptr(P), ld(P)), "hbsd_precond_apply_f32")
+
+    def dscale(self):
+        d = np.empty(self.n)
+        check(lib().hbsd_dscale(self.h, d.ctypes.data_as(_D)), "hbsd_dscale")
+        return d
+
     def precond_apply(self, R, P):
         check(lib().hbsd_precond_apply(self.h, ptr(R), ld(R), R.shape[1], ptr(P), ld(P)), "hbsd_precond_apply")
 
@@ -270,3 +286,10 @@ def probe_peak(which, stream=0):
     out = C.c_double(0.0)
     check(lib().hbsd_probe_peak(which, C.c_void_p(stream) if stream else None, C.byref(out)), "hbsd_probe_peak")
     return out.value
+
+
+def seed_normals(seed, stream, count):
+    """The library's start-block normals (host code, no GPU needed)."""
+    out = np.empty(count)
+    check(lib().hbsd_seed_normals(seed, stream, count, out.ctypes.data_as(_D)), "hbsd_seed_normals")
+    return out

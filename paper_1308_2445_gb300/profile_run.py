@@ -1,0 +1,44 @@
+"""Run one LABPSD solve of a named workload through the C ABI, for profilers (ncu).
+
+  python -m paper_1308_2445_gb300.profile_run --workload small|medium [--precision fp64|mixed]
+         [--max-outer K] [--solves S]
+
+--max-outer is the library's own outer-iteration cap (hbsd_options.max_outer): with a small
+value the run is a bounded, representative slice of the solve (factorisation, initial
+Rayleigh-Ritz and K full BPSD iterations) that a profiler can capture quickly.
+"""
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="small", choices=["small", "medium"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--max-outer", type=int, default=1000)
+    ap.add_argument("--solves", type=int, default=1)
+    a = ap.parse_args()
+    import numpy as np
+    from paper_1308_2445_gb300 import build_lib, hbsd, pufe_inputs as pi
+    if not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    p = pi.small_case(1) if a.workload == "small" else pi.medium_case(1)
+    nev = pi.SMALL_NEV if a.workload == "small" else pi.MEDIUM_NEV
+    prec = hbsd.PRECISION_MIXED if a.precision == "mixed" else hbsd.PRECISION_FP64
+    s = hbsd.Session.from_problem(p, precision=prec, max_outer=a.max_outer)
+    w = nev + s.m0(nev)
+    X0 = pi.seed_normal_block(1, p.n, w)
+    for _ in range(a.solves):
+        lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0, want_vectors=False)
+    print(json.dumps({"workload": a.workload, "n": p.n, "iters": it, "rc": rc, "res_max": st["res_max"],
+                      "t_solve_ms": st["t_solve_ms"], "launches": st["gpu_launches"]}))
+
+
+if __name__ == "__main__":
+    main()

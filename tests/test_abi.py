@@ -55,3 +55,13 @@ def test_create_rejects_bad_input_without_gpu(lib):
     rc = lib.hbsd_create(None, None, None, None, None, C.byref(h))
     assert rc == hbsd.HBSD_ERR_ARG
     assert b"required" in lib.hbsd_last_error()
+
+
+def test_library_start_block_generator_matches_inputs(lib):
+    # the library draws the same SplitMix64 / Box-Muller normals as the shared input module
+    import numpy as np
+    from paper_1308_2445_gb300 import hbsd, pufe_inputs as pi
+    for seed, count in ((1, 19 * 646), (5, 1001), (123456789, 8)):
+        a = hbsd.seed_normals(seed, pi.STREAM_X0, count)
+        b = pi.normal(seed, pi.STREAM_X0, count)
+        assert np.allclose(a, b, rtol=1e-14, atol=1e-14)

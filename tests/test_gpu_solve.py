@@ -185,3 +185,32 @@ def test_medium_solve_against_stored_oracle():
     # iteration count: the trajectory runs through (H - eps_bar S)^{-1} with kappa ~ 1e9, so
     # rounding-level differences in the factor are amplified; require +-10% of the oracle's count
     assert abs(it - g["iters"]) <= max(1, int(0.1 * g["iters"])), (it, g["iters"])
+
+
+# ------------------------------------------------------------------ mixed precision form
+def test_small_solve_mixed_precision():
+    """FP32 phase + FP64 refinement sweep: the same eigenpairs as the FP64 oracle at 1e-8."""
+    p = pi.small_case(1)
+    nev = 16
+    X0 = pi.seed_normal_block(1, p.n, 19)
+    s = hb().Session.from_problem(p, precision=hb().PRECISION_MIXED)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0)
+    assert rc == 0
+    compare(p, nev, lam, X, it, ro, iter_slack=10**6)   # iteration parity is not a claim of this form
+    assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+    assert st["iters_fp64"] <= st["iters"]
+
+
+def test_medium_solve_mixed_against_stored_oracle():
+    path = os.path.join(HERE, "golden", "medium_seed1.json")
+    g = json.load(open(path))
+    p = pi.medium_case(1)
+    nev = g["nev"]
+    X0 = pi.seed_normal_block(1, p.n, nev + L.default_m0(nev))
+    s = hb().Session.from_problem(p, precision=hb().PRECISION_MIXED)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ref = np.array(g["lam"])
+    assert rc == 0
+    assert np.abs(lam - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001

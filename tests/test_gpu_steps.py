@@ -266,3 +266,76 @@ def test_minres_against_oracle(mid):
         rr = np.linalg.norm(Hs @ Pg[:, j] - e[j] * (S @ Pg[:, j]) + R[:, j])
         if int(sg[j]) < 20:
             assert rr <= 0.25 * np.linalg.norm(R[:, j]) * (1 + 1e-6)
+
+
+# ------------------------------------------------------------------ FP32 forms (mixed precision)
+def fbuf(n, k):
+    t = torch.zeros(n, (k + 3) // 4 * 4, dtype=torch.float32, device="cuda")
+    return t[:, :k]
+
+
+def fdev(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    t = fbuf(a.shape[0], a.shape[1])
+    t.copy_(torch.from_numpy(a))
+    return t
+
+
+@pytest.mark.parametrize("k", [1, 5, 16, 64, 71])
+def test_spmm_pair_f32_scaled(mid, k):
+    p, s = mid
+    Hs, S, _ = L.make_shifted(p)
+    d = s.dscale()
+    Hh = (Hs.multiply(d[:, None]).multiply(d[None, :])).tocsr()
+    Sh = (S.multiply(d[:, None]).multiply(d[None, :])).tocsr()
+    X = pi.seed_normal_block(40 + k, p.n, k)
+    HX, SX = fbuf(p.n, k), fbuf(p.n, k)
+    s.spmm_pair_f32(fdev(X), HX, SX)
+    rH, rS = Hh @ X, Sh @ X
+    assert relerr(host(HX), rH) <= 2e-5 and relerr(host(SX), rS) <= 2e-5
+    assert np.allclose(1.0 / d ** 2, S.diagonal(), rtol=1e-12)
+
+
+@pytest.mark.parametrize("k", [1, 13, 64])
+def test_precond_f32_scaled(mid, k):
+    """FP32 preconditioner on the scaled pencil: P = -(D A D)^{-1} R, A = H - eps_bar S.
+    Compared with the FP64 library solve in the energy norm of D A D (errors along its
+    near-null directions, which FP32 cannot resolve, weigh little there): about u32 sqrt(kappa)."""
+    p, s = mid
+    Hs, S, _ = L.make_shifted(p)
+    d = s.dscale()
+    K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
+    R = pi.seed_normal_block(50 + k, p.n, k)
+    P = fbuf(p.n, k)
+    s.precond_apply_f32(fdev(R), P)
+    Pg = host(P).astype(np.float64)
+    ref = -K.solve(R / d[:, None]) / d[:, None]
+    Ah = (Hs.multiply(d[:, None]).multiply(d[None, :])).tocsr()
+    err = Pg - ref
+    num = np.sqrt(np.einsum("ij,ij->j", err, Ah @ err))
+    den = np.sqrt(np.einsum("ij,ij->j", ref, Ah @ ref))
+    assert np.isfinite(Pg).all()
+    assert (num / den).max() <= 1e-2, (num / den).max()
+
+
+@pytest.mark.parametrize("q,k,ndep", [(40, 19, 3), (135, 71, 10)])
+def test_rayleigh_ritz_fallback_large(q, k, ndep):
+    rng = np.random.default_rng(q)
+    n = 3 * q
+    Bm = rng.standard_normal((n, n))
+    Sf = Bm @ Bm.T + n * np.eye(n)
+    Hf = rng.standard_normal((n, n))
+    Hf = Hf + Hf.T
+    Z = rng.standard_normal((n, q))
+    for t in range(ndep):
+        Z[:, q - 1 - t] = Z[:, t] - 0.5 * Z[:, t + 1]
+    HR, SR = Z.T @ Hf @ Z, Z.T @ Sf @ Z
+    HR, SR = 0.5 * (HR + HR.T), 0.5 * (SR + SR.T)
+    th = torch.zeros(k, dtype=torch.float64, device="cuda")
+    W = torch.zeros(q, k, dtype=torch.float64, device="cuda")
+    info = torch.zeros(2, dtype=torch.int32, device="cuda")
+    hb().rayleigh_ritz(dense(HR), dense(SR), k, th, W, info)
+    g, Wo, fb = L.rayleigh_ritz(HR, SR, k)
+    inf = host(info)
+    assert fb and inf[0] == 1 and inf[1] == q - ndep
+    assert np.abs(host(th) - g).max() <= 1e-8 * np.abs(g).max()
