@@ -274,10 +274,6 @@ __global__ void k_copy_panels(const SnDev* __restrict__ sn, int nsn, const doubl
         L[s.L_off + i] = F[s.front_off + i];
 }
 
-__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
-}
 
 // ---- explicit panels G = [L11^{-1}; -L21 L11^{-1}] (factor time) ----------------------------------
 // Running the blocked forward substitution of a supernode on the right-hand side [I; 0] yields

@@ -221,9 +221,10 @@ struct Session {
     DBuf<float> mr_f;
     DBuf<double> mr_col;        // per-column recurrence state, reinterpreted in minres.cu
     DBuf<double> mr_red;
-    DBuf<int> mr_any, mr_steps;
+    DBuf<int> mr_any, mr_steps, mr_idx;
+    int64_t mr_ld = 0;
     // mixed-precision preconditioner buffers (FP32 scaled R and P)
-    DBuf<float> r32, p32;
+    DBuf<float> r32, p32, xa32, ra32, sh32;
     // warm-start state
     DBuf<double> psi_keep;
     int keep_w = 0;

@@ -3,10 +3,11 @@
 // (H - eps_j S) p = -r_j started from the globally preconditioned p_j, stopped when the
 // recurrence residual estimate drops to eta ||r_j|| (Eq. approxp) or after max_minres steps.
 //
-// All refined columns advance in lockstep: one shifted SpMM per step serves every column, the
-// Lanczos inner products are deterministic two-pass column reductions, and the Givens / QR
-// recurrences are per-column scalars updated by one thread per column.  A column that has met
-// its tolerance keeps its iterate and stops updating.
+// All refined columns advance in lockstep: one shifted SpMM per step serves every column still
+// iterating (gathered into a compact block once some have stopped), the Lanczos inner products
+// are deterministic two-pass column reductions, and the Givens / QR recurrences are per-column
+// scalars updated by one thread per column.  A column that has met its tolerance keeps its
+// iterate and stops updating.
 #include <cmath>
 
 #include "common.h"
@@ -86,6 +87,7 @@ __global__ void k_mr_lanczos(const MrCol* __restrict__ col, T* __restrict__ U, c
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx / k;
         const int j = (int)(idx % k);
+        if (!col[j].active) continue;
         const int64_t o = i * ld + j;
         U[o] = U[o] - (T)col[j].alpha * V[o] - (T)col[j].beta_old * Vp[o];
     }
@@ -163,11 +165,48 @@ inline int grid_for(int64_t work) {
     return (int)std::min<int64_t>(std::max<int64_t>(1, (work + 255) / 256), 4096);
 }
 
+__global__ void k_mr_active(const MrCol* __restrict__ col, int k, int* __restrict__ flags) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < k) flags[j] = col[j].active;
+}
+
+template <class T>
+__global__ void k_mr_gather(const T* __restrict__ V, int64_t ld, const T* __restrict__ e, const int* __restrict__ idx,
+                            int na, int64_t n, T* __restrict__ Vc, int64_t ldc, T* __restrict__ ec) {
+    const int64_t total = n * na;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / na;
+        const int j = (int)(t % na);
+        Vc[i * ldc + j] = V[i * ld + idx[j]];
+        if (i == 0) ec[j] = e[idx[j]];
+    }
+}
+
+template <class T>
+__global__ void k_mr_scatter(const T* __restrict__ Uc, int64_t ldc, const int* __restrict__ idx, int na, int64_t n,
+                             T* __restrict__ U, int64_t ld) {
+    const int64_t total = n * na;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / na;
+        const int j = (int)(t % na);
+        U[i * ld + idx[j]] = Uc[i * ldc + j];
+    }
+}
+
 }  // namespace
+
+static int k_active_flags(Session* s, const MrCol* col, int k, int* flags, cudaStream_t st) {
+    k_mr_active<<<ceil_div(k, 128), 128, 0, st>>>(col, k, flags);
+    HBSD_LAUNCHED(s);
+    return 0;
+}
 
 template <class T> static DBuf<T>& mr_vecs(Session* s);
 template <> DBuf<double>& mr_vecs<double>(Session* s) { return s->mr_d; }
 template <> DBuf<float>& mr_vecs<float>(Session* s) { return s->mr_f; }
+// compact block of the active columns (V, U and the shifts), after the 5 state blocks
+template <class T>
+static T* mr_compact(Session* s) { return mr_vecs<T>(s).p + 5 * s->n * s->mr_ld; }
 
 // X (n x k, ldx): start vectors on entry, refined vectors on exit.  R: residual columns.
 // e: shifts eps_j relative to sigma0 (device, k entries of T).  steps: device ints (nullable).
@@ -177,7 +216,9 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     if (k <= 0) return 0;
     const int64_t n = s->n;
     const int64_t ld = round_up(k, 4);
-    HBSD_TRY(mr_vecs<T>(s).alloc((size_t)5 * n * ld));
+    HBSD_TRY(mr_vecs<T>(s).alloc((size_t)7 * n * ld + ld));
+    HBSD_TRY(s->mr_idx.alloc(k));
+    s->mr_ld = ld;
     HBSD_TRY(s->mr_col.alloc((size_t)k * sizeof(MrCol) / sizeof(double) + 1));
     HBSD_TRY(s->mr_red.alloc((size_t)3 * k));
     HBSD_TRY(s->mr_any.alloc(1));
@@ -204,13 +245,34 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     HBSD_LAUNCHED(s);
     k_mr_start<T><<<g, 256, 0, st>>>(colp, V, Vp, Wp, Wpp, ld, n, k);
     HBSD_LAUNCHED(s);
-    int any = 0;
-    HBSD_CUDA(cudaMemcpyAsync(&any, anyp, sizeof(int), cudaMemcpyDeviceToHost, st));
-    HBSD_CUDA(cudaStreamSynchronize(st));
     s->stats.minres_spmm_cols += k;
-    for (int step = 1; step <= maxit && any; ++step) {
-        HBSD_TRY(spmm_shifted<T>(s, s->A, V, ld, k, e, U, ld, st));
-        s->stats.minres_spmm_cols += k;
+    // columns still iterating; the shifted SpMM of a step runs on those only (gathered into a
+    // compact block), the cheap memory-bound kernels run on all columns with masks
+    std::vector<int> act(k), flags(k);
+    for (int j = 0; j < k; ++j) act[j] = j;
+    HBSD_TRY(k_active_flags(s, colp, k, s->mr_steps.p, st));
+    HBSD_CUDA(cudaMemcpyAsync(flags.data(), s->mr_steps.p, k * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HBSD_CUDA(cudaStreamSynchronize(st));
+    act.clear();
+    for (int j = 0; j < k; ++j)
+        if (flags[j]) act.push_back(j);
+    for (int step = 1; step <= maxit && !act.empty(); ++step) {
+        const int na = (int)act.size();
+        if (na == k) {
+            HBSD_TRY(spmm_shifted<T>(s, s->A, V, ld, k, e, U, ld, st));
+        } else {
+            const int64_t ldc = round_up(na, 4);
+            HBSD_CUDA(cudaMemcpyAsync(s->mr_idx.p, act.data(), na * sizeof(int), cudaMemcpyHostToDevice, st));
+            T* Vc = mr_compact<T>(s);
+            T* Uc = Vc + n * ldc;
+            T* ec = Uc + n * ldc;
+            k_mr_gather<T><<<grid_for(n * na), 256, 0, st>>>(V, ld, e, s->mr_idx.p, na, n, Vc, ldc, ec);
+            HBSD_LAUNCHED(s);
+            HBSD_TRY(spmm_shifted<T>(s, s->A, Vc, ldc, na, ec, Uc, ldc, st));
+            k_mr_scatter<T><<<grid_for(n * na), 256, 0, st>>>(Uc, ldc, s->mr_idx.p, na, n, U, ld);
+            HBSD_LAUNCHED(s);
+        }
+        s->stats.minres_spmm_cols += na;
         HBSD_TRY(col_dots<T>(s, V, ld, U, ld, n, k, al, st));
         k_mr_set_alpha<<<ceil_div(k, 128), 128, 0, st>>>(colp, al, k);
         HBSD_LAUNCHED(s);
@@ -222,8 +284,12 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         HBSD_LAUNCHED(s);
         k_mr_vectors<T><<<g, 256, 0, st>>>(colp, X, ldx, V, Vp, U, Wp, Wpp, ld, n, k);
         HBSD_LAUNCHED(s);
-        HBSD_CUDA(cudaMemcpyAsync(&any, anyp, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HBSD_TRY(k_active_flags(s, colp, k, s->mr_steps.p, st));
+        HBSD_CUDA(cudaMemcpyAsync(flags.data(), s->mr_steps.p, k * sizeof(int), cudaMemcpyDeviceToHost, st));
         HBSD_CUDA(cudaStreamSynchronize(st));
+        act.clear();
+        for (int j = 0; j < k; ++j)
+            if (flags[j]) act.push_back(j);
     }
     if (steps || total_steps) {
         int* sp = steps ? steps : s->mr_steps.p;

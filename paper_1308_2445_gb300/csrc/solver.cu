@@ -278,16 +278,14 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                                                              B.RU.p, ldp);
         HBSD_LAUNCHED(S);
         tm.end(ti, st);
+        const bool fp32_dirs = sizeof(T) == 8 && o.precision == HBSD_PRECISION_MIXED;
         ti = tm.begin(StepTimer::PRECOND, st);
-        if (sizeof(T) == 8 && o.precision == HBSD_PRECISION_MIXED) {
-            // 6(a) in FP32 on the scaled pencil: P = D P^, P^ = -(D A D)^{-1} (D R)
+        if (fp32_dirs) {
+            // 6(a) in FP32 on the scaled pencil: P^ = -(D A D)^{-1} (D R); P^ stays scaled for 6(b)
             k_convert_block<T, float><<<grid_for(n * p), 256, 0, st>>>(B.RU.p, ldp, p, n, S->r32.p, ldp,
                                                                       S->A.dscale.p, +1);
             HBSD_LAUNCHED(S);
             HBSD_TRY(factor_solve<float>(S, S->F, S->r32.p, ldp, p, S->p32.p, ldp, st));
-            k_convert_block<float, T><<<grid_for(n * p), 256, 0, st>>>(S->p32.p, ldp, p, n, B.P.p, ldp,
-                                                                      S->A.dscale.p, +1);
-            HBSD_LAUNCHED(S);
         } else {
             HBSD_TRY(factor_solve<T>(S, S->F, B.RU.p, ldp, p, B.P.p, ldp, st));   // 6(a)
         }
@@ -297,12 +295,17 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         if (a > 0) {                                                          // 6(b)
             ti = tm.begin(StepTimer::LOCAL, st);
             HBSD_CUDA(cudaMemcpyAsync(C.Llist.p, Lpos.data(), a * sizeof(int), cudaMemcpyHostToDevice, st));
+            int64_t msteps = 0;
+            if (fp32_dirs) {   // P = D P^ (6(a) in FP32), the refinement in FP64
+                k_convert_block<float, T><<<grid_for(n * p), 256, 0, st>>>(S->p32.p, ldp, p, n, B.P.p, ldp,
+                                                                          S->A.dscale.p, +1);
+                HBSD_LAUNCHED(S);
+            }
             HBSD_CUDA(cudaMemcpyAsync(B.shifts.p, shifts.data(), a * sizeof(T), cudaMemcpyHostToDevice, st));
             k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.P.p, ldp, C.Llist.p, a, n, B.Xa.p, ldp);
             HBSD_LAUNCHED(S);
             k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.RU.p, ldp, C.Llist.p, a, n, B.Ra.p, ldp);
             HBSD_LAUNCHED(S);
-            int64_t msteps = 0;
             HBSD_TRY(minres_batch<T>(S, B.Ra.p, ldp, B.shifts.p, a, o.eta, o.max_minres, B.Xa.p, ldp, C.steps.p,
                                      &msteps, st));
             k_scatter_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.Xa.p, ldp, C.Llist.p, a, n, B.P.p, ldp);
@@ -310,6 +313,11 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             tm.end(ti, st);
             stt.minres_steps += msteps;
             stt.local_cols += a;
+        }
+        if (fp32_dirs && a == 0) {   // P = D P^ (no refinement this iteration)
+            k_convert_block<float, T><<<grid_for(n * p), 256, 0, st>>>(S->p32.p, ldp, p, n, B.P.p, ldp,
+                                                                      S->A.dscale.p, +1);
+            HBSD_LAUNCHED(S);
         }
         // step 7
         ti = tm.begin(StepTimer::MATVEC, st);
@@ -372,11 +380,12 @@ __global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, 
 }
 
 // Whole solve.  FP64: every step in FP64.  Mixed: the same FP64 iteration with step 6(a) -- the
-// global preconditioner, which only shapes the search directions -- applied in FP32 on the
-// diagonally scaled pencil (D A D, D = diag(S)^{-1/2}, which keeps its numbers inside the FP32
-// range).  Residuals, block products, Gram, Rayleigh-Ritz and MINRES stay FP64: the directions
-// K r carry components along the shared near-null space of H and S amplified ~1e11, and
-// extracting the subspace from them in FP32 diverges (measured on the 32^3 workload).
+// global preconditioner, which only shapes the search directions -- in FP32 on the diagonally
+// scaled pencil (D A D, D = diag(S)^{-1/2}, which keeps the numbers inside the FP32 range).
+// Residuals, MINRES, block products, Gram and Rayleigh-Ritz stay FP64: the directions K r carry
+// components along the shared near-null space of H and S amplified ~1e11; extracting the
+// subspace from them in FP32 diverges, and FP32 MINRES on them multiplies the outer iterations
+// (both measured on the 32^3 workload).
 static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t ldx0, double* lam_dev,
                         double* X_dev, int64_t ldx, int* iters_out) {
     cudaStream_t st = S->stream;
@@ -414,6 +423,9 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
         HBSD_TRY(factor_make_fp32(S->F, S->A.dscale.p, st));
         HBSD_TRY(S->r32.alloc((size_t)n * ldp));
         HBSD_TRY(S->p32.alloc((size_t)n * ldp));
+        HBSD_TRY(S->xa32.alloc((size_t)n * ldp));
+        HBSD_TRY(S->ra32.alloc((size_t)n * ldp));
+        HBSD_TRY(S->sh32.alloc(m));
     }
     k_copy_block<double><<<grid_for(n * w), 256, 0, st>>>(X0, ldx0, w, n, B64.Psi.p, ldw);
     HBSD_LAUNCHED(S);
