@@ -219,10 +219,11 @@ struct Session {
     // MINRES workspace (minres.cu)
     DBuf<double> mr_d;
     DBuf<float> mr_f;
-    DBuf<double> mr_col;        // per-column recurrence state, reinterpreted in minres.cu
-    DBuf<double> mr_red;
-    DBuf<int> mr_any, mr_steps, mr_idx;
-    int64_t mr_ld = 0;
+    DBuf<double> mr_red;        // per-block partial sums of the fused MINRES kernel
+    DBuf<int> mr_any, mr_steps; // grid barrier + error flag; per-column step counts
+    DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
+    DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel
+    int mr_blk_grid = 0;
     // mixed-precision preconditioner buffers (FP32 scaled R and P)
     DBuf<float> r32, p32, xa32, ra32, sh32;
     // warm-start state

@@ -3,210 +3,425 @@
 // (H - eps_j S) p = -r_j started from the globally preconditioned p_j, stopped when the
 // recurrence residual estimate drops to eta ||r_j|| (Eq. approxp) or after max_minres steps.
 //
-// All refined columns advance in lockstep: one shifted SpMM per step serves every column still
-// iterating (gathered into a compact block once some have stopped), the Lanczos inner products
-// are deterministic two-pass column reductions, and the Givens / QR recurrences are per-column
-// scalars updated by one thread per column.  A column that has met its tolerance keeps its
-// iterate and stops updating.
+// One cooperative (co-resident) launch runs every step of every column.  The refined columns
+// advance in lockstep; each step is three phases separated by grid barriers:
+//   A. U = (H - e_j S) V for the columns still iterating (SELL-C-sigma rows, lanes over the
+//      columns), with per-block partial sums of alpha_j = v_j . u_j;
+//   B. u_j -= alpha_j v_j + beta_j v_{j-1}, with per-block partials of ||u_j||^2;
+//   C. the Givens update of the QR factorisation of the Lanczos tridiagonal, then the
+//      direction, iterate and Lanczos-vector updates.
+// The per-column scalar recurrences are replicated in every block's shared memory: every block
+// reduces the per-block partials in the same fixed order, so all copies agree bit for bit and
+// nothing has to be broadcast.  A column that has met its tolerance keeps its iterate, stops
+// updating and leaves the SpMM.  The grid barrier is an arrival counter whose wait is bounded
+// by %globaltimer: a block that waits past the limit raises the error flag and every block
+// returns; the host reports HBSD_ERR_TIMEOUT.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "common.h"
 
 namespace hbsd {
 
-struct MrCol {
-    double beta_old, c_prev, s_prev, c_pp, s_pp, phibar, tol;
-    double alpha, beta_next, phi, gamma, delta, eps;
-    int active;     // still iterating
-    int upd;        // this step updates the iterate
-    int cont;       // a next Lanczos vector is needed
-    int steps;
-};
-
-template <class T>
-int col_dots(Session* s, const T* A, int64_t lda, const T* B, int64_t ldb, int64_t n, int k, double* out,
-             cudaStream_t st);
-
 namespace {
 
-// V = -R - U  (r0 = b - A x0 with b = -r_j)
-template <class T>
-__global__ void k_mr_r0(const T* __restrict__ R, int64_t ldr, const T* __restrict__ U, int64_t ldu,
-                        T* __restrict__ V, int64_t ldv, int64_t n, int k) {
-    const int64_t total = n * k;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / k;
-        const int j = (int)(idx % k);
-        V[i * ldv + j] = -R[i * ldr + j] - U[i * ldu + j];
-    }
+constexpr int MR_THREADS = 512;
+constexpr int MR_PASS = 128;                      // columns per pass (>= 4 rows per block step)
+constexpr uint64_t MR_WAIT_NS = 2000000000ull;   // grid-barrier wait limit (2 s)
+constexpr size_t MR_SMEM_MAX = 64 * 1024;
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void k_mr_init(MrCol* __restrict__ col, const double* __restrict__ rr, const double* __restrict__ bb,
-                          int k, double eta, int maxit, int* __restrict__ any) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    MrCol c{};
-    const double beta = sqrt(rr[j]);
-    c.tol = eta * sqrt(bb[j]);
-    c.beta_old = 0.0;
-    c.c_prev = 1.0; c.s_prev = 0.0; c.c_pp = 1.0; c.s_pp = 0.0;
-    c.phibar = beta;
-    c.beta_next = beta;         // used to normalise v_1
-    c.steps = 0;
-    c.active = (beta > c.tol && maxit > 0) ? 1 : 0;
-    c.upd = 0;
-    c.cont = c.active;
-    col[j] = c;
-    if (c.active) atomicOr(any, 1);
-}
-
-// v_1 = r0 / beta_1; v_0 = w_0 = w_{-1} = 0
-template <class T>
-__global__ void k_mr_start(const MrCol* __restrict__ col, T* __restrict__ V, T* __restrict__ Vp, T* __restrict__ Wp,
-                           T* __restrict__ Wpp, int64_t ld, int64_t n, int k) {
-    const int64_t total = n * k;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / k;
-        const int j = (int)(idx % k);
-        const int64_t o = i * ld + j;
-        if (col[j].active) V[o] = (T)((double)V[o] / col[j].beta_next);
-        Vp[o] = T(0); Wp[o] = T(0); Wpp[o] = T(0);
-    }
-}
-
-__global__ void k_mr_set_alpha(MrCol* __restrict__ col, const double* __restrict__ a, int k) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < k) col[j].alpha = a[j];
-}
-
-// U = U - alpha V - beta_old Vp
-template <class T>
-__global__ void k_mr_lanczos(const MrCol* __restrict__ col, T* __restrict__ U, const T* __restrict__ V,
-                             const T* __restrict__ Vp, int64_t ld, int64_t n, int k) {
-    const int64_t total = n * k;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / k;
-        const int j = (int)(idx % k);
-        if (!col[j].active) continue;
-        const int64_t o = i * ld + j;
-        U[o] = U[o] - (T)col[j].alpha * V[o] - (T)col[j].beta_old * Vp[o];
-    }
-}
-
-// Givens update of the QR factorisation of the Lanczos tridiagonal, one thread per column.
-__global__ void k_mr_scalars(MrCol* __restrict__ col, const double* __restrict__ uu, int k, int step,
-                             int* __restrict__ any) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= k) return;
-    MrCol c = col[j];
-    c.upd = 0;
-    c.cont = 0;
-    if (c.active) {
-        const double beta_next = sqrt(uu[j]);
-        const double eps = c.s_pp * c.beta_old;
-        const double dbar = c.c_pp * c.beta_old;
-        const double delta = c.c_prev * dbar + c.s_prev * c.alpha;
-        const double gbar = -c.s_prev * dbar + c.c_prev * c.alpha;
-        const double gamma = hypot(gbar, beta_next);
-        if (gamma == 0.0) {
-            c.active = 0;
+// bar[0]: arrivals, bar[1]: generation.  Returns false (for the whole block) when the wait
+// timed out here or another block has raised the error flag.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* err, int* ok_sm) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned old = atomicAdd(&bar[0], 1u);
+        if (old == nblocks - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
         } else {
-            const double ck = gbar / gamma, sk = beta_next / gamma;
-            c.phi = ck * c.phibar;
-            c.phibar = -sk * c.phibar;
-            c.gamma = gamma;
-            c.delta = delta;
-            c.eps = eps;
-            c.steps = step;
-            c.upd = 1;
-            const bool done = fabs(c.phibar) <= c.tol || beta_next == 0.0;
-            c.cont = done ? 0 : 1;
-            c.beta_next = beta_next;
-            c.beta_old = beta_next;
-            c.c_pp = c.c_prev; c.s_pp = c.s_prev;
-            c.c_prev = ck; c.s_prev = sk;
-            if (done) c.active = 0;
+            const uint64_t t0 = gtimer();
+            while (ld_acquire(&bar[1]) == gen) {
+                if (ld_relaxed(err)) { ok = 0; break; }
+                if (gtimer() - t0 > MR_WAIT_NS) { atomicExch(err, 1); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        gen += 1;
+        *ok_sm = ok;
+    }
+    __syncthreads();
+    return *ok_sm != 0;
+}
+
+struct MrArgs {
+    // SELL-C-sigma pattern with interleaved (h - sigma0 s, s)
+    const int64_t* slice_ptr;
+    const int32_t* slice_len;
+    const int32_t* cols;
+    const void* hs;
+    const int32_t* slot_row;
+    int64_t n_slots;
+    const int64_t* blk;   // gridDim + 1 slot boundaries, balanced by stored entries
+    int C;
+    int64_t n;
+    int k;
+    const void* R;
+    int64_t ldr;
+    const void* e;
+    void* X;
+    int64_t ldx;
+    void *V, *Vp, *U, *Wp, *Wpp;
+    int64_t ld;
+    double* part;   // [2][gridDim][kp] per-block partial sums
+    int64_t kp;
+    double eta;
+    int maxit;
+    int* steps_out;   // k ints (block 0 writes)
+    unsigned* bar;
+    int* err;
+    unsigned long long* stamps;   // nullable: phase times (ns) seen by block 0, for tracing
+};
+
+template <class T> struct Pair;
+template <> struct Pair<double> { using P = double2; };
+template <> struct Pair<float> { using P = float2; };
+
+// One pass over nc (<= MR_PASS) columns: the block's threads are flattened over (row, column)
+// pairs, thread t -> row r = t / nc of the current group of rb = blockDim / nc rows, column
+// c = t % nc, so that almost every lane does useful work for any column count.
+struct Pass {
+    int c0, nc, rb, r, c;
+};
+__device__ __forceinline__ Pass make_pass(int c0, int na) {
+    Pass p;
+    p.c0 = c0;
+    p.nc = min(MR_PASS, na - c0);
+    p.rb = (int)blockDim.x / p.nc;
+    p.r = (int)threadIdx.x / p.nc;
+    p.c = (int)threadIdx.x - p.r * p.nc;
+    return p;
+}
+
+// Block reduction of the per-thread partials (one column per thread) into part_row[c0 + c]:
+// a pairwise tree over the rb row slots, the same order in every block and every run.
+__device__ void block_partials(double acc, const Pass& p, double* red, double* part_row) {
+    const bool on = p.r < p.rb;
+    if (on) red[threadIdx.x] = acc;
+    __syncthreads();
+    int top = 1;
+    while (top < p.rb) top <<= 1;
+    for (int sdist = top >> 1; sdist >= 1; sdist >>= 1) {
+        if (on && p.r < sdist && p.r + sdist < p.rb) red[threadIdx.x] += red[threadIdx.x + sdist * p.nc];
+        __syncthreads();
+    }
+    if (on && p.r == 0) part_row[p.c0 + p.c] = red[p.c];
+    __syncthreads();
+}
+
+// out[pos] = sum over blocks of part[b * kp + pos] in a fixed order (one warp per position,
+// lanes stride over the blocks, then a shuffle tree); every block computes identical values.
+__device__ void grid_sum(const double* part, int64_t kp, int na, double* out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pos = warp; pos < na; pos += nw) {
+        double s = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) s += part[(int64_t)b * kp + pos];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[pos] = s;
+    }
+    __syncthreads();
+}
+
+// Shared-memory column state (k entries per field), replicated in every block: one base
+// pointer and k, fields at fixed multiples of k (keeps the state out of registers).
+enum DField { F_BETA_OLD, F_C_PREV, F_S_PREV, F_C_PP, F_S_PP, F_PHIBAR, F_TOL, F_ALPHA, F_BETA_NEXT, F_PHI, F_GINV,
+              F_BINV, F_DELTA, F_EPS, F_RED1, F_RED2, MR_DFIELDS };
+enum IField { I_ACTIVE, I_UPD, I_CONT, I_STEPS, I_ACT, MR_IFIELDS };
+struct ColState {
+    double* d;   // MR_DFIELDS x k
+    int* i;      // MR_IFIELDS x k, then nact
+    int k;
+    double* red; // blockDim doubles for block_partials
+    __device__ __forceinline__ double* f(DField x) const { return d + (int64_t)x * k; }
+    __device__ __forceinline__ int* g(IField x) const { return i + (int64_t)x * k; }
+    __device__ __forceinline__ int* nact() const { return i + (int64_t)MR_IFIELDS * k; }
+};
+
+__device__ __forceinline__ ColState col_state(double* smem, int k) {
+    ColState s;
+    s.red = smem;
+    s.d = smem + MR_THREADS;
+    s.i = reinterpret_cast<int*>(s.d + (int64_t)MR_DFIELDS * k);
+    s.k = k;
+    return s;
+}
+
+size_t mr_smem_bytes(int k) {
+    return ((size_t)MR_THREADS + (size_t)MR_DFIELDS * k) * sizeof(double) +
+           (size_t)(MR_IFIELDS * k + 2) * sizeof(int);
+}
+
+// Shifted SpMM of one pass over this block's slot range: thread (r, c) takes the slots
+// b0 + r, b0 + r + rb, ... and column j = jcol(c0 + c); f(row, j, y) receives
+// y = ((Hs - e_j S) Xin)(row, j).
+template <class T, class P, class J, class F>
+__device__ __forceinline__ void spmm_pass(const MrArgs& a, const P* hs, const T* E, const T* Xin, int64_t ldxin,
+                                          const Pass& p, J&& jcol, F&& f) {
+    if (p.r >= p.rb) return;
+    const int j = jcol(p.c0 + p.c);
+    const T ej = E[j];
+    const int64_t s1 = a.blk[blockIdx.x + 1];
+    for (int64_t slot = a.blk[blockIdx.x] + p.r; slot < s1; slot += p.rb) {
+        const int64_t sl = slot / a.C;
+        const int t = (int)(slot - sl * a.C);
+        const int64_t base = a.slice_ptr[sl] + t;
+        const int len = a.slice_len[sl];
+        T ah = T(0), as = T(0);
+#pragma unroll 4
+        for (int jj = 0; jj < len; ++jj) {
+            const int64_t ee = base + (int64_t)jj * a.C;
+            const int cj = __ldg(a.cols + ee);
+            const P hv = __ldg(hs + ee);
+            const T x = Xin[(int64_t)cj * ldxin + j];
+            ah = fma(hv.x, x, ah);
+            as = fma(hv.y, x, as);
+        }
+        const int row = a.slot_row[slot];
+        if (row >= 0) f((int64_t)row, j, ah - ej * as);
+    }
+}
+
+// Row-wise visit of one pass over this block's slot range: f(row, j).
+template <class J, class F>
+__device__ __forceinline__ void rows_pass(const MrArgs& a, const Pass& p, J&& jcol, F&& f) {
+    if (p.r >= p.rb) return;
+    const int j = jcol(p.c0 + p.c);
+    const int64_t s1 = a.blk[blockIdx.x + 1];
+    for (int64_t slot = a.blk[blockIdx.x] + p.r; slot < s1; slot += p.rb) {
+        const int row = a.slot_row[slot];
+        if (row >= 0) f((int64_t)row, j);
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
+    using P = typename Pair<T>::P;
+    extern __shared__ __align__(16) double smem[];
+    __shared__ int ok_sm;
+    const int k = a.k;
+    ColState S = col_state(smem, k);
+    const T* R = static_cast<const T*>(a.R);
+    const T* E = static_cast<const T*>(a.e);
+    T* X = static_cast<T*>(a.X);
+    T* V = static_cast<T*>(a.V);
+    T* Vp = static_cast<T*>(a.Vp);
+    T* U = static_cast<T*>(a.U);
+    T* Wp = static_cast<T*>(a.Wp);
+    T* Wpp = static_cast<T*>(a.Wpp);
+    const P* hs = static_cast<const P*>(a.hs);
+    const int64_t ld = a.ld;
+    double* partA = a.part;
+    double* partB = a.part + (int64_t)gridDim.x * a.kp;
+    double* rowA = partA + (int64_t)blockIdx.x * a.kp;
+    double* rowB = partB + (int64_t)blockIdx.x * a.kp;
+    unsigned gen = 0;
+    // tracing: block 0 adds the time since its previous mark to stamps[slot]
+    unsigned long long tmark = 0;
+    const bool tr = a.stamps != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+    if (tr) tmark = gtimer();
+    auto mark = [&](int slot) {
+        if (tr) {
+            const unsigned long long t = gtimer();
+            a.stamps[slot] += t - tmark;
+            tmark = t;
+        }
+    };
+    auto identity = [](int pos) { return pos; };
+    auto active_col = [&](int pos) { return S.g(I_ACT)[pos]; };
+
+    // ---- start: U = A_e X, V = r0 = -R - U, ||r0||^2 and ||R||^2 per column ----
+    for (int c0 = 0; c0 < k; c0 += MR_PASS) {
+        const Pass p = make_pass(c0, k);
+        double acc1 = 0.0, acc2 = 0.0;
+        spmm_pass<T>(a, hs, E, X, a.ldx, p, identity, [&](int64_t row, int j, T u) {
+            const T r = R[row * a.ldr + j];
+            const T v = -r - u;
+            V[row * ld + j] = v;
+            acc1 += (double)v * (double)v;
+            acc2 += (double)r * (double)r;
+        });
+        block_partials(acc1, p, S.red, rowA);
+        block_partials(acc2, p, S.red, rowB);
+    }
+    mark(0);
+    if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+    mark(4);
+    grid_sum(partA, a.kp, k, S.f(F_RED1));
+    grid_sum(partB, a.kp, k, S.f(F_RED2));
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double beta = sqrt(S.f(F_RED1)[j]);
+        S.f(F_TOL)[j] = a.eta * sqrt(S.f(F_RED2)[j]);
+        S.f(F_BETA_OLD)[j] = 0.0;
+        S.f(F_C_PREV)[j] = 1.0; S.f(F_S_PREV)[j] = 0.0; S.f(F_C_PP)[j] = 1.0; S.f(F_S_PP)[j] = 0.0;
+        S.f(F_PHIBAR)[j] = beta;
+        S.f(F_BETA_NEXT)[j] = beta;
+        S.f(F_BINV)[j] = beta > 0.0 ? 1.0 / beta : 0.0;
+        S.g(I_STEPS)[j] = 0;
+        S.g(I_ACTIVE)[j] = (beta > S.f(F_TOL)[j] && a.maxit > 0) ? 1 : 0;
+        S.g(I_UPD)[j] = 0;
+        S.g(I_CONT)[j] = S.g(I_ACTIVE)[j];
+    }
+    __syncthreads();
+    // v_1 = r0 / beta_1 for the active columns; v_0 = w_0 = w_{-1} = 0
+    for (int c0 = 0; c0 < k; c0 += MR_PASS) {
+        const Pass p = make_pass(c0, k);
+        rows_pass(a, p, identity, [&](int64_t i, int j) {
+            const int64_t o = i * ld + j;
+            if (S.g(I_ACTIVE)[j]) V[o] = (T)((double)V[o] * S.f(F_BINV)[j]);
+            Vp[o] = T(0);
+            Wp[o] = T(0);
+            Wpp[o] = T(0);
+        });
+    }
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int j = 0; j < k; ++j)
+            if (S.g(I_ACTIVE)[j]) S.g(I_ACT)[na++] = j;
+        S.nact()[0] = na;
+    }
+    mark(0);
+    if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+    mark(4);
+
+    for (int step = 1; step <= a.maxit && S.nact()[0] > 0; ++step) {
+        const int na = S.nact()[0];
+        // ---- A: U = A_e V on the active columns, partial alpha ----
+        for (int c0 = 0; c0 < na; c0 += MR_PASS) {
+            const Pass p = make_pass(c0, na);
+            double acc = 0.0;
+            spmm_pass<T>(a, hs, E, V, ld, p, active_col, [&](int64_t row, int j, T u) {
+                U[row * ld + j] = u;
+                acc += (double)V[row * ld + j] * (double)u;
+            });
+            block_partials(acc, p, S.red, rowA);
+        }
+        mark(1);
+        if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+        mark(4);
+        grid_sum(partA, a.kp, na, S.f(F_RED1));
+        for (int q = threadIdx.x; q < na; q += blockDim.x) S.f(F_ALPHA)[S.g(I_ACT)[q]] = S.f(F_RED1)[q];
+        __syncthreads();
+        // ---- B: Lanczos three-term update, partial ||u||^2 ----
+        for (int c0 = 0; c0 < na; c0 += MR_PASS) {
+            const Pass p = make_pass(c0, na);
+            double acc = 0.0;
+            rows_pass(a, p, active_col, [&](int64_t i, int j) {
+                const int64_t o = i * ld + j;
+                const T u = U[o] - (T)S.f(F_ALPHA)[j] * V[o] - (T)S.f(F_BETA_OLD)[j] * Vp[o];
+                U[o] = u;
+                acc += (double)u * (double)u;
+            });
+            block_partials(acc, p, S.red, rowB);
+        }
+        mark(2);
+        if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+        mark(4);
+        grid_sum(partB, a.kp, na, S.f(F_RED2));
+        // ---- C: Givens update (replicated per block), then the vector updates ----
+        for (int q = threadIdx.x; q < na; q += blockDim.x) {
+            const int j = S.g(I_ACT)[q];
+            S.g(I_UPD)[j] = 0;
+            S.g(I_CONT)[j] = 0;
+            const double beta_next = sqrt(S.f(F_RED2)[q]);
+            const double eps = S.f(F_S_PP)[j] * S.f(F_BETA_OLD)[j];
+            const double dbar = S.f(F_C_PP)[j] * S.f(F_BETA_OLD)[j];
+            const double delta = S.f(F_C_PREV)[j] * dbar + S.f(F_S_PREV)[j] * S.f(F_ALPHA)[j];
+            const double gbar = -S.f(F_S_PREV)[j] * dbar + S.f(F_C_PREV)[j] * S.f(F_ALPHA)[j];
+            const double gamma = hypot(gbar, beta_next);
+            if (gamma == 0.0) {
+                S.g(I_ACTIVE)[j] = 0;
+            } else {
+                const double ck = gbar / gamma, sk = beta_next / gamma;
+                S.f(F_PHI)[j] = ck * S.f(F_PHIBAR)[j];
+                S.f(F_PHIBAR)[j] = -sk * S.f(F_PHIBAR)[j];
+                S.f(F_GINV)[j] = 1.0 / gamma;
+                S.f(F_DELTA)[j] = delta;
+                S.f(F_EPS)[j] = eps;
+                S.g(I_STEPS)[j] = step;
+                S.g(I_UPD)[j] = 1;
+                const bool done = fabs(S.f(F_PHIBAR)[j]) <= S.f(F_TOL)[j] || beta_next == 0.0;
+                S.g(I_CONT)[j] = done ? 0 : 1;
+                S.f(F_BETA_NEXT)[j] = beta_next;
+                S.f(F_BINV)[j] = beta_next > 0.0 ? 1.0 / beta_next : 0.0;
+                S.f(F_BETA_OLD)[j] = beta_next;
+                S.f(F_C_PP)[j] = S.f(F_C_PREV)[j]; S.f(F_S_PP)[j] = S.f(F_S_PREV)[j];
+                S.f(F_C_PREV)[j] = ck; S.f(F_S_PREV)[j] = sk;
+                if (done) S.g(I_ACTIVE)[j] = 0;
+            }
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < na; c0 += MR_PASS) {
+            const Pass p = make_pass(c0, na);
+            rows_pass(a, p, active_col, [&](int64_t i, int j) {
+                if (!S.g(I_UPD)[j]) return;
+                const int64_t o = i * ld + j;
+                const double v = (double)V[o];
+                const double w = (v - S.f(F_DELTA)[j] * (double)Wp[o] - S.f(F_EPS)[j] * (double)Wpp[o]) * S.f(F_GINV)[j];
+                T* xp = X + i * a.ldx + j;
+                *xp = (T)((double)*xp + S.f(F_PHI)[j] * w);
+                Wpp[o] = Wp[o];
+                Wp[o] = (T)w;
+                if (S.g(I_CONT)[j]) {
+                    Vp[o] = V[o];
+                    V[o] = (T)((double)U[o] * S.f(F_BINV)[j]);
+                }
+            });
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int nn = 0;
+            for (int q = 0; q < na; ++q)
+                if (S.g(I_ACTIVE)[S.g(I_ACT)[q]]) S.g(I_ACT)[nn++] = S.g(I_ACT)[q];
+            S.nact()[0] = nn;
+        }
+        __syncthreads();
+        mark(3);
+        if (S.nact()[0] > 0 && step < a.maxit) {
+            if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+            mark(4);
         }
     }
-    col[j] = c;
-    if (c.active) atomicOr(any, 1);
-}
-
-// w = (v - delta w_prev - eps w_pp) / gamma;  x += phi w;  shift w;  v_prev = v; v = u / beta
-template <class T>
-__global__ void k_mr_vectors(const MrCol* __restrict__ col, T* __restrict__ X, int64_t ldx, T* __restrict__ V,
-                             T* __restrict__ Vp, const T* __restrict__ U, T* __restrict__ Wp, T* __restrict__ Wpp,
-                             int64_t ld, int64_t n, int k) {
-    const int64_t total = n * k;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / k;
-        const int j = (int)(idx % k);
-        const MrCol& c = col[j];
-        if (!c.upd) continue;
-        const int64_t o = i * ld + j;
-        const double v = (double)V[o];
-        const double w = (v - c.delta * (double)Wp[o] - c.eps * (double)Wpp[o]) / c.gamma;
-        X[i * ldx + j] = (T)((double)X[i * ldx + j] + c.phi * w);
-        Wpp[o] = Wp[o];
-        Wp[o] = (T)w;
-        if (c.cont) {
-            Vp[o] = V[o];
-            V[o] = (T)((double)U[o] / c.beta_next);
-        }
-    }
-}
-
-__global__ void k_mr_steps(const MrCol* __restrict__ col, int k, int* __restrict__ steps) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < k) steps[j] = col[j].steps;
-}
-
-inline int grid_for(int64_t work) {
-    return (int)std::min<int64_t>(std::max<int64_t>(1, (work + 255) / 256), 4096);
-}
-
-__global__ void k_mr_active(const MrCol* __restrict__ col, int k, int* __restrict__ flags) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < k) flags[j] = col[j].active;
-}
-
-template <class T>
-__global__ void k_mr_gather(const T* __restrict__ V, int64_t ld, const T* __restrict__ e, const int* __restrict__ idx,
-                            int na, int64_t n, T* __restrict__ Vc, int64_t ldc, T* __restrict__ ec) {
-    const int64_t total = n * na;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / na;
-        const int j = (int)(t % na);
-        Vc[i * ldc + j] = V[i * ld + idx[j]];
-        if (i == 0) ec[j] = e[idx[j]];
-    }
-}
-
-template <class T>
-__global__ void k_mr_scatter(const T* __restrict__ Uc, int64_t ldc, const int* __restrict__ idx, int na, int64_t n,
-                             T* __restrict__ U, int64_t ld) {
-    const int64_t total = n * na;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / na;
-        const int j = (int)(t % na);
-        U[i * ld + idx[j]] = Uc[i * ldc + j];
-    }
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < k; j += blockDim.x) a.steps_out[j] = S.g(I_STEPS)[j];
 }
 
 }  // namespace
 
-static int k_active_flags(Session* s, const MrCol* col, int k, int* flags, cudaStream_t st) {
-    k_mr_active<<<ceil_div(k, 128), 128, 0, st>>>(col, k, flags);
-    HBSD_LAUNCHED(s);
-    return 0;
-}
-
 template <class T> static DBuf<T>& mr_vecs(Session* s);
 template <> DBuf<double>& mr_vecs<double>(Session* s) { return s->mr_d; }
 template <> DBuf<float>& mr_vecs<float>(Session* s) { return s->mr_f; }
-// compact block of the active columns (V, U and the shifts), after the 5 state blocks
-template <class T>
-static T* mr_compact(Session* s) { return mr_vecs<T>(s).p + 5 * s->n * s->mr_ld; }
 
 // X (n x k, ldx): start vectors on entry, refined vectors on exit.  R: residual columns.
 // e: shifts eps_j relative to sigma0 (device, k entries of T).  steps: device ints (nullable).
@@ -214,96 +429,113 @@ template <class T>
 int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double eta, int maxit, T* X,
                  int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st) {
     if (k <= 0) return 0;
+    const size_t smem = mr_smem_bytes(k);
+    if (smem > MR_SMEM_MAX) return fail(HBSD_ERR_ARG, "minres: too many columns for one launch");
     const int64_t n = s->n;
     const int64_t ld = round_up(k, 4);
-    HBSD_TRY(mr_vecs<T>(s).alloc((size_t)7 * n * ld + ld));
-    HBSD_TRY(s->mr_idx.alloc(k));
-    s->mr_ld = ld;
-    HBSD_TRY(s->mr_col.alloc((size_t)k * sizeof(MrCol) / sizeof(double) + 1));
-    HBSD_TRY(s->mr_red.alloc((size_t)3 * k));
-    HBSD_TRY(s->mr_any.alloc(1));
+    HBSD_TRY(mr_vecs<T>(s).alloc((size_t)5 * n * ld));
     HBSD_TRY(s->mr_steps.alloc(k));
-    MrCol* colp = reinterpret_cast<MrCol*>(s->mr_col.p);
-    int* anyp = s->mr_any.p;
+    HBSD_TRY(s->mr_any.alloc(4));   // [0..1] grid barrier, [2] error flag
+    static int blocks_per_sm[2] = {-1, -1};
+    static int num_sms = 0;
+    const int ti = sizeof(T) == 8 ? 0 : 1;
+    if (blocks_per_sm[ti] < 0) {
+        int dev = 0;
+        HBSD_CUDA(cudaGetDevice(&dev));
+        HBSD_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+        HBSD_CUDA(cudaFuncSetAttribute(k_minres<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_MAX));
+        int nb = 0;
+        HBSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_minres<T>, MR_THREADS, MR_SMEM_MAX));
+        blocks_per_sm[ti] = nb;
+    }
+    if (blocks_per_sm[ti] < 1) return fail(HBSD_ERR_UNSUPPORTED, "minres: kernel cannot be resident");
+    const int grid = blocks_per_sm[ti] * num_sms;
+    const int64_t kp = round_up(k, 4);
+    HBSD_TRY(s->mr_red.alloc((size_t)2 * grid * kp));
+    if (s->mr_blk_grid != grid) {
+        // contiguous slot ranges per block with about equal stored entries (+2 per row for the
+        // per-row work outside the nonzero loop)
+        const Sell& A = s->A;
+        std::vector<int64_t> wcum(A.n_slots + 1, 0);
+        for (int64_t sl = 0; sl < A.n_slices; ++sl) {
+            const int64_t len = (A.h_slice_ptr[sl + 1] - A.h_slice_ptr[sl]) / A.C;
+            for (int t = 0; t < A.C; ++t) {
+                const int64_t slot = sl * A.C + t;
+                if (slot < A.n_slots) wcum[slot + 1] = len + 2;
+            }
+        }
+        for (int64_t i = 0; i < A.n_slots; ++i) wcum[i + 1] += wcum[i];
+        std::vector<int64_t> blk(grid + 1, A.n_slots);
+        blk[0] = 0;
+        int64_t slot = 0;
+        for (int b = 1; b < grid; ++b) {
+            const double target = (double)wcum[A.n_slots] * b / grid;
+            while (slot < A.n_slots && (double)wcum[slot] < target) ++slot;
+            blk[b] = slot;
+        }
+        HBSD_TRY(s->mr_blk.alloc(grid + 1));
+        HBSD_CUDA(cudaMemcpy(s->mr_blk.p, blk.data(), (grid + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        s->mr_blk_grid = grid;
+    }
+    HBSD_CUDA(cudaMemsetAsync(s->mr_any.p, 0, 4 * sizeof(int), st));
     T* V = mr_vecs<T>(s).p;
-    T* Vp = V + n * ld;
-    T* U = Vp + n * ld;
-    T* Wp = U + n * ld;
-    T* Wpp = Wp + n * ld;
-    double* rr = s->mr_red.p;
-    double* bb = rr + k;
-    double* al = bb + k;
-    const int g = grid_for(n * k);
-    // r0 = -R - A X
-    HBSD_TRY(spmm_shifted<T>(s, s->A, X, ldx, k, e, U, ld, st));
-    k_mr_r0<T><<<g, 256, 0, st>>>(R, ldr, U, ld, V, ld, n, k);
+    MrArgs a;
+    a.slice_ptr = s->A.slice_ptr.p;
+    a.slice_len = s->A.slice_len.p;
+    a.cols = s->A.cols.p;
+    a.hs = sizeof(T) == 8 ? static_cast<const void*>(s->A.hs.p) : static_cast<const void*>(s->A.hs32.p);
+    a.slot_row = s->A.slot_row.p;
+    a.n_slots = s->A.n_slots;
+    a.blk = s->mr_blk.p;
+    a.C = s->A.C;
+    a.n = n;
+    a.k = k;
+    a.R = R;
+    a.ldr = ldr;
+    a.e = e;
+    a.X = X;
+    a.ldx = ldx;
+    a.V = V;
+    a.Vp = V + n * ld;
+    a.U = V + 2 * n * ld;
+    a.Wp = V + 3 * n * ld;
+    a.Wpp = V + 4 * n * ld;
+    a.ld = ld;
+    a.part = s->mr_red.p;
+    a.kp = kp;
+    a.eta = eta;
+    a.maxit = maxit;
+    int* sp = steps ? steps : s->mr_steps.p;
+    a.steps_out = sp;
+    a.bar = reinterpret_cast<unsigned*>(s->mr_any.p);
+    a.err = s->mr_any.p + 2;
+    static const bool trace = std::getenv("HBSD_TRACE") != nullptr;
+    a.stamps = nullptr;
+    if (trace) {
+        HBSD_TRY(s->mr_stamps.alloc(8));
+        HBSD_CUDA(cudaMemsetAsync(s->mr_stamps.p, 0, 8 * sizeof(unsigned long long), st));
+        a.stamps = s->mr_stamps.p;
+    }
+    void* args[] = {&a};
+    HBSD_CUDA(cudaLaunchCooperativeKernel((const void*)k_minres<T>, dim3(grid), dim3(MR_THREADS), args, smem, st));
     HBSD_LAUNCHED(s);
-    HBSD_TRY(col_dots<T>(s, V, ld, V, ld, n, k, rr, st));
-    HBSD_TRY(col_dots<T>(s, R, ldr, R, ldr, n, k, bb, st));
-    HBSD_CUDA(cudaMemsetAsync(anyp, 0, sizeof(int), st));
-    k_mr_init<<<ceil_div(k, 128), 128, 0, st>>>(colp, rr, bb, k, eta, maxit, anyp);
-    HBSD_LAUNCHED(s);
-    k_mr_start<T><<<g, 256, 0, st>>>(colp, V, Vp, Wp, Wpp, ld, n, k);
-    HBSD_LAUNCHED(s);
-    s->stats.minres_spmm_cols += k;
-    // columns still iterating; the shifted SpMM of a step runs on those only (gathered into a
-    // compact block), the cheap memory-bound kernels run on all columns with masks
-    std::vector<int> act(k), flags(k);
-    for (int j = 0; j < k; ++j) act[j] = j;
-    HBSD_TRY(k_active_flags(s, colp, k, s->mr_steps.p, st));
-    HBSD_CUDA(cudaMemcpyAsync(flags.data(), s->mr_steps.p, k * sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int> h(k);
+    int flags[4] = {0, 0, 0, 0};
+    HBSD_CUDA(cudaMemcpyAsync(flags, s->mr_any.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    HBSD_CUDA(cudaMemcpyAsync(h.data(), sp, k * sizeof(int), cudaMemcpyDeviceToHost, st));
     HBSD_CUDA(cudaStreamSynchronize(st));
-    act.clear();
-    for (int j = 0; j < k; ++j)
-        if (flags[j]) act.push_back(j);
-    for (int step = 1; step <= maxit && !act.empty(); ++step) {
-        const int na = (int)act.size();
-        if (na == k) {
-            HBSD_TRY(spmm_shifted<T>(s, s->A, V, ld, k, e, U, ld, st));
-        } else {
-            const int64_t ldc = round_up(na, 4);
-            HBSD_CUDA(cudaMemcpyAsync(s->mr_idx.p, act.data(), na * sizeof(int), cudaMemcpyHostToDevice, st));
-            T* Vc = mr_compact<T>(s);
-            T* Uc = Vc + n * ldc;
-            T* ec = Uc + n * ldc;
-            k_mr_gather<T><<<grid_for(n * na), 256, 0, st>>>(V, ld, e, s->mr_idx.p, na, n, Vc, ldc, ec);
-            HBSD_LAUNCHED(s);
-            HBSD_TRY(spmm_shifted<T>(s, s->A, Vc, ldc, na, ec, Uc, ldc, st));
-            k_mr_scatter<T><<<grid_for(n * na), 256, 0, st>>>(Uc, ldc, s->mr_idx.p, na, n, U, ld);
-            HBSD_LAUNCHED(s);
-        }
-        s->stats.minres_spmm_cols += na;
-        HBSD_TRY(col_dots<T>(s, V, ld, U, ld, n, k, al, st));
-        k_mr_set_alpha<<<ceil_div(k, 128), 128, 0, st>>>(colp, al, k);
-        HBSD_LAUNCHED(s);
-        k_mr_lanczos<T><<<g, 256, 0, st>>>(colp, U, V, Vp, ld, n, k);
-        HBSD_LAUNCHED(s);
-        HBSD_TRY(col_dots<T>(s, U, ld, U, ld, n, k, rr, st));
-        HBSD_CUDA(cudaMemsetAsync(anyp, 0, sizeof(int), st));
-        k_mr_scalars<<<ceil_div(k, 128), 128, 0, st>>>(colp, rr, k, step, anyp);
-        HBSD_LAUNCHED(s);
-        k_mr_vectors<T><<<g, 256, 0, st>>>(colp, X, ldx, V, Vp, U, Wp, Wpp, ld, n, k);
-        HBSD_LAUNCHED(s);
-        HBSD_TRY(k_active_flags(s, colp, k, s->mr_steps.p, st));
-        HBSD_CUDA(cudaMemcpyAsync(flags.data(), s->mr_steps.p, k * sizeof(int), cudaMemcpyDeviceToHost, st));
-        HBSD_CUDA(cudaStreamSynchronize(st));
-        act.clear();
-        for (int j = 0; j < k; ++j)
-            if (flags[j]) act.push_back(j);
+    if (flags[2]) return fail(HBSD_ERR_TIMEOUT, "minres: a grid barrier wait timed out");
+    int64_t tot = 0;
+    int mx = 0;
+    for (int v : h) { tot += v; mx = std::max(mx, v); }
+    if (trace) {
+        unsigned long long t[8];
+        HBSD_CUDA(cudaMemcpy(t, s->mr_stamps.p, sizeof(t), cudaMemcpyDeviceToHost));
+        std::fprintf(stderr, "[hbsd]   MINRES k %d grid %d steps max %d sum %lld | us: start %.0f A %.0f B %.0f C %.0f barriers %.0f\n",
+                     k, grid, mx, (long long)tot, t[0] * 1e-3, t[1] * 1e-3, t[2] * 1e-3, t[3] * 1e-3, t[4] * 1e-3);
     }
-    if (steps || total_steps) {
-        int* sp = steps ? steps : s->mr_steps.p;
-        k_mr_steps<<<ceil_div(k, 128), 128, 0, st>>>(colp, k, sp);
-        HBSD_LAUNCHED(s);
-        if (total_steps) {
-            std::vector<int> h(k);
-            HBSD_CUDA(cudaMemcpyAsync(h.data(), sp, k * sizeof(int), cudaMemcpyDeviceToHost, st));
-            HBSD_CUDA(cudaStreamSynchronize(st));
-            int64_t tot = 0;
-            for (int v : h) tot += v;
-            *total_steps = tot;
-        }
-    }
+    s->stats.minres_spmm_cols += tot + k;   // the start SpMM plus one column per step
+    if (total_steps) *total_steps = tot;
     return 0;
 }
 
