@@ -223,6 +223,7 @@ struct Session {
     DBuf<int> mr_any, mr_steps; // grid barrier + error flag; per-column step counts
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel
+    double dbg_rr_kernel_ms = 0.0, dbg_rr_host_ms = 0.0, dbg_rr_wake_ms = 0.0;   // Rayleigh-Ritz timing accounting (HBSD_RRDBG)
     int mr_blk_grid = 0;
     // mixed-precision preconditioner buffers (FP32 scaled R and P)
     DBuf<float> r32, p32, xa32, ra32, sh32;

@@ -336,7 +336,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                          sizeof(T) == 4 ? "fp32" : "fp64", iters + 1, hist.back(), p, a,
                          count_nonfinite(C.HR.p, (int64_t)q * q, st), count_nonfinite(C.SR.p, (int64_t)q * q, st));
         ti = tm.begin(StepTimer::RR, st);
+        const auto h0 = std::chrono::steady_clock::now();
         HBSD_TRY(rayleigh_ritz_cluster(S, C.HR.p, C.SR.p, q, w, C.theta.p, C.W.p, info, st, drop_tol));
+        S->dbg_rr_host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h0).count();
         tm.end(ti, st);
         stt.rr_fallbacks += info[0];
         if (trace_on())
@@ -442,6 +444,9 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     stt.t_local_ms = tm.acc[StepTimer::LOCAL];
     stt.t_gram_ms = tm.acc[StepTimer::GRAM];
     stt.t_rr_ms = tm.acc[StepTimer::RR];
+    if (std::getenv("HBSD_RRDBG"))
+        std::fprintf(stderr, "[hbsd] RR step timer %.1f ms, kernel events %.1f ms, host call %.1f ms, sync-to-next-event %.1f ms\n",
+                     tm.acc[StepTimer::RR], S->dbg_rr_kernel_ms, S->dbg_rr_host_ms, S->dbg_rr_wake_ms);
     stt.t_update_ms = tm.acc[StepTimer::UPDATE];
     if (lam_dev) {
         k_shift_add<<<ceil_div(m, 128), 128, 0, st>>>(C.E.p, m, S->sigma0, lam_dev);
