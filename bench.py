@@ -264,7 +264,8 @@ def main():
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "nev": nev, "precision": args.precision,
                        "iters": st["iters"], "iters_fp64": st["iters_fp64"], "t_factor_ms": st["t_factor_ms"],
-                       "nnz_L": st["nnz_L"], "res_max": st["res_max"],
+                       "nnz_L": st["nnz_L"], "res_max": st["res_max"], "rr_fallbacks": st["rr_fallbacks"],
+                       "minres_steps": st["minres_steps"],
                        "l2": "working set > L2 (factor %.0f MB + matrix %.0f MB)" % (st["nnz_L"] * 8e-6, p.nnz * 20e-6),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "roofline": roof, "e2e": e2e, "gpu_launches": int(sum(s["gpu_launches"] for s in stats)),

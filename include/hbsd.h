@@ -234,6 +234,17 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
  * q x k matrix W (row-major, ld k, device), k <= q. */
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream);
 
+/* Double-float forms of hbsd_gram and hbsd_update, the ones the mixed form (HBSD_PRECISION_MIXED)
+ * runs: FP64 inputs and outputs, products and short sums in pairs of floats (about 48 bits per
+ * term, TwoProd / TwoSum), the Gram sums accumulated in FP64 across 128-row tiles.  hbsd_gram_df64
+ * computes the entries a <= b of Z^T ZH and Z^T ZS and mirrors them (no averaging).  Arguments,
+ * layouts and errors as hbsd_gram / hbsd_update; FP64 values enter the products with ~47 bits
+ * above 2^-96 in magnitude, at least 24 bits down to 2^-126, and as zero below; q * (k + 8 * max(1, min(256 / min(k, 256), 8))) pairs must fit in 220 KB of
+ * shared memory for hbsd_update_df64 (HBSD_ERR_ARG otherwise). */
+int hbsd_gram_df64(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
+                   int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream);
+int hbsd_update_df64(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream);
+
 /* The start-block generator used when hbsd_solve gets X0 = NULL (host only, no GPU needed):
  * count standard normals from SplitMix64 (Steele, Lea & Flood 2014) used as a counter-based
  * generator (draw t = mix(key + (t+1) * 0x9E3779B97F4A7C15), key = mix((seed ^ stream *

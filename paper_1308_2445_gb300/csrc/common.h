@@ -189,6 +189,12 @@ int update2(Session* s, T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, in
             const double* W, int k, cudaStream_t st);
 int rayleigh_ritz(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
                   double* W, int* info_host, cudaStream_t st);
+// double-float (hi + lo float pairs) forms of the Gram and update products, for the mixed form
+int gram2_df64(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
+               const double* H0, int64_t ldh0, const double* H1, int64_t ldh1, const double* S0, int64_t lds0,
+               const double* S1, int64_t lds1, int64_t n, double* HR, double* SR, cudaStream_t st);
+int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
+                 const double* W, int k, cudaStream_t st, bool split_w);
 int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
                           double* W, int* info_host, cudaStream_t st, double drop_tol = 0.0);
 template <class T>
@@ -223,6 +229,8 @@ struct Session {
     DBuf<int> mr_any, mr_steps; // grid barrier + error flag; per-column step counts
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel
+    DBuf<float2> df_w;          // double-float copy of the Rayleigh-Ritz coefficients W
+    bool opt_df64 = true;       // mixed form: Gram and update in double-float (HBSD_NO_DF64=1 turns off)
     double dbg_rr_kernel_ms = 0.0, dbg_rr_host_ms = 0.0, dbg_rr_wake_ms = 0.0;   // Rayleigh-Ritz timing accounting (HBSD_RRDBG)
     int mr_blk_grid = 0;
     // mixed-precision preconditioner buffers (FP32 scaled R and P)

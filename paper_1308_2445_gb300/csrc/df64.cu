@@ -1,0 +1,277 @@
+// Double-float ("df64") block products for the mixed form: steps 8 (Gram) and 10-11 (update).
+//
+// GB300 issues FP32 FMAs at 128 lanes per clock per SM and FP64 FMAs at 2, so a product whose
+// FP64 rate is the bound runs faster as pairs of floats (hi + lo, Dekker 1971; Knuth's
+// TwoSum): a product of two pairs is hi*hi exactly (TwoProd by FMA) plus the two cross terms,
+// and the running sum is a pair kept by TwoSum and renormalised every few terms.  About 48
+// significant bits per term; the Gram sums keep FP64 across 128-row tiles, so their long sums
+// carry FP64 accuracy.
+//
+// Operands are split without the FP64 pipe: hi = the FP64 value truncated to 24 bits, built
+// from its sign, exponent and top mantissa bits; lo = the remaining 29 mantissa bits converted
+// by the integer-to-float unit and scaled by the exponent.  The pair carries ~47 bits for
+// magnitudes above 2^-96; below that lo is an FP32 subnormal and the precision falls towards
+// 24 bits, and magnitudes below 2^-126 enter as zero (all far below the method's quantities).
+#include "common.h"
+
+namespace hbsd {
+
+namespace {
+
+__device__ __forceinline__ float2 split_d(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32);
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7FFu);
+    float h = 0.f, l = 0.f;
+    if (e >= 897) {
+        if (e > 1150) {
+            h = __uint_as_float(sign | 0x7F800000u);   // beyond the FP32 range: +-inf, never silent
+        } else {
+            const unsigned top23 = ((hi32 & 0xFFFFFu) << 3) | (unsigned)((b >> 29) & 7u);
+            h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | top23);
+            const unsigned low29 = (unsigned)(b & 0x1FFFFFFFull);
+            if (e >= 949) {   // lo = low29 * 2^(e - 1075), the scale a normal float
+                l = __fmul_rn(__uint_as_float(sign | ((unsigned)(e - 948) << 23)), __uint2float_rn(low29));
+            } else {          // the same in two normal-range factors, 2^-64 and 2^(e - 1011)
+                l = __fmul_rn(__fmul_rn(__uint2float_rn(low29), __uint_as_float(sign | (63u << 23))),
+                              __uint_as_float((unsigned)(e - 884) << 23));
+            }
+        }
+    }
+    return make_float2(h, l);
+}
+
+// (sh, sl) += a * b for double-float a, b
+// (the _rn intrinsics are never contracted into FMAs, which would break the error-free steps)
+__device__ __forceinline__ void dfma(const float2 a, const float2 b, float& sh, float& sl) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);   // rounding error of p, exact
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float t = __fadd_rn(sh, p);   // TwoSum(sh, p)
+    const float bp = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+    sh = t;
+}
+
+__device__ __forceinline__ void renorm(float& sh, float& sl) {   // FastTwoSum, |sh| >= |sl|
+    const float t = __fadd_rn(sh, sl);
+    sl = __fsub_rn(sl, __fsub_rn(t, sh));
+    sh = t;
+}
+
+__device__ __forceinline__ double to_d(float sh, float sl) { return __dadd_rn((double)sh, (double)sl); }
+
+struct Seg2d {
+    const double* p0;
+    int64_t ld0;
+    int q0;
+    const double* p1;
+    int64_t ld1;
+    __device__ __forceinline__ double at(int64_t i, int c) const {
+        return c < q0 ? p0[i * ld0 + c] : p1[i * ld1 + (c - q0)];
+    }
+};
+
+constexpr int GT = 32;          // output tile edge
+constexpr int GR = 32;          // rows per shared-memory stage
+constexpr int GFLUSH = 4;       // stages per FP64 flush (128 rows)
+
+// One CTA: a 32 x 32 tile (a-block <= b-block) of Z^T H Z and Z^T S Z over a chunk of rows.
+__global__ void __launch_bounds__(256) k_gram_df64(Seg2d Z, Seg2d ZH, Seg2d ZS, int q,
+                                                   int64_t n, int64_t rows_per_chunk, double* __restrict__ partial) {
+    __shared__ float2 sz[GR][GT + 1], sh[GR][GT + 1], ss[GR][GT + 1];
+    // tile pair (ta <= tb) from the packed-triangle index of the block
+    const int pidx = blockIdx.x;
+    int tb = (int)((sqrtf(8.0f * (float)pidx + 1.0f) - 1.0f) * 0.5f);
+    while ((tb + 1) * (tb + 2) / 2 <= pidx) ++tb;
+    while (tb * (tb + 1) / 2 > pidx) --tb;
+    const int ta = pidx - tb * (tb + 1) / 2;
+    const int a0 = ta * GT, b0 = tb * GT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 2 x 2 outputs each
+    const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
+    const int64_t r1 = min(n, r0 + rows_per_chunk);
+    double aH[2][2] = {{0, 0}, {0, 0}}, aS[2][2] = {{0, 0}, {0, 0}};
+    float hH[2][2], lH[2][2], hS[2][2], lS[2][2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) { hH[u][v] = lH[u][v] = hS[u][v] = lS[u][v] = 0.f; }
+    int stage = 0;
+    for (int64_t i0 = r0; i0 < r1; i0 += GR, ++stage) {
+        for (int t = threadIdx.x; t < GR * GT; t += 256) {
+            const int rr = t / GT, cc = t % GT;
+            const int64_t i = i0 + rr;
+            const bool ok = i < r1;
+            sz[rr][cc] = split_d((ok && a0 + cc < q) ? Z.at(i, a0 + cc) : 0.0);
+            sh[rr][cc] = split_d((ok && b0 + cc < q) ? ZH.at(i, b0 + cc) : 0.0);
+            ss[rr][cc] = split_d((ok && b0 + cc < q) ? ZS.at(i, b0 + cc) : 0.0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < GR; ++rr) {
+            const float2 z0 = sz[rr][ty * 2], z1 = sz[rr][ty * 2 + 1];
+            const float2 h0 = sh[rr][tx * 2], h1 = sh[rr][tx * 2 + 1];
+            const float2 s0 = ss[rr][tx * 2], s1 = ss[rr][tx * 2 + 1];
+            dfma(z0, h0, hH[0][0], lH[0][0]); dfma(z0, h1, hH[0][1], lH[0][1]);
+            dfma(z1, h0, hH[1][0], lH[1][0]); dfma(z1, h1, hH[1][1], lH[1][1]);
+            dfma(z0, s0, hS[0][0], lS[0][0]); dfma(z0, s1, hS[0][1], lS[0][1]);
+            dfma(z1, s0, hS[1][0], lS[1][0]); dfma(z1, s1, hS[1][1], lS[1][1]);
+            if ((rr & 7) == 7) {
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) { renorm(hH[u][v], lH[u][v]); renorm(hS[u][v], lS[u][v]); }
+            }
+        }
+        __syncthreads();
+        if ((stage % GFLUSH) == GFLUSH - 1 || i0 + GR >= r1) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    aH[u][v] += to_d(hH[u][v], lH[u][v]);
+                    aS[u][v] += to_d(hS[u][v], lS[u][v]);
+                    hH[u][v] = lH[u][v] = hS[u][v] = lS[u][v] = 0.f;
+                }
+        }
+    }
+    const int64_t qq = (int64_t)q * q;
+    double* ph = partial + (int64_t)blockIdx.y * 2 * qq;
+    double* ps = ph + qq;
+    for (int u = 0; u < 2; ++u)
+        for (int v = 0; v < 2; ++v) {
+            const int a = a0 + ty * 2 + u, b = b0 + tx * 2 + v;
+            if (a < q && b < q) {
+                ph[(int64_t)a * q + b] = aH[u][v];
+                ps[(int64_t)a * q + b] = aS[u][v];
+            }
+        }
+}
+
+// Sum the chunks in order; entry (a, b), a <= b, of Z^T X Z is used for both (a, b) and (b, a).
+__global__ void k_gram_final_upper(const double* __restrict__ partial, int nchunks, int q, double* __restrict__ HR,
+                                   double* __restrict__ SR) {
+    const int64_t qq = (int64_t)q * q;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= qq) return;
+    int a = (int)(idx / q), b = (int)(idx % q);
+    if (a > b) { const int t = a; a = b; b = t; }
+    const int64_t src = (int64_t)a * q + b;
+    double h = 0, s = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const double* ph = partial + (int64_t)c * 2 * qq;
+        h += ph[src];
+        s += ph[qq + src];
+    }
+    HR[idx] = h;
+    SR[idx] = s;
+}
+
+// W (q x k, FP64) -> pairs
+__global__ void k_split_w(const double* __restrict__ W, int64_t cnt, float2* __restrict__ W2) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += (int64_t)gridDim.x * blockDim.x)
+        W2[t] = split_d(W[t]);
+}
+
+// Z0(:, 0:k) <- [Z0 Z1] W.  Threads are flattened over (row group, column): kc = min(k, 256)
+// columns per pass, ng = min(256 / kc, 8) row groups of UR rows, so a CTA covers ng * UR rows;
+// W (q x k pairs) and the rows (split) are staged in shared memory.
+constexpr int UR = 8;
+
+__global__ void __launch_bounds__(256) k_update_df64(double* __restrict__ Z0, int64_t ld0, int q0,
+                                                     const double* __restrict__ Z1, int64_t ld1, int q1, int64_t n,
+                                                     const float2* __restrict__ W2, int k, int ng) {
+    extern __shared__ __align__(16) float2 smu[];
+    const int q = q0 + q1;
+    const int rows = ng * UR;
+    float2* zrow = smu;                      // [rows][q]
+    float2* wsm = smu + (int64_t)rows * q;   // [q][k]
+    const int64_t i0 = (int64_t)blockIdx.x * rows;
+    for (int t = threadIdx.x; t < rows * q; t += 256) {
+        const int rr = t / q, c = t % q;
+        const int64_t i = i0 + rr;
+        double v = 0.0;
+        if (i < n) v = c < q0 ? Z0[i * ld0 + c] : Z1[i * ld1 + (c - q0)];
+        zrow[t] = split_d(v);
+    }
+    for (int t = threadIdx.x; t < q * k; t += 256) wsm[t] = W2[t];
+    __syncthreads();
+    const int kc = min(k, 256);
+    const int g = threadIdx.x / kc, cl = threadIdx.x % kc;
+    if (g >= ng) return;
+    for (int jb = 0; jb < k; jb += kc) {
+        const int j = jb + cl;
+        if (j >= k) continue;
+        float ah[UR], al[UR];
+#pragma unroll
+        for (int u = 0; u < UR; ++u) { ah[u] = 0.f; al[u] = 0.f; }
+        const float2* zr = zrow + (int64_t)g * UR * q;
+        for (int c = 0; c < q; ++c) {
+            const float2 wv = wsm[c * k + j];
+#pragma unroll
+            for (int u = 0; u < UR; ++u) dfma(zr[u * q + c], wv, ah[u], al[u]);
+            if ((c & 7) == 7) {
+#pragma unroll
+                for (int u = 0; u < UR; ++u) renorm(ah[u], al[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int64_t i = i0 + g * UR + u;
+            if (i < n) Z0[i * ld0 + j] = to_d(ah[u], al[u]);
+        }
+    }
+}
+
+}  // namespace
+
+int gram2_df64(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
+               const double* H0, int64_t ldh0, const double* H1, int64_t ldh1, const double* S0, int64_t lds0,
+               const double* S1, int64_t lds1, int64_t n, double* HR, double* SR, cudaStream_t st) {
+    const int q = q0 + q1;
+    if (q <= 0) return 0;
+    const int tb = ceil_div(q, GT);
+    const int ntile = tb * (tb + 1) / 2;
+    // chunks of rows: enough CTAs for every SM several times over, a multiple of the stage height
+    int nch = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, ceil_div(152 * 8, ntile)));
+    int64_t rpc = round_up((n + nch - 1) / nch, GR);
+    nch = (int)((n + rpc - 1) / rpc);
+    HBSD_TRY(s->ws.alloc((size_t)nch * 2 * q * q + 64));
+    Seg2d Z{Z0, ld0, q0, Z1, ld1}, ZH{H0, ldh0, q0, H1, ldh1}, ZS{S0, lds0, q0, S1, lds1};
+    k_gram_df64<<<dim3(ntile, nch), 256, 0, st>>>(Z, ZH, ZS, q, n, rpc, s->ws.p);
+    HBSD_LAUNCHED(s);
+    const int64_t qq = (int64_t)q * q;
+    k_gram_final_upper<<<ceil_div(qq, 256), 256, 0, st>>>(s->ws.p, nch, q, HR, SR);
+    HBSD_LAUNCHED(s);
+    return 0;
+}
+
+int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
+                 const double* W, int k, cudaStream_t st, bool split_w) {
+    const int q = q0 + q1;
+    if (k > q0) return fail(HBSD_ERR_ARG, "update: k must not exceed the first segment width");
+    const int kc = std::min(k, 256);
+    const int ng = std::max(1, std::min(256 / kc, 8));
+    const int rows = ng * UR;
+    const size_t smem = ((size_t)rows * q + (size_t)q * k) * sizeof(float2);
+    if (smem > 220 * 1024) return fail(HBSD_ERR_ARG, "update: q too large for the double-float kernel");
+    static size_t attr = 0;
+    if (smem > 48 * 1024 && smem > attr) {
+        HBSD_CUDA(cudaFuncSetAttribute(k_update_df64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = smem;
+    }
+    HBSD_TRY(s->df_w.alloc((size_t)q * k));
+    if (split_w) {
+        const int64_t cnt = (int64_t)q * k;
+        k_split_w<<<ceil_div(cnt, 256), 256, 0, st>>>(W, cnt, s->df_w.p);
+        HBSD_LAUNCHED(s);
+    }
+    k_update_df64<<<ceil_div(n, rows), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, s->df_w.p, k, ng);
+    HBSD_LAUNCHED(s);
+    return 0;
+}
+
+}  // namespace hbsd

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <limits>
+#include <type_traits>
 
 #include "common.h"
 
@@ -164,6 +165,27 @@ struct StepTimer {
     }
 };
 
+// Gram and update of the loop: the mixed form computes them in double-float arithmetic on the
+// FP32 pipes (FP64 accumulation across 128-row tiles for the Gram sums), the FP64 form in FP64.
+template <class T>
+static int gram_step(Session* S, bool df, const T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1,
+                     const T* H0, int64_t ldh0, const T* H1, int64_t ldh1, const T* S0, int64_t lds0, const T* S1,
+                     int64_t lds1, int64_t n, double* HR, double* SR, cudaStream_t st) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (df) return gram2_df64(S, Z0, ld0, q0, Z1, ld1, q1, H0, ldh0, H1, ldh1, S0, lds0, S1, lds1, n, HR, SR, st);
+    }
+    return gram2<T>(S, Z0, ld0, q0, Z1, ld1, q1, H0, ldh0, H1, ldh1, S0, lds0, S1, lds1, n, HR, SR, st);
+}
+template <class T>
+static int update_step(Session* S, bool df, T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1, int64_t n,
+                       const double* W, int k, cudaStream_t st, bool first) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (df) return update2_df64(S, Z0, ld0, q0, Z1, ld1, q1, n, W, k, st, first);
+    }
+    (void)first;
+    return update2<T>(S, Z0, ld0, q0, Z1, ld1, q1, n, W, k, st);
+}
+
 // ---- per-solve buffers -----------------------------------------------------------------------
 template <class T>
 struct SolveBufs {
@@ -204,13 +226,14 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     // FP32 phase: Gram entries carry ~1e-7 relative noise, so a scaled-S_R pivot below 1e-6 is
     // treated as a dependent direction and dropped; FP64 keeps the reading of the paper (R13).
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
+    const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
     // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
     ti = tm.begin(StepTimer::MATVEC, st);
     HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
     tm.end(ti, st);
     stt.matvec_cols += w;
     ti = tm.begin(StepTimer::GRAM, st);
-    HBSD_TRY(gram2<T>(S, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, B.PsiH.p, ldw, (const T*)nullptr, 0, B.PsiS.p,
+    HBSD_TRY(gram_step<T>(S, dfp, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, B.PsiH.p, ldw, (const T*)nullptr, 0, B.PsiS.p,
                       ldw, (const T*)nullptr, 0, n, C.HR.p, C.SR.p, st));
     tm.end(ti, st);
     if (trace_on())
@@ -222,9 +245,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     tm.end(ti, st);
     stt.rr_fallbacks += info[0];
     ti = tm.begin(StepTimer::UPDATE, st);
-    HBSD_TRY(update2<T>(S, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st));
-    HBSD_TRY(update2<T>(S, B.PsiH.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st));
-    HBSD_TRY(update2<T>(S, B.PsiS.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st));
+    HBSD_TRY(update_step<T>(S, dfp, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, true));
+    HBSD_TRY(update_step<T>(S, dfp, B.PsiH.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
+    HBSD_TRY(update_step<T>(S, dfp, B.PsiS.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
     tm.end(ti, st);
     HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
     HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
@@ -327,7 +350,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         // step 8
         const int q = w + p;
         ti = tm.begin(StepTimer::GRAM, st);
-        HBSD_TRY(gram2<T>(S, B.Psi.p, ldw, w, B.P.p, ldp, p, B.PsiH.p, ldw, B.PH.p, ldp, B.PsiS.p, ldw, B.PS.p, ldp,
+        HBSD_TRY(gram_step<T>(S, dfp, B.Psi.p, ldw, w, B.P.p, ldp, p, B.PsiH.p, ldw, B.PH.p, ldp, B.PsiS.p, ldw, B.PS.p, ldp,
                           n, C.HR.p, C.SR.p, st));
         tm.end(ti, st);
         // step 9
@@ -346,9 +369,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                          count_nonfinite(C.theta.p, w, st), count_nonfinite(C.W.p, (int64_t)q * w, st));
         // steps 10-11
         ti = tm.begin(StepTimer::UPDATE, st);
-        HBSD_TRY(update2<T>(S, B.Psi.p, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st));
-        HBSD_TRY(update2<T>(S, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st));
-        HBSD_TRY(update2<T>(S, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st));
+        HBSD_TRY(update_step<T>(S, dfp, B.Psi.p, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st, true));
+        HBSD_TRY(update_step<T>(S, dfp, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st, false));
+        HBSD_TRY(update_step<T>(S, dfp, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st, false));
         tm.end(ti, st);
         Eprev = E;
         HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
@@ -530,6 +553,10 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
     S->n = H->n;
     S->nnz = H->nnz;
     S->opt = *opt;
+    {
+        const char* e = std::getenv("HBSD_NO_DF64");
+        S->opt_df64 = !(e && e[0] && e[0] != '0');
+    }
     S->sigma0 = std::isnan(opt->sigma0) ? opt->sigma_bar : opt->sigma0;
     if (stream) {
         S->stream = (cudaStream_t)stream;
@@ -734,6 +761,18 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
     if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
     return update2<double>(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
+}
+
+int hbsd_gram_df64(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
+                   int64_t n, int q, double* HR, double* SR, void* stream) {
+    if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    return gram2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR,
+                      SR, (cudaStream_t)stream);
+}
+
+int hbsd_update_df64(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
+    if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
+    return update2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

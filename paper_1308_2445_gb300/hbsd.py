@@ -90,6 +90,8 @@ _SIGS = {
     "hbsd_gram_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int, _P, _P, _P]),
     "hbsd_rayleigh_ritz": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "hbsd_update": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int, _P]),
+    "hbsd_gram_df64": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int, _P, _P, _P]),
+    "hbsd_update_df64": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int, _P]),
     "hbsd_probe_peak": (C.c_int, [C.c_int, _P, C.POINTER(C.c_double)]),
     "hbsd_seed_normals": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int64, _D]),
 }
@@ -279,6 +281,18 @@ def rayleigh_ritz(HR, SR, k, theta, W, info, stream=0):
 def update(Z, W, k, stream=0):
     check(lib().hbsd_update(ptr(Z), ld(Z), Z.shape[0], W.shape[0], ptr(W), k, C.c_void_p(stream) if stream else None),
           "hbsd_update")
+
+
+def gram_df64(Z, ZH, ZS, HR, SR, stream=0):
+    """Double-float Gram of the mixed form (upper entries, mirrored)."""
+    check(lib().hbsd_gram_df64(ptr(Z), ld(Z), ptr(ZH), ld(ZH), ptr(ZS), ld(ZS), Z.shape[0], Z.shape[1], ptr(HR),
+                               ptr(SR), C.c_void_p(stream) if stream else None), "hbsd_gram_df64")
+
+
+def update_df64(Z, W, k, stream=0):
+    """Double-float block update of the mixed form: Z(:, :k) = Z W."""
+    check(lib().hbsd_update_df64(ptr(Z), ld(Z), Z.shape[0], W.shape[0], ptr(W), k,
+                                 C.c_void_p(stream) if stream else None), "hbsd_update_df64")
 
 
 def probe_peak(which, stream=0):

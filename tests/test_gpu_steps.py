@@ -239,6 +239,64 @@ def test_update(q, k, n):
     assert np.array_equal(out[:, k:], Z[:, k:])
 
 
+# ---- double-float forms (mixed precision): products of hi + lo float pairs, FP64 across
+# 128-row tiles.  Bound: each entry within c * 2^-44 of |Z|^T |ZH| (the sum of the absolute
+# products), a few times the FP64 summation bound at these lengths; an FP32-accurate product
+# (2^-24) would miss it by ~10^6.
+@pytest.mark.parametrize("q,n", [(19, 646), (35, 4000), (135, 1000), (70, 33), (135, 47620)])
+def test_gram_df64(q, n):
+    Z = pi.seed_normal_block(q, n, q)
+    ZH = pi.seed_normal_block(q + 1, n, q)
+    ZS = pi.seed_normal_block(q + 2, n, q)
+    # columns of very different magnitudes, and a near-cancelling part, as in the search blocks
+    sc = np.logspace(-6, 6, q)
+    Z = Z * sc
+    ZH = ZH / sc + 1e3 * Z
+    HR = torch.zeros(q, q, dtype=torch.float64, device="cuda")
+    SR = torch.zeros(q, q, dtype=torch.float64, device="cuda")
+    hb().gram_df64(dev(Z), dev(ZH), dev(ZS), HR, SR)
+    h, sr = host(HR), host(SR)
+    exH, exS = Z.T @ ZH, Z.T @ ZS
+    bH, bS = np.abs(Z).T @ np.abs(ZH), np.abs(Z).T @ np.abs(ZS)
+    iu = np.triu_indices(q)
+    assert np.all(np.abs(h - exH)[iu] <= 2.0 ** -44 * bH[iu] + 1e-300)
+    assert np.all(np.abs(sr - exS)[iu] <= 2.0 ** -44 * bS[iu] + 1e-300)
+    assert np.array_equal(h, h.T) and np.array_equal(sr, sr.T)
+
+
+@pytest.mark.parametrize("q,k,n", [(19, 19, 646), (35, 19, 1000), (135, 71, 3001), (8, 3, 5), (282, 30, 700)])
+def test_update_df64(q, k, n):
+    Z = pi.seed_normal_block(q * 3, n, q) * np.logspace(-4, 4, q)
+    W = pi.seed_normal_block(q * 5, q, k)
+    Zd = dbuf(n, q)
+    Zd.copy_(dev(Z))
+    hb().update_df64(Zd, dense(W), k)
+    out = host(Zd)
+    bound = np.abs(Z) @ np.abs(W)
+    assert np.all(np.abs(out[:, :k] - Z @ W) <= 2.0 ** -44 * bound + 1e-300)
+    assert np.array_equal(out[:, k:], Z[:, k:])
+
+
+def test_df64_split_edge_values():
+    # zeros, signs, magnitudes from 1e-28 to 1e30 and exact powers of two go through to ~2^-47;
+    # magnitudes below 2^-126 enter as zero; in between (subnormal lo) at least FP32 precision
+    v = np.array([0.0, -0.0, 1.0, -1.0, 2.0 ** 100, -(2.0 ** -100), 1e30, -1e-28, 3.141592653589793,
+                  1.0 + 2.0 ** -40, 1e-39, -1e-300, 2.0 ** -80 * 3.141592653589793, -1e-35])
+    q = v.size
+    Z = np.zeros((1, q))
+    Z[0] = v
+    W = np.eye(q)
+    Zd = dbuf(1, q)
+    Zd.copy_(dev(Z))
+    hb().update_df64(Zd, dense(W), q)
+    out = host(Zd)[0]
+    full = np.abs(v) >= 2.0 ** -96
+    mid = (np.abs(v) >= 2.0 ** -126) & ~full
+    assert np.all(np.abs(out[full] - v[full]) <= 2.0 ** -46 * np.abs(v[full]))
+    assert np.all(np.abs(out[mid] - v[mid]) <= 2.0 ** -23 * np.abs(v[mid]))
+    assert np.all(out[np.abs(v) < 2.0 ** -126] == 0.0)
+
+
 def test_minres_against_oracle(mid):
     p, s = mid
     Hs, S, _ = L.make_shifted(p)
