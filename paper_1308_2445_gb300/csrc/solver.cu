@@ -227,6 +227,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     // treated as a dependent direction and dropped; FP64 keeps the reading of the paper (R13).
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
     const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
+    bool certified = false;   // Psi_H, Psi_S freshly recomputed in FP64 (mixed form)
     // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
     ti = tm.begin(StepTimer::MATVEC, st);
     HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
@@ -271,7 +272,23 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         }
         stt.res_max = rmax;
         hist.push_back(rmax);
-        if (rmax <= rule.tol) { *converged = true; break; }
+        if (rmax <= rule.tol) {
+            // the mixed form carries Psi_H, Psi_S through double-float updates: before accepting,
+            // recompute them from Psi in FP64 and test the residual again (a failing test just
+            // continues the iteration from the recomputed blocks)
+            if (dfp && !certified) {
+                certified = true;
+                ti = tm.begin(StepTimer::MATVEC, st);
+                HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+                tm.end(ti, st);
+                stt.matvec_cols += w;
+                hist.pop_back();
+                continue;
+            }
+            *converged = true;
+            break;
+        }
+        certified = false;
         if (iters >= rule.max_iters) break;
         if (rule.stagnation && (int)hist.size() > rule.window) {
             double best_before = hist[0];
