@@ -234,6 +234,69 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
  * q x k matrix W (row-major, ld k, device), k <= q. */
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream);
 
+/* ---- Served form (continuous batching of solve requests on one GPU) ------------------------
+ *
+ * A server runs up to max_slots requests at a time, each on its own CUDA stream, so the kernels
+ * of different solves overlap on the device.  Requests are taken in arrival order, except that
+ * one that cannot run yet (its session busy with an earlier request, or not enough device
+ * memory under hbm_budget_bytes) does not hold back later ones.  A new problem is copied at
+ * submission and factorised when it runs; its session (matrix, factor, last block) then stays
+ * resident for follow-up requests (SCF steps, Sec. 3: new H values on the same pattern, warm
+ * start from the previous block; the factor of the session's first H is kept, reading R2).
+ * Idle sessions are evicted least-recently-used first when memory is short, or released by the
+ * caller.  Device-memory use is estimated per problem from n, nnz and nev.  All functions are
+ * thread-safe. */
+typedef struct {
+    size_t hbm_budget_bytes;  /* device memory the server may hold; 0 = 80% of the free memory */
+    int max_slots;            /* requests running at once (1..64), default 4                   */
+} hbsd_server_opts;
+
+typedef struct {
+    /* new problem: H, S, lb and opt (copied at submission); session_id = -1 */
+    const hbsd_csr* H;
+    const hbsd_csr* S;
+    const hbsd_local_blocks* lb;
+    const hbsd_options* opt;
+    /* follow-up: session_id >= 0 (from an earlier result); H_val = new H values (nnz
+     * doubles, copied) or NULL to keep H */
+    int64_t session_id;
+    const double* H_val;
+    int nev;
+    double tol;
+    const double* X0;   /* host, n x (nev + m0) row-major, copied; or NULL (seeded start) */
+    int warm;           /* follow-up only: start from the session's last block (X0 = NULL) */
+} hbsd_request;
+
+typedef struct {
+    uint64_t ticket;
+    int status;          /* HBSD_OK, HBSD_NOT_CONVERGED or an error code of the solve       */
+    int iters;
+    int64_t session_id;  /* the session the request ran in (-1 if a new problem failed)     */
+    double res_max;      /* final max relative residual                                     */
+    double latency_ms;   /* submission to completion                                        */
+    double queue_ms;     /* submission to start                                             */
+    double run_ms;       /* start to completion (factorisation included for a new problem)  */
+} hbsd_result;
+
+typedef struct hbsd_server hbsd_server;
+
+void hbsd_server_opts_default(hbsd_server_opts* opts);
+/* Starts the worker threads.  HBSD_ERR_ARG for max_slots outside [1, 64]. */
+int hbsd_server_create(const hbsd_server_opts* opts, hbsd_server** out);
+/* Queues a request and returns at once with its ticket.  lambda_out (nev doubles) and X_out
+ * (n x nev, row-major, or NULL) are host buffers the caller keeps valid until the result has
+ * been polled.  HBSD_ERR_OOM if the problem alone exceeds the memory budget, HBSD_ERR_ARG for
+ * an unknown session or malformed input. */
+int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, double* X_out, uint64_t* ticket);
+/* HBSD_BUSY while the request is queued or running; HBSD_OK once, with the result (the ticket
+ * is then forgotten); HBSD_ERR_ARG for an unknown ticket. */
+int hbsd_poll(hbsd_server* sv, uint64_t ticket, hbsd_result* out);
+/* Frees an idle session now (HBSD_BUSY while a request of it runs). */
+int hbsd_session_release(hbsd_server* sv, int64_t session_id);
+/* Waits for the running requests, stops the workers and frees every session; queued requests
+ * are dropped. */
+void hbsd_server_destroy(hbsd_server* sv);
+
 /* Double-float forms of hbsd_gram and hbsd_update, the ones the mixed form (HBSD_PRECISION_MIXED)
  * runs: FP64 inputs and outputs, products and short sums in pairs of floats (about 48 bits per
  * term, TwoProd / TwoSum), the Gram sums accumulated in FP64 across 128-row tiles.  hbsd_gram_df64

@@ -205,6 +205,17 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
                  int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st);
 
 // ---- session -----------------------------------------------------------------------
+// Block buffers of one solve (steps 1-11), kept in the session between solves.
+template <class T>
+struct SolveBufs {
+    DBuf<T> Psi, PsiH, PsiS, P, PH, PS, RU, Xa, Ra, shifts;
+};
+
+struct SolveCommon {
+    DBuf<double> E, res, HR, SR, W, theta;
+    DBuf<int> Ulist, Llist, steps;
+};
+
 struct Session {
     int64_t n = 0, nnz = 0;
     hbsd_options opt{};
@@ -230,6 +241,9 @@ struct Session {
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel
     DBuf<float2> df_w;          // double-float copy of the Rayleigh-Ritz coefficients W
+    SolveBufs<double> sb;       // per-solve blocks, resident (grow only)
+    SolveCommon sc;
+    DBuf<double> io_x0, io_lam, io_x;   // host API staging of X0, lambda, X
     bool opt_df64 = true;       // mixed form: Gram and update in double-float (HBSD_NO_DF64=1 turns off)
     double dbg_rr_kernel_ms = 0.0, dbg_rr_host_ms = 0.0, dbg_rr_wake_ms = 0.0;   // Rayleigh-Ritz timing accounting (HBSD_RRDBG)
     int mr_blk_grid = 0;

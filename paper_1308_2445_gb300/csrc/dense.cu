@@ -355,8 +355,14 @@ int update2(Session* s, T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, in
     if (k > q0) return fail(HBSD_ERR_ARG, "update: k must not exceed the first segment width");
     const size_t smem = (size_t)16 * q * sizeof(T);
     if (smem > 200 * 1024) return fail(HBSD_ERR_ARG, "update: q too large");
-    if (smem > 48 * 1024)
-        HBSD_CUDA(cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {   // the cap, once: concurrent sessions never lower it under each other
+        static std::once_flag once;
+        static cudaError_t e = cudaSuccess;
+        std::call_once(once, [] {
+            e = cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        });
+        HBSD_CUDA(e);
+    }
     k_update<T><<<ceil_div(n, 16), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, W, k);
     HBSD_LAUNCHED(s);
     return 0;
@@ -743,8 +749,14 @@ int rayleigh_ritz(Session* s, const double* HR, const double* SR, int q, int k, 
     HBSD_TRY(s->rr_info.alloc(4));
     const size_t smem = (size_t)(5 * q + 40) * sizeof(double) + (size_t)(2 * q + 4) * sizeof(int);
     if (smem > 200 * 1024) return fail(HBSD_ERR_ARG, "rayleigh_ritz: q too large");
-    if (smem > 48 * 1024)
-        HBSD_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) {   // the cap, once (see update2)
+        static std::once_flag once;
+        static cudaError_t e = cudaSuccess;
+        std::call_once(once, [] {
+            e = cudaFuncSetAttribute(k_rayleigh_ritz, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        });
+        HBSD_CUDA(e);
+    }
     k_rayleigh_ritz<<<1, RR_THREADS, smem, st>>>(HR, SR, q, k, theta, W, s->rr_ws.p, s->rr_info.p);
     HBSD_LAUNCHED(s);
     int info[4] = {0, 0, 0, 0};

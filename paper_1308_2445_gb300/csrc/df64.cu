@@ -8,6 +8,8 @@
 // carry FP64 accuracy.
 //
 // The pair arithmetic (split, TwoProd + TwoSum, renormalisation) is in df64.h.
+#include <mutex>
+
 #include "common.h"
 #include "df64.h"
 
@@ -214,10 +216,14 @@ int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, 
     const int rows = ng * UR;
     const size_t smem = ((size_t)rows * q + (size_t)q * k) * sizeof(float2);
     if (smem > 220 * 1024) return fail(HBSD_ERR_ARG, "update: q too large for the double-float kernel");
-    static size_t attr = 0;
-    if (smem > 48 * 1024 && smem > attr) {
-        HBSD_CUDA(cudaFuncSetAttribute(k_update_df64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = smem;
+    {
+        static std::mutex attr_mu;
+        static size_t attr = 0;
+        std::lock_guard<std::mutex> lk(attr_mu);
+        if (smem > 48 * 1024 && smem > attr) {
+            HBSD_CUDA(cudaFuncSetAttribute(k_update_df64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            attr = smem;
+        }
     }
     HBSD_TRY(s->df_w.alloc((size_t)q * k));
     if (split_w) {

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "common.h"
 
@@ -438,7 +439,9 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     HBSD_TRY(s->mr_any.alloc(4));   // [0..1] grid barrier, [2] error flag
     static int blocks_per_sm[2] = {-1, -1};
     static int num_sms = 0;
+    static std::mutex init_mu;
     const int ti = sizeof(T) == 8 ? 0 : 1;
+    std::unique_lock<std::mutex> init_lk(init_mu);
     if (blocks_per_sm[ti] < 0) {
         int dev = 0;
         HBSD_CUDA(cudaGetDevice(&dev));
@@ -450,6 +453,7 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     }
     if (blocks_per_sm[ti] < 1) return fail(HBSD_ERR_UNSUPPORTED, "minres: kernel cannot be resident");
     const int grid = blocks_per_sm[ti] * num_sms;
+    init_lk.unlock();
     const int64_t kp = round_up(k, 4);
     HBSD_TRY(s->mr_red.alloc((size_t)2 * grid * kp));
     if (s->mr_blk_grid != grid) {

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <mutex>
 
 #include "common.h"
 
@@ -792,8 +793,8 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
     HBSD_TRY(s->rr_ws.alloc((size_t)std::max<int64_t>(rr_cluster_ws_doubles(q, k, 16), (int64_t)4 * q * q + 3 * q + 64)));
     HBSD_TRY(s->rr_info.alloc(4));
     static const bool trace = std::getenv("HBSD_TRACE") != nullptr || std::getenv("HBSD_RRDBG") != nullptr;
-    static cudaEvent_t tev[4];
-    static bool tev_made = false;
+    static thread_local cudaEvent_t tev[4];
+    static thread_local bool tev_made = false;
     if (trace && !tev_made) {
         for (auto& e : tev) cudaEventCreate(&e);
         tev_made = true;
@@ -819,6 +820,8 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
         const size_t smem = (size_t)L.total * sizeof(double);
         // attribute and co-scheduling checks are host calls of tens of microseconds: once per
         // (cluster size, shared-memory size)
+        static std::mutex cache_mu;   // sessions of a server call this from several threads
+        std::lock_guard<std::mutex> cache_lk(cache_mu);
         static size_t attr_smem = 0;
         static bool nonportable = false;
         static int ok_cache[17] = {0};

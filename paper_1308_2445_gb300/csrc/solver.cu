@@ -187,15 +187,6 @@ static int update_step(Session* S, bool df, T* Z0, int64_t ld0, int q0, const T*
 }
 
 // ---- per-solve buffers -----------------------------------------------------------------------
-template <class T>
-struct SolveBufs {
-    DBuf<T> Psi, PsiH, PsiS, P, PH, PS, RU, Xa, Ra, shifts;
-};
-
-struct SolveCommon {
-    DBuf<double> E, res, HR, SR, W, theta;
-    DBuf<int> Ulist, Llist, steps;
-};
 
 template <class S_, class D_>
 __global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, int64_t n, D_* __restrict__ dst,
@@ -439,7 +430,7 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     const bool mixed = o.precision == HBSD_PRECISION_MIXED;
     const int64_t ldw = round_up(w, 4), ldp = round_up(std::max(m, 1), 4);
     const int qmax = w + m;
-    SolveCommon C;
+    SolveCommon& C = S->sc;   // session-resident: the DBufs only grow, so repeated solves do not allocate
     HBSD_TRY(C.E.alloc(w)); HBSD_TRY(C.res.alloc(m)); HBSD_TRY(C.theta.alloc(w));
     HBSD_TRY(C.HR.alloc((size_t)qmax * qmax)); HBSD_TRY(C.SR.alloc((size_t)qmax * qmax));
     HBSD_TRY(C.W.alloc((size_t)qmax * w));
@@ -457,7 +448,7 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     stt.precond_calls = 0;
     StepTimer tm;
     std::vector<double> E(w), Eprev;
-    SolveBufs<double> B64;
+    SolveBufs<double>& B64 = S->sb;
     HBSD_TRY(alloc_blocks(B64, n, ldw, ldp, m));
     int it32 = 0, it64 = 0;
     bool conv = false;
@@ -625,13 +616,13 @@ int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev,
     if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
     if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
         return fail(HBSD_ERR_ARG, "unknown precision mode");
-    DBuf<double> x0buf;
     if (!X0_dev) {
         std::vector<double> hx((size_t)S->n * w);
         seed_normals(S->opt.seed, 2, (int64_t)hx.size(), hx.data());
-        HBSD_TRY(x0buf.alloc(hx.size()));
-        HBSD_CUDA(cudaMemcpy(x0buf.p, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice));
-        X0_dev = x0buf.p;
+        HBSD_TRY(S->io_x0.alloc(hx.size()));
+        HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice, S->stream));
+        HBSD_CUDA(cudaStreamSynchronize(S->stream));   // hx is released at the end of this block
+        X0_dev = S->io_x0.p;
         ldx0 = w;
     } else if (ldx0 < w) {
         return fail(HBSD_ERR_ARG, "ldx0 < nev + m0");
@@ -653,31 +644,30 @@ int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm, 
     if (nev < 1) return fail(HBSD_ERR_ARG, "nev >= 1 required");
     const int w = nev + m0_of(*S, nev);
     if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
-    DBuf<double> x0, lam, xo;
+    // host <-> device traffic goes through session-resident buffers on the session's stream
+    // (no allocation after the first solve of a size, no legacy-stream synchronisation)
     const double* x0p = nullptr;
     int64_t ld0 = w;
     if (warm) {
         if (X0) return fail(HBSD_ERR_ARG, "warm start takes X0 = NULL");
         if (!S->psi_keep.p || S->keep_w != w) return fail(HBSD_ERR_ARG, "no previous block of this width to warm-start from");
-        x0p = S->psi_keep.p;
+        // the solve overwrites psi_keep; start from a copy
+        HBSD_TRY(S->io_x0.alloc(S->psi_keep.n));
+        HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, S->psi_keep.p, S->psi_keep.n * 8, cudaMemcpyDeviceToDevice, S->stream));
+        x0p = S->io_x0.p;
         ld0 = S->keep_ld;
     } else if (X0) {
-        HBSD_TRY(x0.alloc((size_t)S->n * w));
-        HBSD_CUDA(cudaMemcpyAsync(x0.p, X0, (size_t)S->n * w * 8, cudaMemcpyHostToDevice, S->stream));
-        x0p = x0.p;
+        HBSD_TRY(S->io_x0.alloc((size_t)S->n * w));
+        HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, X0, (size_t)S->n * w * 8, cudaMemcpyHostToDevice, S->stream));
+        x0p = S->io_x0.p;
     }
-    HBSD_TRY(lam.alloc(nev));
-    if (X) HBSD_TRY(xo.alloc((size_t)S->n * nev));
-    DBuf<double> keep_copy;
-    if (warm) {  // the solve overwrites psi_keep; start from a copy
-        HBSD_TRY(keep_copy.alloc(S->psi_keep.n));
-        HBSD_CUDA(cudaMemcpyAsync(keep_copy.p, S->psi_keep.p, S->psi_keep.n * 8, cudaMemcpyDeviceToDevice, S->stream));
-        x0p = keep_copy.p;
-    }
-    int rc = hbsd_solve_device(h, nev, tol, x0p, ld0, lam.p, X ? xo.p : nullptr, nev, iters, st);
+    HBSD_TRY(S->io_lam.alloc(nev));
+    if (X) HBSD_TRY(S->io_x.alloc((size_t)S->n * nev));
+    int rc = hbsd_solve_device(h, nev, tol, x0p, ld0, S->io_lam.p, X ? S->io_x.p : nullptr, nev, iters, st);
     if (rc < 0) return rc;
-    HBSD_CUDA(cudaMemcpy(lambda, lam.p, nev * 8, cudaMemcpyDeviceToHost));
-    if (X) HBSD_CUDA(cudaMemcpy(X, xo.p, (size_t)S->n * nev * 8, cudaMemcpyDeviceToHost));
+    HBSD_CUDA(cudaMemcpyAsync(lambda, S->io_lam.p, nev * 8, cudaMemcpyDeviceToHost, S->stream));
+    if (X) HBSD_CUDA(cudaMemcpyAsync(X, S->io_x.p, (size_t)S->n * nev * 8, cudaMemcpyDeviceToHost, S->stream));
+    HBSD_CUDA(cudaStreamSynchronize(S->stream));
     return rc;
 }
 

@@ -47,6 +47,25 @@ class hbsd_options(C.Structure):
                 ("precision", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64)]
 
 
+class hbsd_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_slots", C.c_int)]
+
+
+class hbsd_request(C.Structure):
+    _fields_ = [("H", C.POINTER(hbsd_csr)), ("S", C.POINTER(hbsd_csr)), ("lb", C.POINTER(hbsd_local_blocks)),
+                ("opt", C.POINTER(hbsd_options)), ("session_id", C.c_int64), ("H_val", C.POINTER(C.c_double)),
+                ("nev", C.c_int), ("tol", C.c_double), ("X0", C.POINTER(C.c_double)), ("warm", C.c_int)]
+
+
+class hbsd_result(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int), ("iters", C.c_int), ("session_id", C.c_int64),
+                ("res_max", C.c_double), ("latency_ms", C.c_double), ("queue_ms", C.c_double),
+                ("run_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class hbsd_stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("iters_fp64", C.c_int), ("minres_steps", C.c_int64),
                 ("precond_cols", C.c_int64), ("local_cols", C.c_int64), ("rr_fallbacks", C.c_int),
@@ -92,6 +111,12 @@ _SIGS = {
     "hbsd_update": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int, _P]),
     "hbsd_gram_df64": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int, _P, _P, _P]),
     "hbsd_update_df64": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int, _P, C.c_int, _P]),
+    "hbsd_server_opts_default": (None, [C.POINTER(hbsd_server_opts)]),
+    "hbsd_server_create": (C.c_int, [C.POINTER(hbsd_server_opts), C.POINTER(C.c_void_p)]),
+    "hbsd_submit": (C.c_int, [C.c_void_p, C.POINTER(hbsd_request), _P, _P, C.POINTER(C.c_uint64)]),
+    "hbsd_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(hbsd_result)]),
+    "hbsd_session_release": (C.c_int, [C.c_void_p, C.c_int64]),
+    "hbsd_server_destroy": (None, [C.c_void_p]),
     "hbsd_probe_peak": (C.c_int, [C.c_int, _P, C.POINTER(C.c_double)]),
     "hbsd_seed_normals": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int64, _D]),
 }
@@ -307,3 +332,96 @@ def seed_normals(seed, stream, count):
     out = np.empty(count)
     check(lib().hbsd_seed_normals(seed, stream, count, out.ctypes.data_as(_D)), "hbsd_seed_normals")
     return out
+
+
+class Server:
+    """hbsd_server_*: solve requests of several problems in flight at once on one GPU.
+
+    submit() copies what it is given and returns a ticket at once; poll(ticket) returns None
+    while the request is queued or running, then (result dict, lambda, X)."""
+
+    def __init__(self, max_slots=4, hbm_budget_bytes=0):
+        o = hbsd_server_opts()
+        lib().hbsd_server_opts_default(C.byref(o))
+        o.max_slots = int(max_slots)
+        o.hbm_budget_bytes = int(hbm_budget_bytes)
+        h = C.c_void_p()
+        check(lib().hbsd_server_create(C.byref(o), C.byref(h)), "hbsd_server_create")
+        self.h = h
+        self._out = {}   # ticket -> (lambda, X) host buffers, kept alive until polled
+
+    def submit(self, nev, tol, problem=None, session_id=-1, H_val=None, X0=None, warm=False, want_vectors=True,
+               **opts):
+        keep = []
+        rq = hbsd_request()
+        rq.session_id = int(session_id)
+        rq.nev = int(nev)
+        rq.tol = float(tol)
+        rq.warm = int(bool(warm))
+        n = None
+        if problem is not None:
+            p = problem
+            rp = np.ascontiguousarray(p.row_ptr, dtype=np.int64)
+            ci = np.ascontiguousarray(p.col_idx, dtype=np.int32)
+            hv = np.ascontiguousarray(p.h_val, dtype=np.float64)
+            sv = np.ascontiguousarray(p.s_val, dtype=np.float64)
+            dn = np.ascontiguousarray(p.dof_node, dtype=np.int32)
+            H = hbsd_csr(p.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                         ci.ctypes.data_as(C.POINTER(C.c_int32)), hv.ctypes.data_as(_D), 0)
+            S = hbsd_csr(p.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
+                         ci.ctypes.data_as(C.POINTER(C.c_int32)), sv.ctypes.data_as(_D), 0)
+            lb = hbsd_local_blocks(dn.ctypes.data_as(C.POINTER(C.c_int32)), None, (C.c_int32 * 3)(*p.grid))
+            op = options_default(sigma_bar=float(p.eps_bar), **opts)
+            keep += [rp, ci, hv, sv, dn, H, S, lb, op]
+            rq.H, rq.S, rq.lb, rq.opt = C.pointer(H), C.pointer(S), C.pointer(lb), C.pointer(op)
+            rq.session_id = -1
+            n = p.n
+        if H_val is not None:
+            hvn = np.ascontiguousarray(H_val, dtype=np.float64)
+            keep.append(hvn)
+            rq.H_val = hvn.ctypes.data_as(_D)
+        if X0 is not None:
+            x0 = np.ascontiguousarray(X0, dtype=np.float64)
+            keep.append(x0)
+            rq.X0 = x0.ctypes.data_as(_D)
+            n = x0.shape[0]
+        if n is None and want_vectors:
+            raise ValueError("want_vectors for a follow-up needs X0 or n; pass n through X0 or problem")
+        lam = np.empty(nev)
+        X = np.empty((n, nev)) if want_vectors else None
+        t = C.c_uint64(0)
+        check(lib().hbsd_submit(self.h, C.byref(rq), lam.ctypes.data_as(_D),
+                                X.ctypes.data_as(_D) if X is not None else None, C.byref(t)), "hbsd_submit")
+        self._out[t.value] = (lam, X)
+        return t.value
+
+    def poll(self, ticket):
+        r = hbsd_result()
+        rc = lib().hbsd_poll(self.h, C.c_uint64(ticket), C.byref(r))
+        if rc == 2:
+            return None
+        check(rc, "hbsd_poll")
+        lam, X = self._out.pop(ticket)
+        return r.as_dict(), lam, X
+
+    def wait(self, ticket, poll_s=0.0005):
+        import time
+        while True:
+            out = self.poll(ticket)
+            if out is not None:
+                return out
+            time.sleep(poll_s)
+
+    def release(self, session_id):
+        return check(lib().hbsd_session_release(self.h, C.c_int64(session_id)), "hbsd_session_release")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hbsd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

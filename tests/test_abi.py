@@ -1,4 +1,5 @@
 """The C-ABI library builds, loads without a GPU, and exports every symbol include/hbsd.h declares."""
+import ctypes
 import os
 import re
 
@@ -65,3 +66,34 @@ def test_library_start_block_generator_matches_inputs(lib):
         a = hbsd.seed_normals(seed, pi.STREAM_X0, count)
         b = pi.normal(seed, pi.STREAM_X0, count)
         assert np.allclose(a, b, rtol=1e-14, atol=1e-14)
+
+
+def test_server_host_bookkeeping_without_gpu():
+    # the request loop's argument checks and ticket bookkeeping run on the host; with an explicit
+    # memory budget, creating and destroying a server makes no CUDA call
+    from paper_1308_2445_gb300 import hbsd
+    lib = hbsd.lib()
+    o = hbsd.hbsd_server_opts()
+    lib.hbsd_server_opts_default(ctypes.byref(o))
+    assert o.max_slots == 4 and o.hbm_budget_bytes == 0
+    o.max_slots = 0
+    h = ctypes.c_void_p()
+    assert lib.hbsd_server_create(ctypes.byref(o), ctypes.byref(h)) == hbsd.HBSD_ERR_ARG
+    o.max_slots = 2
+    o.hbm_budget_bytes = 1 << 30
+    assert lib.hbsd_server_create(ctypes.byref(o), ctypes.byref(h)) == hbsd.HBSD_OK
+    r = hbsd.hbsd_result()
+    assert lib.hbsd_poll(h, ctypes.c_uint64(7), ctypes.byref(r)) == hbsd.HBSD_ERR_ARG      # unknown ticket
+    rq = hbsd.hbsd_request()
+    rq.session_id = 3
+    rq.nev = 4
+    rq.tol = 1e-8
+    lam = (ctypes.c_double * 4)()
+    t = ctypes.c_uint64(0)
+    assert lib.hbsd_submit(h, ctypes.byref(rq), lam, None, ctypes.byref(t)) == hbsd.HBSD_ERR_ARG  # no session 3
+    rq.nev = 0
+    assert lib.hbsd_submit(h, ctypes.byref(rq), lam, None, ctypes.byref(t)) == hbsd.HBSD_ERR_ARG  # nev < 1
+    rq.nev, rq.session_id = 4, -1
+    assert lib.hbsd_submit(h, ctypes.byref(rq), lam, None, ctypes.byref(t)) == hbsd.HBSD_ERR_ARG  # no problem
+    assert lib.hbsd_session_release(h, ctypes.c_int64(0)) == hbsd.HBSD_ERR_ARG
+    lib.hbsd_server_destroy(h)
