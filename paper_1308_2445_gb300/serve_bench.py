@@ -1,0 +1,165 @@
+"""Served-form benchmark: a stream of solve requests through hbsd_server_* on one GPU.
+
+  python -m paper_1308_2445_gb300.serve_bench [--requests R] [--slots S] [--load 0.8] [--seed 11]
+
+Request mix (synthetic, seeded): problems on 16^3 and 24^3 meshes with 4-8 atoms and 2-4
+enrichment dofs per node (r_c = 0.15), nev from {32, 64}; about half of the requests are
+SCF-style follow-ups of a session seen before (V perturbed by 1% Gaussian noise at the
+quadrature points, H re-assembled, warm start from the session's last block).
+
+1. Capacity: a closed loop keeps `slots` requests in flight; capacity = requests / wall time.
+2. Served run: Poisson arrivals at `load` x capacity; each request's latency runs from its
+   arrival (the submit call) to its completion.  Reports p50 / p99 latency and the converged
+   eigenpairs per second of wall time.
+3. The same closed loop with one slot (requests one at a time) for comparison.
+
+Prints one JSON line.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def build_pool(seed):
+    from paper_1308_2445_gb300 import pufe_inputs as pi
+    rng = np.random.default_rng(seed)
+    pool = []
+    for k, mesh in enumerate([16, 16, 24, 24]):
+        atoms = int(rng.integers(4, 9))
+        enr = int(rng.integers(2, 5))
+        s = int(rng.integers(1, 1 << 30))
+        base = pi.generate(mesh, atoms, enr, 0.15, s)
+        follow = [pi.generate(mesh, atoms, enr, 0.15, s, v_noise=0.01, noise_seed=s + j + 1).h_val for j in range(2)]
+        pool.append((f"{mesh}^3/{atoms}at/{enr}enr/n={base.n}", base, follow))
+    return pool
+
+
+def make_requests(pool, count, seed):
+    """(pool index, nev, follow-up index or -1); a follow-up only after its problem appeared."""
+    rng = np.random.default_rng(seed + 1)
+    seen = set()
+    out = []
+    for _ in range(count):
+        i = int(rng.integers(len(pool)))
+        nev = int(rng.choice([32, 64]))
+        if i in seen and rng.random() < 0.5:
+            out.append((i, nev, int(rng.integers(2))))
+        else:
+            out.append((i, nev, -1))
+            seen.add(i)
+    return out
+
+
+def run(hbsd, pool, reqs, slots, arrivals=None):
+    """Submit the requests (at the given arrival offsets, or closed-loop with `slots` in flight);
+    returns per-request results and the wall time."""
+    sv = hbsd.Server(max_slots=slots)
+    sessions = {}   # pool index -> (session id, nev of its last solve)
+    done = []
+    t0 = time.perf_counter()
+    pending = {}
+
+    def submit(k):
+        i, nev, fol = reqs[k]
+        name, p, follow = pool[i]
+        if fol >= 0 and i in sessions and sessions[i][1] == nev:
+            t = sv.submit(nev, 1e-8, session_id=sessions[i][0], H_val=follow[fol], warm=True, want_vectors=False)
+        else:
+            t = sv.submit(nev, 1e-8, problem=p, want_vectors=False, precision=hbsd.PRECISION_MIXED)
+        pending[t] = (k, time.perf_counter())
+
+    def collect(block):
+        while True:
+            for t in list(pending):
+                out = sv.poll(t)
+                if out is not None:
+                    k, ts = pending.pop(t)
+                    res = out[0]
+                    i, nev, fol = reqs[k]
+                    if res["status"] >= 0 and res["session_id"] >= 0:
+                        sessions[i] = (res["session_id"], nev)
+                    done.append((k, res))
+                    if not block:
+                        return True
+                    return True
+            if not block:
+                return False
+            time.sleep(0.0005)
+
+    if arrivals is None:
+        nxt = 0
+        while nxt < len(reqs) or pending:
+            while nxt < len(reqs) and len(pending) < slots:
+                # a follow-up waits until its session has been created
+                i, nev, fol = reqs[nxt]
+                if fol >= 0 and i not in sessions and any(reqs[kk][0] == i for kk, _ in pending.values()):
+                    break
+                submit(nxt)
+                nxt += 1
+            collect(True)
+    else:
+        nxt = 0
+        while nxt < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and arrivals[nxt] <= now:
+                submit(nxt)
+                nxt += 1
+            if not collect(False):
+                time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    sv.close()
+    return done, wall
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--seed", type=int, default=11)
+    a = ap.parse_args()
+    from paper_1308_2445_gb300 import build_lib, hbsd
+    if not os.path.exists(build_lib.LIB):
+        build_lib.build()
+    pool = build_pool(a.seed)
+    reqs = make_requests(pool, a.requests, a.seed)
+    # warm the library (module loading, first launches) on one request
+    run(hbsd, pool, reqs[:1], 1)
+    closed, t_closed = run(hbsd, pool, reqs, a.slots)
+    capacity = len(reqs) / t_closed
+    rng = np.random.default_rng(a.seed + 2)
+    gaps = rng.exponential(1.0 / (a.load * capacity), size=len(reqs))
+    arrivals = np.cumsum(gaps) - gaps[0]
+    served, t_served = run(hbsd, pool, reqs, a.slots, arrivals=arrivals)
+    single, t_single = run(hbsd, pool, reqs, 1)
+    lat = np.array([r["latency_ms"] for _, r in served])
+    conv = sum(reqs[k][1] for k, r in served if r["status"] == 0 and r["res_max"] <= 1e-8)
+    conv_closed = sum(reqs[k][1] for k, r in closed if r["status"] == 0 and r["res_max"] <= 1e-8)
+    conv_single = sum(reqs[k][1] for k, r in single if r["status"] == 0 and r["res_max"] <= 1e-8)
+    line = {
+        "metric": "served LABPSD solves: p50/p99 latency at Poisson arrivals, eigenpairs/s",
+        "requests": len(reqs), "slots": a.slots, "load": a.load,
+        "capacity_req_per_s": capacity,
+        "served": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                   "mean_ms": float(lat.mean()), "eigenpairs_per_s": conv / t_served, "wall_s": t_served,
+                   "failed": int(sum(1 for _, r in served if r["status"] != 0))},
+        "closed_loop": {"eigenpairs_per_s": conv_closed / t_closed, "wall_s": t_closed},
+        "one_slot": {"eigenpairs_per_s": conv_single / t_single, "wall_s": t_single},
+        "followups": int(sum(1 for r in reqs if r[2] >= 0)),
+        "pool": [name for name, _, _ in pool],
+        "precision": "mixed",
+        "data": "synthetic",
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
