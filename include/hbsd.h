@@ -76,6 +76,9 @@ typedef struct {
 
 #define HBSD_PRECOND_HYBRID   0   /* steps 6(a) + 6(b) (Sec. 3 hybrid scheme)           */
 #define HBSD_PRECOND_GLOBAL   1   /* step 6(a) only (Eq. globalprecond)                  */
+#define HBSD_PRECOND_LOCAL    2   /* step 6(b) only (Sec. 5 "local" comparison): P = -R,
+                                     localized columns refined by MINRES from zero; no
+                                     global factor is built                              */
 
 /* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
  * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,

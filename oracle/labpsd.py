@@ -51,6 +51,7 @@ class Options:
     max_outer: int = 1000      # R12
     m0: int | None = None      # R6
     local: bool = True         # False: global preconditioner only (step 6(a) alone)
+    use_global: bool = True    # False: local only, Sec. 5 (6(b) without 6(a)), reading R16
 
 
 def default_m0(m: int) -> int:
@@ -313,7 +314,7 @@ def labpsd(problem, nev, tol, X0=None, opts: Options | None = None, seed=1,
     w = m + m0
     Hs, S, sigma0 = make_shifted(problem)
     n = problem.n
-    if precond is None:
+    if precond is None and opts.use_global:
         precond = GlobalPreconditioner(Hs - (problem.eps_bar - sigma0) * S,
                                        problem.dof_node, problem.grid)
     if X0 is None:
@@ -346,12 +347,18 @@ def labpsd(problem, nev, tol, X0=None, opts: Options | None = None, seed=1,
             break
         # step 6: search directions for unconverged columns only (remark 3)
         U = np.nonzero(res > tol)[0]
-        P = precond.apply(R[:, U])                                    # 6(a)
+        if opts.use_global:
+            P = precond.apply(R[:, U])                                # 6(a)
+        else:
+            # local only (Sec. 5, reading R16): no global step; an unlocalized column keeps the
+            # unpreconditioned direction -r_i, a localized one is refined by MINRES from zero
+            P = -R[:, U]
         loc = localized(res, E, E_prev, opts.tau1, opts.tau2) if opts.local else np.zeros(m, bool)
         steps = []
         for j, i in enumerate(U):
             if loc[i]:                                                  # 6(b)
-                P[:, j], k, _ = refine(Hs, S, E[i], R[:, i], P[:, j], opts.eta, opts.max_minres)
+                p0 = P[:, j] if opts.use_global else np.zeros(n)
+                P[:, j], k, _ = refine(Hs, S, E[i], R[:, i], p0, opts.eta, opts.max_minres)
                 steps.append(k)
         minres_steps.append(np.array(steps, dtype=np.int64))
         n_precond.append(int(U.size))

@@ -191,6 +191,9 @@ static int update_step(Session* S, bool df, T* Z0, int64_t ld0, int q0, const T*
 template <class S_, class D_>
 __global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, int64_t n, D_* __restrict__ dst,
                                 int64_t ldd, const double* __restrict__ d, int pw);
+template <class T>
+__global__ void k_neg_block(const T* __restrict__ src, int64_t lds, int k, int64_t n, T* __restrict__ dst,
+                            int64_t ldd);
 
 // Stopping rule of one precision phase.
 struct PhaseRule {
@@ -247,7 +250,8 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     std::vector<int> U, Lpos;
     std::vector<T> shifts;
     std::vector<double> hist;
-    const bool hybrid = o.precond == HBSD_PRECOND_HYBRID;
+    const bool hybrid = o.precond == HBSD_PRECOND_HYBRID || o.precond == HBSD_PRECOND_LOCAL;   // localization on
+    const bool local_only = o.precond == HBSD_PRECOND_LOCAL;   // no step 6(a) (reading R16)
     int iters = 0;
     for (;;) {
         // steps 4-5
@@ -309,9 +313,12 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                                                              B.RU.p, ldp);
         HBSD_LAUNCHED(S);
         tm.end(ti, st);
-        const bool fp32_dirs = sizeof(T) == 8 && o.precision == HBSD_PRECISION_MIXED;
+        const bool fp32_dirs = sizeof(T) == 8 && o.precision == HBSD_PRECISION_MIXED && !local_only;
         ti = tm.begin(StepTimer::PRECOND, st);
-        if (fp32_dirs) {
+        if (local_only) {   // P = -R on the unconverged columns
+            k_neg_block<T><<<grid_for(n * p), 256, 0, st>>>(B.RU.p, ldp, p, n, B.P.p, ldp);
+            HBSD_LAUNCHED(S);
+        } else if (fp32_dirs) {
             // 6(a) in FP32 on the scaled pencil: P^ = -(D A D)^{-1} (D R); P^ stays scaled for 6(b)
             k_convert_block<T, float><<<grid_for(n * p), 256, 0, st>>>(B.RU.p, ldp, p, n, S->r32.p, ldp,
                                                                       S->A.dscale.p, +1);
@@ -333,8 +340,12 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                 HBSD_LAUNCHED(S);
             }
             HBSD_CUDA(cudaMemcpyAsync(B.shifts.p, shifts.data(), a * sizeof(T), cudaMemcpyHostToDevice, st));
-            k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.P.p, ldp, C.Llist.p, a, n, B.Xa.p, ldp);
-            HBSD_LAUNCHED(S);
+            if (local_only) {   // MINRES from zero
+                HBSD_CUDA(cudaMemsetAsync(B.Xa.p, 0, (size_t)n * ldp * sizeof(T), st));
+            } else {
+                k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.P.p, ldp, C.Llist.p, a, n, B.Xa.p, ldp);
+                HBSD_LAUNCHED(S);
+            }
             k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.RU.p, ldp, C.Llist.p, a, n, B.Ra.p, ldp);
             HBSD_LAUNCHED(S);
             HBSD_TRY(minres_batch<T>(S, B.Ra.p, ldp, B.shifts.p, a, o.eta, o.max_minres, B.Xa.p, ldp, C.steps.p,
@@ -399,6 +410,18 @@ static int alloc_blocks(SolveBufs<T>& B, int64_t n, int64_t ldw, int64_t ldp, in
     return 0;
 }
 
+// dst(i, j) = -src(i, j)
+template <class T>
+__global__ void k_neg_block(const T* __restrict__ src, int64_t lds, int k, int64_t n, T* __restrict__ dst,
+                            int64_t ldd) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t % k);
+        dst[i * ldd + j] = -src[i * lds + j];
+    }
+}
+
 // dst(i, j) = src(i, j) * d_i^pow  (pow = -1: into scaled coordinates y = D^{-1} x; +1: back)
 template <class S_, class D_>
 __global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, int64_t n, D_* __restrict__ dst,
@@ -452,7 +475,7 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     HBSD_TRY(alloc_blocks(B64, n, ldw, ldp, m));
     int it32 = 0, it64 = 0;
     bool conv = false;
-    if (mixed) {
+    if (mixed && S->has_factor) {
         HBSD_TRY(factor_make_fp32(S->F, S->A.dscale.p, st));
         HBSD_TRY(S->r32.alloc((size_t)n * ldp));
         HBSD_TRY(S->p32.alloc((size_t)n * ldp));
@@ -554,6 +577,8 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
     for (int64_t e = 0; e < H->nnz; ++e)
         if (H->col_idx[e] < 0 || H->col_idx[e] >= H->n) return fail(HBSD_ERR_ARG, "column index out of range");
     if (!std::isfinite(opt->sigma_bar)) return fail(HBSD_ERR_ARG, "sigma_bar must be set");
+    if (opt->precond < HBSD_PRECOND_HYBRID || opt->precond > HBSD_PRECOND_LOCAL)
+        return fail(HBSD_ERR_ARG, "unknown preconditioner mode");
     if (!lb->dof_node || lb->grid[0] <= 0 || lb->grid[1] <= 0 || lb->grid[2] <= 0)
         return fail(HBSD_ERR_ARG, "local blocks need dof_node and a positive grid");
     hbsd_handle* h = new hbsd_handle();
@@ -580,9 +605,11 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
     S->h_sval.assign(Sm->val, Sm->val + S->nnz);
     std::vector<double> aval(S->nnz);
     for (int64_t e = 0; e < S->nnz; ++e) aval[e] = H->val[e] - opt->sigma_bar * Sm->val[e];
-    rc = factor_build(S, S->F, S->n, H->row_ptr, H->col_idx, aval.data(), lb->dof_node, lb->grid, S->stream);
-    if (rc < 0) { std::string keep = g_last_error; hbsd_destroy(h); g_last_error = keep; return rc; }
-    S->has_factor = true;
+    if (opt->precond != HBSD_PRECOND_LOCAL) {   // the local-only mode has no global step
+        rc = factor_build(S, S->F, S->n, H->row_ptr, H->col_idx, aval.data(), lb->dof_node, lb->grid, S->stream);
+        if (rc < 0) { std::string keep = g_last_error; hbsd_destroy(h); g_last_error = keep; return rc; }
+        S->has_factor = true;
+    }
     *out = h;
     return HBSD_OK;
 }

@@ -29,6 +29,7 @@ PRECISION_FP64 = 0
 PRECISION_MIXED = 1
 PRECOND_HYBRID = 0
 PRECOND_GLOBAL = 1
+PRECOND_LOCAL = 2
 
 
 class hbsd_csr(C.Structure):

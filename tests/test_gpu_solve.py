@@ -89,6 +89,27 @@ def test_small_solve_global_only():
     assert st["local_cols"] == 0
 
 
+def test_small_solve_local_only():
+    # Sec. 5 "local" comparison (reading R16): no global step and no factor; P = -R, localized
+    # columns refined by MINRES from zero.  As in the paper, it stagnates (the oracle stays near
+    # 3e-4 after 400 iterations on this case), so a fixed 20-iteration trajectory is compared
+    # with the oracle's, and the hybrid scheme must end far lower.
+    p = pi.small_case(1)
+    nev = 16
+    X0 = pi.seed_normal_block(1, p.n, 19)
+    s = hb().Session.from_problem(p, precond=hb().PRECOND_LOCAL, max_outer=20)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0, opts=L.Options(use_global=False, max_outer=20))
+    assert rc == 1 and not ro.converged and it == ro.iters == 20
+    scale = np.abs(ro.lam).max()
+    assert np.abs(lam - ro.lam).max() <= 1e-7 * scale
+    assert 0.5 <= st["res_max"] / ro.res_history[-1] <= 2.0
+    assert st["local_cols"] > 0 and st["t_factor_ms"] == 0.0
+    sh = hb().Session.from_problem(p, max_outer=20)
+    _, _, _, rch, sth = sh.solve(nev, 1e-8, X0=X0)
+    assert sth["res_max"] < 1e-3 * st["res_max"]
+
+
 def test_closed_form_solve():
     q = pi.generate(6, 0, 0, 0.1, 1, v0=0.3)
     s = hb().Session.from_problem(q)

@@ -144,6 +144,42 @@ def test_hybrid_beats_global_only(small_problem):
     assert np.abs(rh.lam - rg.lam).max() <= 1e-9 * np.abs(rh.lam).max()
 
 
+def test_local_only_without_localization_is_textbook_block_sd():
+    # the local-only mode (Sec. 5, reading R16) with no localized column (tau1 = 0) is plain
+    # block steepest descent: P = -R on the unconverged columns, Rayleigh-Ritz on [Psi P];
+    # written out here with scipy's generalized eigh and compared iteration by iteration
+    p = pi.generate(4, 1, 1, 0.3, 5)
+    Hs, S, _ = L.make_shifted(p)
+    Hd, Sd = Hs.toarray(), S.toarray()
+    m, w = 3, 6
+    X0 = pi.seed_normal_block(4, p.n, w)
+    r = L.labpsd(p, m, 1e-10, X0=X0, opts=L.Options(use_global=False, tau1=0.0, m0=w - m, max_outer=6))
+    ev, V = sla.eigh(X0.T @ Hd @ X0, X0.T @ Sd @ X0)
+    Psi, E = X0 @ V[:, :w], ev[:w]
+    hist = [E.copy()]
+    for _ in range(6):
+        R = Hd @ Psi[:, :m] - Sd @ Psi[:, :m] * E[:m]
+        res = np.linalg.norm(R, axis=0) / np.linalg.norm(Hd @ Psi[:, :m], axis=0)
+        U = np.nonzero(res > 1e-10)[0]
+        Z = np.hstack([Psi, -R[:, U]])
+        ev, V = sla.eigh(Z.T @ Hd @ Z, Z.T @ Sd @ Z)
+        Psi, E = Z @ V[:, :w], ev[:w]
+        hist.append(E.copy())
+    assert len(r.ritz_history) == len(hist)
+    for a, b in zip(r.ritz_history, hist):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()   # both held shifted by sigma0
+
+
+def test_local_only_is_slower_than_hybrid(small_problem):
+    # Sec. 5 (Fig. 9 comparison): without the global step, the same eigenpairs need more outer
+    # iterations than the hybrid scheme
+    p = small_problem
+    rh = L.labpsd(p, 16, 1e-8, seed=1)
+    rl = L.labpsd(p, 16, 1e-8, seed=1, opts=L.Options(use_global=False, max_outer=400))
+    assert rh.converged
+    assert rl.iters > rh.iters
+
+
 # ------------------------------------------------------------------ MINRES
 def _indefinite(n, seed):
     rng = np.random.default_rng(seed)
