@@ -28,6 +28,10 @@ solve) as the only library steps.  Readings of points the paper leaves open:
   R12 max_outer default 1000.
   R13 Rayleigh-Ritz on the diagonally scaled pair; if the Cholesky of the scaled S_R breaks
       down or a pivot is below 1e-14, drop S_R eigen-directions below 1e-14 * max.
+  R17 with a nonlocal term H = H_loc + F G F^H (Eq. fgf) the global factor is that of the
+      local part H_loc^(1) - eps_bar S (Eq. ldl) and the nonlocal part enters through the
+      Sherman-Morrison-Woodbury steps 1-6 of Sec. 4; every product with H (steps 3, 7 and the
+      MINRES operator of 6(b)) applies the full H.
 """
 from __future__ import annotations
 
@@ -60,6 +64,33 @@ def default_m0(m: int) -> int:
 
 def _ctr(A):
     return A.conj().T
+
+
+# ---------------------------------------------------------------------------------------
+# The shifted Hamiltonian: sparse local part plus the low-rank nonlocal part (Eq. fgf)
+# ---------------------------------------------------------------------------------------
+class ShiftedHamiltonian:
+    """Hs = (H_loc - sigma0 S) + F G F^H, held as the sparse local part `loc` and the factors
+    F (n x k) and G (k x k Hermitian) of the nonlocal term (none when F is None)."""
+
+    def __init__(self, loc, F=None, G=None):
+        self.loc = loc
+        self.F = None if F is None or F.shape[1] == 0 else np.asarray(F)
+        self.G = None if self.F is None else np.asarray(G)
+        self.shape = loc.shape
+
+    def toarray(self):
+        """Dense Hs (small cases only)."""
+        D = self.loc.toarray()
+        if self.F is not None:
+            D = D + self.F @ self.G @ _ctr(self.F)
+        return D
+
+    def __matmul__(self, X):
+        Y = self.loc @ X
+        if self.F is not None:
+            Y = Y + self.F @ (self.G @ (_ctr(self.F) @ X))
+        return Y
 
 
 # ---------------------------------------------------------------------------------------
@@ -137,9 +168,15 @@ def nested_dissection_nodes(N: int, leaf: int = 64) -> np.ndarray:
 
 
 class GlobalPreconditioner:
-    """P = -K R with K = (H^(1) - eps_bar S)^{-1}, factorised once (Sec. 4, Eq. ldl)."""
+    """P = -K R with K = (H^(1) - eps_bar S)^{-1}, factorised once (Sec. 4, Eq. ldl).
 
-    def __init__(self, A, dof_node=None, grid=None):
+    A is the sparse H^(1) - eps_bar S, or a ShiftedHamiltonian whose local part is that matrix
+    and whose F, G give the nonlocal term (R17): then the factor is that of the local part and
+    SMW steps 1-4 run here, once."""
+
+    def __init__(self, A, dof_node=None, grid=None, F=None, G=None):
+        if isinstance(A, ShiftedHamiltonian):
+            A, F, G = A.loc, A.F, A.G
         n = A.shape[0]
         if dof_node is not None and grid is not None:
             N = grid[0]
@@ -155,6 +192,16 @@ class GlobalPreconditioner:
         d = self.lu.U.diagonal()
         if np.any(d.real <= 0):
             raise np.linalg.LinAlgError("H - eps_bar S is not positive definite")
+        # SMW steps 1-4 (Sec. 4), only with a nonlocal term
+        self.Fhat = self.Fsmw = None
+        if F is not None and F.shape[1] > 0:
+            F = np.asarray(F)
+            k = F.shape[1]
+            Fhat = self.solve(F)                               # step 1: Fhat = (H_loc - eps_bar S)^{-1} F
+            F = F @ np.asarray(G)                              # step 2: F := F G
+            T = np.eye(k) + _ctr(F) @ Fhat                     # step 3: T = I + F^H Fhat
+            F = _ctr(np.linalg.solve(T, _ctr(F)))              # step 4: F := F T^{-H}
+            self.Fhat, self.Fsmw = Fhat, F
 
     def solve(self, R):
         R = np.asarray(R)
@@ -163,8 +210,11 @@ class GlobalPreconditioner:
         return out
 
     def apply(self, R):
-        """Step 6(a): P = -K R."""
-        return -self.solve(R)
+        """Step 6(a): P = -K R (SMW steps 5-6 with a nonlocal term)."""
+        P = -self.solve(R)                                     # step 5
+        if self.Fhat is not None:
+            P = P - self.Fhat @ (_ctr(self.Fsmw) @ P)          # step 6
+        return P
 
 
 # ---------------------------------------------------------------------------------------
@@ -299,10 +349,12 @@ class Result:
 
 
 def make_shifted(problem):
-    """R4: Hs = H - sigma0 S with sigma0 = eps_bar; returns (Hs, S, sigma0)."""
+    """R4: Hs = H - sigma0 S with sigma0 = eps_bar; returns (Hs, S, sigma0), Hs a
+    ShiftedHamiltonian (carrying the nonlocal term of the problem, if any)."""
     H, S = problem.scipy_pair()
     sigma0 = problem.eps_bar
-    return (H - sigma0 * S).tocsr(), S.tocsr(), sigma0
+    F = getattr(problem, "F", None)
+    return ShiftedHamiltonian((H - sigma0 * S).tocsr(), F, getattr(problem, "G", None)), S.tocsr(), sigma0
 
 
 def labpsd(problem, nev, tol, X0=None, opts: Options | None = None, seed=1,
@@ -315,8 +367,8 @@ def labpsd(problem, nev, tol, X0=None, opts: Options | None = None, seed=1,
     Hs, S, sigma0 = make_shifted(problem)
     n = problem.n
     if precond is None and opts.use_global:
-        precond = GlobalPreconditioner(Hs - (problem.eps_bar - sigma0) * S,
-                                       problem.dof_node, problem.grid)
+        precond = GlobalPreconditioner((Hs.loc - (problem.eps_bar - sigma0) * S).tocsr(),
+                                       problem.dof_node, problem.grid, F=Hs.F, G=Hs.G)
     if X0 is None:
         from paper_1308_2445_gb300.pufe_inputs import seed_normal_block
         X0 = seed_normal_block(seed, n, w)

@@ -25,6 +25,14 @@ Definitions (all integrals by 3x3x3 Gauss-Legendre quadrature per element):
     distances are >= 2 r_c (each enriched node then belongs to one atom).
   * Bloch k: a basis function wrapped by the lattice translation T picks up the
     phase exp(i k.T); H and S become complex Hermitian.
+  * nonlocal term (optional, Sec. 4, Eq. fgf): H_nl = F G F^T with
+    F_ij = int psi_i beta_j for n_proj projectors per atom -- an s channel
+    beta = c exp(-d^2 / w_p) f(d) and, for n_proj = 4, three p channels
+    c' d_x exp(-d^2 / w_p) f(d) (likewise y, z) -- with d the minimum-image offset
+    from the atom, the smooth cutoff f(d) = (1 - d^2 / r_p^2)^2 for d < r_p (0
+    beyond, so F is sparse), and c, c' normalising int beta^2 = 1 on the
+    quadrature.  G is diagonal: E_s on the s channel, E_p on the p channels
+    (positive, so eps_bar = V_min - 0.1 still bounds the spectrum from below).
 
 Random numbers: SplitMix64 (Steele, Lea, Flood 2014), used as a counter-based
 generator: draw t of stream s is mix(key(seed, s) + (t+1) * 0x9E3779B97F4A7C15).
@@ -106,6 +114,8 @@ class Problem:
     eps_bar: float           # global shift below the spectrum: v_min - 0.1
     kpt: tuple | None = None
     params: dict = dataclasses.field(default_factory=dict)
+    F: np.ndarray | None = None  # n x k nonlocal projector matrix (None: no nonlocal term)
+    G: np.ndarray | None = None  # k x k symmetric coupling of the projectors
 
     @property
     def nnz(self) -> int:
@@ -169,14 +179,21 @@ def place_atoms(seed: int, n_atoms: int, r_c: float, max_draws: int = 100000) ->
 
 def generate(n_el: int, n_atoms: int, n_enr: int, r_c: float, seed: int, *, Z: float = 4.0,
              width: float = 0.05, v0: float = 0.0, kpt=None, v_noise: float = 0.0,
-             noise_seed: int | None = None, atoms: np.ndarray | None = None) -> Problem:
+             noise_seed: int | None = None, atoms: np.ndarray | None = None, n_proj: int = 0,
+             proj_width: float = 0.01, proj_rc: float = 0.2, proj_energies=(1.0, 0.5)) -> Problem:
     """Assemble (H, S) on an n_el^3 periodic Q1 mesh of the unit cube.
 
     kpt: Bloch wave vector (3 floats) or None for the Gamma point (real matrices).
     v_noise: if > 0, V at every quadrature point is multiplied by (1 + v_noise * N(0,1))
              with normals from (noise_seed, STREAM_NOISE) -- an SCF-style follow-up that
              changes H but not S.
+    n_proj: nonlocal projectors per atom (0: none, 1: s, 4: s and p); proj_width = w_p,
+            proj_rc = r_p, proj_energies = (E_s, E_p).  Real (Gamma point) problems only.
     """
+    if n_proj not in (0, 1, 4):
+        raise ValueError("n_proj must be 0, 1 or 4")
+    if n_proj and kpt is not None:
+        raise ValueError("the nonlocal term is generated for real (Gamma point) problems only")
     N = int(n_el)
     h = 1.0 / N
     nn = N ** 3
@@ -303,6 +320,43 @@ def generate(n_el: int, n_atoms: int, n_enr: int, r_c: float, seed: int, *, Z: f
         rows.append(gdof[ee, aa]); cols.append(gdof[ee, bb])
         hv.append(He[ee, aa, bb]); sv.append(Me[ee, aa, bb])
 
+    # ---- nonlocal projectors F_ij = int psi_i beta_j (optional) --------------------------
+    Fnl = Gnl = None
+    if n_proj > 0 and atoms.shape[0] > 0:
+        kp = atoms.shape[0] * n_proj
+        Fnl = np.zeros((n, kp))
+        if enr_nodes.size > 0:
+            tpos = np.full(nn, -1, dtype=np.int64)
+            tpos[touched] = np.arange(touched.size)
+        for ia, a in enumerate(atoms):
+            d = rq - a
+            d -= np.round(d)
+            r2 = np.einsum("eqd,eqd->eq", d, d)
+            sup = np.nonzero((r2 < proj_rc * proj_rc).any(axis=1))[0]           # elements meeting the support
+            dd, rr = d[sup], r2[sup]
+            cut = np.where(rr < proj_rc * proj_rc, (1.0 - rr / (proj_rc * proj_rc)) ** 2, 0.0)
+            g = np.exp(-rr / proj_width) * cut                                     # (Es, 27)
+            chans = [g, dd[..., 0] * g, dd[..., 1] * g, dd[..., 2] * g][:n_proj]
+            beta = np.stack(chans, axis=-1)                                        # (Es, 27, n_proj)
+            norm2 = np.einsum("eqc,eqc,q->c", beta, beta, wJ)
+            bw = beta * (wJ[None, :, None] / np.sqrt(norm2)[None, None, :])        # weighted, normalised
+            col0 = ia * n_proj
+            nodal = np.einsum("aq,eqc->eac", Nref, bw)                             # (Es, 8, n_proj)
+            for c in range(n_proj):
+                np.add.at(Fnl[:, col0 + c], gnode[sup].ravel(), nodal[:, :, c].ravel())
+            if enr_nodes.size > 0:
+                tp = tpos[sup]
+                sel = np.nonzero(tp >= 0)[0]
+                if sel.size:
+                    te = tp[sel]
+                    enr = np.einsum("efq,eqc->efc", B[te, 8:], bw[sel])              # (Et, 8J, n_proj)
+                    ok = valid[te, 8:]
+                    rws = gdof[te, 8:][ok]
+                    for c in range(n_proj):
+                        np.add.at(Fnl[:, col0 + c], rws, enr[:, :, c][ok])
+        ene = np.array([proj_energies[0]] + [proj_energies[1]] * 3)[:n_proj]
+        Gnl = np.diag(np.tile(ene, atoms.shape[0]))
+
     rows = np.concatenate(rows).astype(np.int64)
     cols = np.concatenate(cols).astype(np.int64)
     hv = np.concatenate(hv)
@@ -325,11 +379,12 @@ def generate(n_el: int, n_atoms: int, n_enr: int, r_c: float, seed: int, *, Z: f
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(urow, minlength=n), out=row_ptr[1:])
     params = dict(n_el=N, n_atoms=int(atoms.shape[0]), n_enr=n_enr, r_c=r_c, seed=seed, Z=Z,
-                  width=width, v0=v0, v_noise=v_noise)
+                  width=width, v0=v0, v_noise=v_noise, n_proj=n_proj, proj_width=proj_width,
+                  proj_rc=proj_rc, proj_energies=tuple(proj_energies))
     return Problem(n=n, row_ptr=row_ptr, col_idx=ucol, h_val=hsum, s_val=ssum,
                    dof_node=dof_node, dof_cluster=dof_cluster, grid=(N, N, N), atoms=atoms,
                    v_min=v_min, eps_bar=v_min - 0.1, kpt=None if kpt is None else tuple(kvec),
-                   params=params)
+                   params=params, F=Fnl, G=Gnl)
 
 
 # ---- named workloads -------------------------------------------------------------------
@@ -348,6 +403,11 @@ def medium_case(seed: int = 1) -> Problem:
 
 
 MEDIUM_NEV = 64
+
+
+def medium_nonlocal_case(seed: int = 1) -> Problem:
+    """The 32^3 medium case with a nonlocal term: s and p projectors on each of the 8 atoms (k = 32)."""
+    return generate(32, 8, 4, 0.15, seed, n_proj=4)
 
 
 def large_case(seed: int = 1) -> Problem:

@@ -344,7 +344,7 @@ def test_spmm_pair_f32_scaled(mid, k):
     p, s = mid
     Hs, S, _ = L.make_shifted(p)
     d = s.dscale()
-    Hh = (Hs.multiply(d[:, None]).multiply(d[None, :])).tocsr()
+    Hh = (Hs.loc.multiply(d[:, None]).multiply(d[None, :])).tocsr()
     Sh = (S.multiply(d[:, None]).multiply(d[None, :])).tocsr()
     X = pi.seed_normal_block(40 + k, p.n, k)
     HX, SX = fbuf(p.n, k), fbuf(p.n, k)
@@ -368,7 +368,7 @@ def test_precond_f32_scaled(mid, k):
     s.precond_apply_f32(fdev(R), P)
     Pg = host(P).astype(np.float64)
     ref = -K.solve(R / d[:, None]) / d[:, None]
-    Ah = (Hs.multiply(d[:, None]).multiply(d[None, :])).tocsr()
+    Ah = (Hs.loc.multiply(d[:, None]).multiply(d[None, :])).tocsr()
     err = Pg - ref
     num = np.sqrt(np.einsum("ij,ij->j", err, Ah @ err))
     den = np.sqrt(np.einsum("ij,ij->j", ref, Ah @ ref))
