@@ -142,6 +142,21 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* S, const hbsd_local_blocks* l
  * first H (Sec. 4: K built from H^(1) and reused through the SCF). */
 int hbsd_update_H(hbsd_handle* h, const double* H_val);
 
+/* Nonlocal term of the Hamiltonian (Sec. 4, Eq. fgf): from now on the session's H is
+ * H_loc + F G F^T, with H_loc the CSR values given to hbsd_create / hbsd_update_H.
+ * F: host, row-major n x k (leading dimension ldf >= k), the projector matrix; only its
+ * nonzero entries are stored, so projectors of compact support make its products cheap.
+ * G: host, row-major k x k, symmetric (HBSD_ERR_ARG if |G_lm - G_ml| > 1e-14 max|G|).
+ * Both are copied; k = 0 removes the term (F, G may then be NULL).  k <= 4096.
+ * Every product with H (steps 3 and 7, the MINRES operator of step 6(b), hbsd_spmm_pair,
+ * hbsd_spmm_shifted, the FP32 entry points on the scaled pencil) adds F (G (F^T X)); the
+ * global preconditioner becomes the Sherman-Morrison-Woodbury inverse of
+ * H_loc^(1) - eps_bar S + F G F^T (Sec. 4, steps 1-6): Fhat = K F and M = (I + G F^T Fhat)^{-1} G
+ * are formed on first use with the factor of the local part and kept until the next call.
+ * HBSD_ERR_ARG there if I + G F^T Fhat is singular.  The factor itself is unchanged (it is
+ * that of the local part).  Waits for the session's stream; not to be called during a solve. */
+int hbsd_set_nonlocal(hbsd_handle* h, int k, const double* F, int64_t ldf, const double* G);
+
 /* LABPSD (Sec. 3 outline, steps 1-12): lowest nev eigenpairs to Res_max <= tol (remark 2).
  * X0: host, row-major n x (nev + m0) start block (remark 1), or NULL for seed-normal draws,
  * or the previous solve's block if warm != 0 (X0 must then be NULL).  lambda: host, nev
@@ -268,6 +283,13 @@ typedef struct {
     double tol;
     const double* X0;   /* host, n x (nev + m0) row-major, copied; or NULL (seeded start) */
     int warm;           /* follow-up only: start from the session's last block (X0 = NULL) */
+    /* new problem only: nonlocal term F G F^T as in hbsd_set_nonlocal (nl_k = 0: none);
+     * F n x nl_k row-major with leading dimension nl_ldf, G nl_k x nl_k; both copied.  A
+     * follow-up keeps its session's term. */
+    int nl_k;
+    const double* nl_F;
+    int64_t nl_ldf;
+    const double* nl_G;
 } hbsd_request;
 
 typedef struct {

@@ -204,6 +204,45 @@ template <class T>
 int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double eta, int maxit, T* X,
                  int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st);
 
+// ---- nonlocal low-rank term H_nl = F G F^T (Eq. fgf) and its SMW data (Sec. 4) -----------
+// F is kept by its nonzero entries (projectors of compact support make it sparse) in two
+// orders: by projector (F^T X products) and by row (F Z products).  SMW steps 1-4 are held as
+// Fh = -(H_loc - eps_bar S)^{-1} F (dense) and M = T^{-1} G, so that step 6 reads
+// P -= Fhat (M (F^T P)); this equals the stored F := F G T^{-H} of step 4 and keeps F sparse.
+struct Nonlocal {
+    int k = 0;                      // projectors (0: no nonlocal term)
+    int version = 0;                // bumped by every nl_set (invalidates derived data)
+    int64_t nnz = 0, nfr = 0;       // stored entries of F; rows with entries
+    int n_items = 0;                // F^T X work items
+    std::vector<int64_t> h_rptr;    // host copies used to build the fused-MINRES index
+    std::vector<int32_t> h_rcol, h_frows, h_gptr, h_gcol;
+    std::vector<double> h_rval, h_gval;
+    DBuf<int64_t> cptr, item_e;     // F by projector; entry range of each work item
+    DBuf<int32_t> crow, item_ptr;   // row of each entry; first work item of each projector
+    DBuf<double> cval;
+    DBuf<float> cval32;             // D F (scaled pencil of the FP32 paths)
+    DBuf<int64_t> rptr;             // F by row, over all n rows
+    DBuf<int32_t> rcol, frows;      // projector of each entry; rows with entries
+    DBuf<double> rval;
+    DBuf<float> rval32;
+    bool scaled32 = false;
+    DBuf<int32_t> gptr, gcol;       // G by rows
+    DBuf<double> gval;
+    int64_t ldf = 0;                // SMW: Fh (n x k, ld ldf); M = T^{-1} G dense (CSR form)
+    bool smw64 = false, smw32 = false;
+    DBuf<double> Fh, M64, M32;
+    DBuf<float> Fh32;
+    DBuf<int32_t> mptr, mcol;
+    DBuf<double> part, z, tmat;     // work
+    DBuf<float> part32, z32;
+    DBuf<int> info;
+    // fused-MINRES index for one grid size (see minres.cu)
+    int mr_grid = -1, mr_version = -1, mr_nslots = 0, mr_nneed = 0;
+    DBuf<int64_t> ch_row_off, pan_off;
+    DBuf<int32_t> ch_lptr, cl_ptr, cl_slot, nb_ptr, nb_napply, nb_l, lmap;
+    DBuf<double> pan, mr_part, zv, zg;
+};
+
 // ---- session -----------------------------------------------------------------------
 // Block buffers of one solve (steps 1-11), kept in the session between solves.
 template <class T>
@@ -247,13 +286,23 @@ struct Session {
     bool opt_df64 = true;       // mixed form: Gram and update in double-float (HBSD_NO_DF64=1 turns off)
     double dbg_rr_kernel_ms = 0.0, dbg_rr_host_ms = 0.0, dbg_rr_wake_ms = 0.0;   // Rayleigh-Ritz timing accounting (HBSD_RRDBG)
     int mr_blk_grid = 0;
+    std::vector<int64_t> h_mr_blk;   // host copy of mr_blk
     // mixed-precision preconditioner buffers (FP32 scaled R and P)
     DBuf<float> r32, p32, xa32, ra32, sh32;
     // warm-start state
     DBuf<double> psi_keep;
     int keep_w = 0;
     int64_t keep_ld = 0;
+    Nonlocal nl;                // H_nl = F G F^T (k = 0: none)
 };
+
+// nonlocal term (nonlocal.cu)
+int nl_set(Session* s, int k, const double* F, int64_t ldf, const double* G);
+template <class T>   // Y += F G F^T X (T = float: the scaled pencil, D F G F^T D)
+int nl_apply_add(Session* s, const T* X, int64_t ldx, int w, T* Y, int64_t ldy, cudaStream_t st);
+template <class T>   // SMW step 6 on P = -K R (T = float: scaled P^ of the mixed form)
+int nl_smw_correct(Session* s, T* P, int64_t ldp, int p, cudaStream_t st);
+int nl_minres_index(Session* s, int grid, const std::vector<int64_t>& blk, int64_t kp);
 
 // ---- small utilities -----------------------------------------------------------------
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }

@@ -16,6 +16,11 @@
 // updating and leaves the SpMM.  The grid barrier is an arrival counter whose wait is bounded
 // by %globaltimer: a block that waits past the limit raises the error flag and every block
 // returns; the host reports HBSD_ERR_TIMEOUT.
+// With a nonlocal term H_nl = F G F^T (Eq. fgf) phase A adds F (G (F^T v_j)) to each row.
+// F^T v_{j+1} = F^T u_j / beta_{j+1} is gathered in phase C, when every u_j is final: block c
+// sums the rows of its chunk of F against U into per-chunk partials; after the barrier each
+// block reduces, in a fixed order, only the projectors its own rows meet (and those coupled to
+// them through G), so the step keeps its three barriers.  The start takes one more.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -103,6 +108,28 @@ struct MrArgs {
     unsigned* bar;
     int* err;
     unsigned long long* stamps;   // nullable: phase times (ns) seen by block 0, for tracing
+    // nonlocal term (nl_k = 0: none); index built by nl_minres_index for this grid
+    int nl_k;
+    const int64_t* nl_rptr;       // F by row (all n rows)
+    const int32_t* nl_rcol;
+    const double* nl_rval;
+    const int32_t* nl_frows;      // rows with F entries
+    const int64_t* nl_ch_row_off; // chunk c: frows[ch_row_off[c] .. ch_row_off[c+1])
+    const int32_t* nl_ch_lptr;    // chunk c: projector slots [ch_lptr[c], ch_lptr[c+1])
+    const double* nl_pan;         // chunk c: rows x slots panel at pan_off[c]
+    const int64_t* nl_pan_off;
+    const int32_t* nl_cl_ptr;     // projector l: chunk slots cl_slot[cl_ptr[l] .. cl_ptr[l+1])
+    const int32_t* nl_cl_slot;
+    const int32_t* nl_nb_ptr;     // block b: projectors nb_l[nb_ptr[b] ..], the first napply[b] applied
+    const int32_t* nl_nb_napply;
+    const int32_t* nl_nb_l;
+    const int32_t* nl_lmap;       // [b * nl_k + l]: local index of projector l in block b, or -1
+    const int32_t* nl_gptr;       // G by rows
+    const int32_t* nl_gcol;
+    const double* nl_gval;
+    double* nl_part;              // [chunk slot][kp] partials of F^T U
+    double* nl_zv;                // [block slot][kp] F^T v
+    double* nl_zg;                // [block slot][kp] G F^T v
 };
 
 template <class T> struct Pair;
@@ -184,6 +211,71 @@ size_t mr_smem_bytes(int k) {
            (size_t)(MR_IFIELDS * k + 2) * sizeof(int);
 }
 
+// Nonlocal row term sum_e F(row, l_e) (G F^T v)(l_e, j) from this block's reduced values.
+__device__ __forceinline__ double nl_row(const MrArgs& a, int64_t row, int j) {
+    double s = 0.0;
+    const int64_t e1 = a.nl_rptr[row + 1];
+    const int64_t nb0 = a.nl_nb_ptr[blockIdx.x];
+    const int32_t* lm = a.nl_lmap + (int64_t)blockIdx.x * a.nl_k;
+    for (int64_t e = a.nl_rptr[row]; e < e1; ++e)
+        s = fma(a.nl_rval[e], a.nl_zg[(nb0 + lm[a.nl_rcol[e]]) * a.kp + j], s);
+    return s;
+}
+
+// Chunk partials of F^T Src for the columns jcol(0 .. cnt-1) with keep(j): block c writes
+// nl_part[(ch_lptr[c] + t) * kp + j] = scale(j) * sum_r panel(r, t) Src(frows[r], j).
+template <class J, class K, class Sc>
+__device__ void nl_chunk_partial(const MrArgs& a, const double* Src, int64_t lds, int cnt, J&& jcol, K&& keep,
+                                 Sc&& scale) {
+    const int c = blockIdx.x;
+    const int l0 = a.nl_ch_lptr[c], nlc = a.nl_ch_lptr[c + 1] - l0;
+    const int64_t r0 = a.nl_ch_row_off[c], nr = a.nl_ch_row_off[c + 1] - r0;
+    const double* pan = a.nl_pan + a.nl_pan_off[c];
+    const int total = nlc * cnt;
+    for (int pidx = threadIdx.x; pidx < total; pidx += blockDim.x) {
+        const int t = pidx / cnt, q = pidx - t * cnt;
+        const int j = jcol(q);
+        if (!keep(j)) continue;
+        double a0 = 0.0, a1 = 0.0;
+        int64_t r = 0;
+        for (; r + 1 < nr; r += 2) {
+            a0 = fma(pan[r * nlc + t], Src[(int64_t)a.nl_frows[r0 + r] * lds + j], a0);
+            a1 = fma(pan[(r + 1) * nlc + t], Src[(int64_t)a.nl_frows[r0 + r + 1] * lds + j], a1);
+        }
+        if (r < nr) a0 = fma(pan[r * nlc + t], Src[(int64_t)a.nl_frows[r0 + r] * lds + j], a0);
+        a.nl_part[(int64_t)(l0 + t) * a.kp + j] = (a0 + a1) * scale(j);
+    }
+}
+
+// This block's F^T v (projectors it needs) from the chunk partials in chunk order, then
+// G F^T v for the projectors its rows apply.  Block-uniform control flow.
+template <class J>
+__device__ void nl_reduce(const MrArgs& a, int cnt, J&& jcol) {
+    const int b = blockIdx.x;
+    const int n0 = a.nl_nb_ptr[b], nn = a.nl_nb_ptr[b + 1] - n0, napp = a.nl_nb_napply[b];
+    if (nn == 0) return;
+    for (int pidx = threadIdx.x; pidx < nn * cnt; pidx += blockDim.x) {
+        const int t = pidx / cnt, q = pidx - t * cnt;
+        const int j = jcol(q);
+        const int l = a.nl_nb_l[n0 + t];
+        double s = 0.0;
+        for (int u = a.nl_cl_ptr[l]; u < a.nl_cl_ptr[l + 1]; ++u) s += a.nl_part[(int64_t)a.nl_cl_slot[u] * a.kp + j];
+        a.nl_zv[(int64_t)(n0 + t) * a.kp + j] = s;
+    }
+    __syncthreads();
+    const int32_t* lm = a.nl_lmap + (int64_t)b * a.nl_k;
+    for (int pidx = threadIdx.x; pidx < napp * cnt; pidx += blockDim.x) {
+        const int t = pidx / cnt, q = pidx - t * cnt;
+        const int j = jcol(q);
+        const int l = a.nl_nb_l[n0 + t];
+        double s = 0.0;
+        for (int e = a.nl_gptr[l]; e < a.nl_gptr[l + 1]; ++e)
+            s = fma(a.nl_gval[e], a.nl_zv[(int64_t)(n0 + lm[a.nl_gcol[e]]) * a.kp + j], s);
+        a.nl_zg[(int64_t)(n0 + t) * a.kp + j] = s;
+    }
+    __syncthreads();
+}
+
 // Shifted SpMM of one pass over this block's slot range: thread (r, c) takes the slots
 // b0 + r, b0 + r + rb, ... and column j = jcol(c0 + c); f(row, j, y) receives
 // y = ((Hs - e_j S) Xin)(row, j).
@@ -210,7 +302,11 @@ __device__ __forceinline__ void spmm_pass(const MrArgs& a, const P* hs, const T*
             as = fma(hv.y, x, as);
         }
         const int row = a.slot_row[slot];
-        if (row >= 0) f((int64_t)row, j, ah - ej * as);
+        if (row >= 0) {
+            T y = ah - ej * as;
+            if (a.nl_k) y += (T)nl_row(a, row, j);
+            f((int64_t)row, j, y);
+        }
     }
 }
 
@@ -262,6 +358,13 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
     auto identity = [](int pos) { return pos; };
     auto active_col = [&](int pos) { return S.g(I_ACT)[pos]; };
 
+    // ---- nonlocal: F^T X for the start product ----
+    if (a.nl_k) {
+        nl_chunk_partial(a, reinterpret_cast<const double*>(X), a.ldx, k, identity, [](int) { return true; },
+                         [](int) { return 1.0; });
+        if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+        nl_reduce(a, k, identity);
+    }
     // ---- start: U = A_e X, V = r0 = -R - U, ||r0||^2 and ||R||^2 per column ----
     for (int c0 = 0; c0 < k; c0 += MR_PASS) {
         const Pass p = make_pass(c0, k);
@@ -295,17 +398,21 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
         S.g(I_CONT)[j] = S.g(I_ACTIVE)[j];
     }
     __syncthreads();
-    // v_1 = r0 / beta_1 for the active columns; v_0 = w_0 = w_{-1} = 0
+    // v_1 = r0 / beta_1 for the active columns, written to U (V keeps r0, which the nonlocal
+    // partials read from every block); v_0 = w_0 = w_{-1} = 0.  V and U swap roles below.
     for (int c0 = 0; c0 < k; c0 += MR_PASS) {
         const Pass p = make_pass(c0, k);
         rows_pass(a, p, identity, [&](int64_t i, int j) {
             const int64_t o = i * ld + j;
-            if (S.g(I_ACTIVE)[j]) V[o] = (T)((double)V[o] * S.f(F_BINV)[j]);
+            U[o] = S.g(I_ACTIVE)[j] ? (T)((double)V[o] * S.f(F_BINV)[j]) : V[o];
             Vp[o] = T(0);
             Wp[o] = T(0);
             Wpp[o] = T(0);
         });
     }
+    if (a.nl_k)
+        nl_chunk_partial(a, reinterpret_cast<const double*>(V), ld, k, identity,
+                         [&](int j) { return S.g(I_ACTIVE)[j] != 0; }, [&](int j) { return S.f(F_BINV)[j]; });
     if (threadIdx.x == 0) {
         int na = 0;
         for (int j = 0; j < k; ++j)
@@ -315,10 +422,16 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
     mark(0);
     if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
     mark(4);
+    {
+        T* t = V;
+        V = U;
+        U = t;
+    }
 
     for (int step = 1; step <= a.maxit && S.nact()[0] > 0; ++step) {
         const int na = S.nact()[0];
         // ---- A: U = A_e V on the active columns, partial alpha ----
+        if (a.nl_k) nl_reduce(a, na, active_col);
         for (int c0 = 0; c0 < na; c0 += MR_PASS) {
             const Pass p = make_pass(c0, na);
             double acc = 0.0;
@@ -383,6 +496,10 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
             }
         }
         __syncthreads();
+        // F^T v_{j+1} = F^T u_j / beta_{j+1} for the columns that go on (U is final here)
+        if (a.nl_k && step < a.maxit)
+            nl_chunk_partial(a, reinterpret_cast<const double*>(U), ld, na, active_col,
+                             [&](int j) { return S.g(I_CONT)[j] != 0; }, [&](int j) { return S.f(F_BINV)[j]; });
         for (int c0 = 0; c0 < na; c0 += MR_PASS) {
             const Pass p = make_pass(c0, na);
             rows_pass(a, p, active_col, [&](int64_t i, int j) {
@@ -422,7 +539,6 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
 
 template <class T> static DBuf<T>& mr_vecs(Session* s);
 template <> DBuf<double>& mr_vecs<double>(Session* s) { return s->mr_d; }
-template <> DBuf<float>& mr_vecs<float>(Session* s) { return s->mr_f; }
 
 // X (n x k, ldx): start vectors on entry, refined vectors on exit.  R: residual columns.
 // e: shifts eps_j relative to sigma0 (device, k entries of T).  steps: device ints (nullable).
@@ -479,8 +595,11 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         }
         HBSD_TRY(s->mr_blk.alloc(grid + 1));
         HBSD_CUDA(cudaMemcpy(s->mr_blk.p, blk.data(), (grid + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        s->h_mr_blk = std::move(blk);
         s->mr_blk_grid = grid;
     }
+    const bool nl = s->nl.k > 0 && s->nl.nnz > 0;
+    if (nl) HBSD_TRY(nl_minres_index(s, grid, s->h_mr_blk, kp));
     HBSD_CUDA(cudaMemsetAsync(s->mr_any.p, 0, 4 * sizeof(int), st));
     T* V = mr_vecs<T>(s).p;
     MrArgs a;
@@ -520,6 +639,16 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         HBSD_CUDA(cudaMemsetAsync(s->mr_stamps.p, 0, 8 * sizeof(unsigned long long), st));
         a.stamps = s->mr_stamps.p;
     }
+    a.nl_k = nl ? s->nl.k : 0;
+    {
+        Nonlocal& q = s->nl;
+        a.nl_rptr = q.rptr.p; a.nl_rcol = q.rcol.p; a.nl_rval = q.rval.p; a.nl_frows = q.frows.p;
+        a.nl_ch_row_off = q.ch_row_off.p; a.nl_ch_lptr = q.ch_lptr.p; a.nl_pan = q.pan.p; a.nl_pan_off = q.pan_off.p;
+        a.nl_cl_ptr = q.cl_ptr.p; a.nl_cl_slot = q.cl_slot.p;
+        a.nl_nb_ptr = q.nb_ptr.p; a.nl_nb_napply = q.nb_napply.p; a.nl_nb_l = q.nb_l.p; a.nl_lmap = q.lmap.p;
+        a.nl_gptr = q.gptr.p; a.nl_gcol = q.gcol.p; a.nl_gval = q.gval.p;
+        a.nl_part = q.mr_part.p; a.nl_zv = q.zv.p; a.nl_zg = q.zg.p;
+    }
     void* args[] = {&a};
     HBSD_CUDA(cudaLaunchCooperativeKernel((const void*)k_minres<T>, dim3(grid), dim3(MR_THREADS), args, smem, st));
     HBSD_LAUNCHED(s);
@@ -545,7 +674,5 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
 
 template int minres_batch<double>(Session*, const double*, int64_t, const double*, int, double, int, double*,
                                   int64_t, int*, int64_t*, cudaStream_t);
-template int minres_batch<float>(Session*, const float*, int64_t, const float*, int, double, int, float*,
-                                 int64_t, int*, int64_t*, cudaStream_t);
 
 }  // namespace hbsd

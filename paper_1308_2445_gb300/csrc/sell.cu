@@ -283,16 +283,19 @@ static int spmm_launch(Session* s, const Sell& m, const T* X, int64_t ldx, int k
     return 0;
 }
 
+// Both add the nonlocal term F G F^T X of the session (Eq. fgf) to the H product.
 template <class T>
 int spmm_pair(Session* s, const Sell& m, const T* X, int64_t ldx, int k, T* HX, int64_t ldhx,
               T* SX, int64_t ldsx, cudaStream_t st) {
-    return spmm_launch<T, 0>(s, m, X, ldx, k, HX, ldhx, SX, ldsx, nullptr, st);
+    HBSD_TRY((spmm_launch<T, 0>(s, m, X, ldx, k, HX, ldhx, SX, ldsx, nullptr, st)));
+    return nl_apply_add<T>(s, X, ldx, k, HX, ldhx, st);
 }
 
 template <class T>
 int spmm_shifted(Session* s, const Sell& m, const T* X, int64_t ldx, int k, const T* e, T* Y,
                  int64_t ldy, cudaStream_t st) {
-    return spmm_launch<T, 1>(s, m, X, ldx, k, Y, ldy, nullptr, 0, e, st);
+    HBSD_TRY((spmm_launch<T, 1>(s, m, X, ldx, k, Y, ldy, nullptr, 0, e, st)));
+    return nl_apply_add<T>(s, X, ldx, k, Y, ldy, st);
 }
 
 template int spmm_pair<double>(Session*, const Sell&, const double*, int64_t, int, double*, int64_t,

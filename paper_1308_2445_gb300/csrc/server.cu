@@ -36,6 +36,8 @@ struct Request {
     std::vector<double> hval, sval;
     int32_t grid[3] = {0, 0, 0};
     hbsd_options opt{};
+    int nl_k = 0;                    // nonlocal term F (n x nl_k, row-major) and G
+    std::vector<double> nl_F, nl_G;
     // follow-up
     int64_t session_id = -1;
     std::vector<double> hval_new;
@@ -63,11 +65,13 @@ struct SessionRec {
     Clock::time_point last_use;
 };
 
-size_t estimate_bytes(int64_t n, int64_t nnz, int nev) {
+size_t estimate_bytes(int64_t n, int64_t nnz, int nev, int nl_k) {
     // matrix (index + (h, s) pair), factor panels and solve panels (FP64 + FP32), ~16 nnz
-    // of fill per nonzero for 3-D nested dissection, and ~16 FP64 blocks of n x (nev + m0)
+    // of fill per nonzero for 3-D nested dissection, ~16 FP64 blocks of n x (nev + m0), and
+    // with a nonlocal term the dense Fhat (FP64 + FP32) and its setup block
     const int64_t w = nev + std::max(3, (nev + 9) / 10);
-    return (size_t)(20 * nnz + 16 * 20 * nnz + (int64_t)16 * 8 * n * w + ((int64_t)64 << 20));
+    return (size_t)(20 * nnz + 16 * 20 * nnz + (int64_t)16 * 8 * n * w + (int64_t)20 * n * nl_k +
+                    ((int64_t)64 << 20));
 }
 
 }  // namespace
@@ -167,6 +171,13 @@ void run_request(hbsd_server* sv, Request& rq) {
             lb.dof_cluster = rq.dof_cluster.empty() ? nullptr : rq.dof_cluster.data();
             std::memcpy(lb.grid, rq.grid, sizeof(lb.grid));
             rc = hbsd_create(&H, &S, &lb, &rq.opt, stream, &h);
+            if (rc >= 0 && rq.nl_k > 0) {
+                rc = hbsd_set_nonlocal(h, rq.nl_k, rq.nl_F.data(), rq.nl_k, rq.nl_G.data());
+                if (rc < 0) {
+                    hbsd_destroy(h);
+                    h = nullptr;
+                }
+            }
             std::lock_guard<std::mutex> lk(sv->mu);
             if (rc < 0) {
                 cudaStreamDestroy(stream);
@@ -305,7 +316,16 @@ int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, dou
         if (rq->lb->dof_cluster) r->dof_cluster.assign(rq->lb->dof_cluster, rq->lb->dof_cluster + n);
         std::memcpy(r->grid, rq->lb->grid, sizeof(r->grid));
         r->opt = *rq->opt;
-        r->est_bytes = estimate_bytes(n, r->nnz, rq->nev);
+        if (rq->nl_k < 0 || (rq->nl_k > 0 && (!rq->nl_F || !rq->nl_G || rq->nl_ldf < rq->nl_k)))
+            return fail(HBSD_ERR_ARG, "nonlocal term: nl_F, nl_G required and nl_ldf >= nl_k");
+        if (rq->nl_k > 0) {
+            r->nl_k = rq->nl_k;
+            r->nl_F.resize((size_t)n * rq->nl_k);
+            for (int64_t i = 0; i < n; ++i)
+                std::memcpy(r->nl_F.data() + i * rq->nl_k, rq->nl_F + i * rq->nl_ldf, rq->nl_k * sizeof(double));
+            r->nl_G.assign(rq->nl_G, rq->nl_G + (size_t)rq->nl_k * rq->nl_k);
+        }
+        r->est_bytes = estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
         if (r->est_bytes > sv->opts.hbm_budget_bytes) return fail(HBSD_ERR_OOM, "request exceeds the server's memory budget");
     } else {   // follow-up of a resident session: new H values (optional), warm start or X0
         std::lock_guard<std::mutex> lk(sv->mu);

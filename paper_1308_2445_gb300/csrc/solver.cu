@@ -324,8 +324,10 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                                                                       S->A.dscale.p, +1);
             HBSD_LAUNCHED(S);
             HBSD_TRY(factor_solve<float>(S, S->F, S->r32.p, ldp, p, S->p32.p, ldp, st));
+            HBSD_TRY(nl_smw_correct<float>(S, S->p32.p, ldp, p, st));            // SMW step 6 (scaled)
         } else {
             HBSD_TRY(factor_solve<T>(S, S->F, B.RU.p, ldp, p, B.P.p, ldp, st));   // 6(a)
+            HBSD_TRY(nl_smw_correct<T>(S, B.P.p, ldp, p, st));                    // SMW step 6
         }
         tm.end(ti, st);
         stt.precond_cols += p;
@@ -705,6 +707,12 @@ int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out
 }
 
 // ---- step-level entry points ---------------------------------------------------------------
+int hbsd_set_nonlocal(hbsd_handle* h, int k, const double* F, int64_t ldf, const double* G) {
+    if (!h) return fail(HBSD_ERR_ARG, "bad arguments");
+    HBSD_CUDA(cudaStreamSynchronize(h->s.stream));   // no work of this session reads the old term any more
+    return nl_set(&h->s, k, F, ldf, G);
+}
+
 int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx, double* SX,
                    int64_t ldsx) {
     if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
@@ -720,7 +728,8 @@ int hbsd_spmm_pair_f32(hbsd_handle* h, const float* X, int64_t ldx, int k, float
 int hbsd_precond_apply_f32(hbsd_handle* h, const float* R, int64_t ldr, int k, float* P, int64_t ldp) {
     if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
     HBSD_TRY(factor_make_fp32(h->s.F, h->s.A.dscale.p, h->s.stream));
-    return factor_solve<float>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream);
+    HBSD_TRY(factor_solve<float>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
+    return nl_smw_correct<float>(&h->s, P, ldp, k, h->s.stream);
 }
 
 int hbsd_dscale(const hbsd_handle* h, double* d_host) {
@@ -744,7 +753,8 @@ int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double*
 
 int hbsd_precond_apply(hbsd_handle* h, const double* R, int64_t ldr, int k, double* P, int64_t ldp) {
     if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    return factor_solve<double>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream);
+    HBSD_TRY(factor_solve<double>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
+    return nl_smw_correct<double>(&h->s, P, ldp, k, h->s.stream);
 }
 
 int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k, double eta, int max_minres,

@@ -55,7 +55,9 @@ class hbsd_server_opts(C.Structure):
 class hbsd_request(C.Structure):
     _fields_ = [("H", C.POINTER(hbsd_csr)), ("S", C.POINTER(hbsd_csr)), ("lb", C.POINTER(hbsd_local_blocks)),
                 ("opt", C.POINTER(hbsd_options)), ("session_id", C.c_int64), ("H_val", C.POINTER(C.c_double)),
-                ("nev", C.c_int), ("tol", C.c_double), ("X0", C.POINTER(C.c_double)), ("warm", C.c_int)]
+                ("nev", C.c_int), ("tol", C.c_double), ("X0", C.POINTER(C.c_double)), ("warm", C.c_int),
+                ("nl_k", C.c_int), ("nl_F", C.POINTER(C.c_double)), ("nl_ldf", C.c_int64),
+                ("nl_G", C.POINTER(C.c_double))]
 
 
 class hbsd_result(C.Structure):
@@ -88,6 +90,7 @@ _SIGS = {
     "hbsd_create": (C.c_int, [C.POINTER(hbsd_csr), C.POINTER(hbsd_csr), C.POINTER(hbsd_local_blocks),
                               C.POINTER(hbsd_options), _P, C.POINTER(_P)]),
     "hbsd_update_H": (C.c_int, [_P, _D]),
+    "hbsd_set_nonlocal": (C.c_int, [_P, C.c_int, _D, C.c_int64, _D]),
     "hbsd_solve": (C.c_int, [_P, C.c_int, C.c_double, _D, C.c_int, _D, _D, C.POINTER(C.c_int),
                              C.POINTER(hbsd_stats)]),
     "hbsd_solve_device": (C.c_int, [_P, C.c_int, C.c_double, _P, C.c_int64, _P, _P, C.c_int64,
@@ -207,7 +210,23 @@ class Session:
 
     @classmethod
     def from_problem(cls, p, stream=None, **opts):
-        return cls(p.n, p.row_ptr, p.col_idx, p.h_val, p.s_val, p.dof_node, p.grid, p.eps_bar, stream=stream, **opts)
+        s = cls(p.n, p.row_ptr, p.col_idx, p.h_val, p.s_val, p.dof_node, p.grid, p.eps_bar, stream=stream, **opts)
+        if getattr(p, "F", None) is not None:
+            s.set_nonlocal(p.F, p.G)
+        return s
+
+    def set_nonlocal(self, F, G):
+        """hbsd_set_nonlocal: H := H_loc + F G F^T (F n x k, G k x k symmetric); F = None removes it."""
+        if F is None:
+            check(lib().hbsd_set_nonlocal(self.h, 0, None, 0, None), "hbsd_set_nonlocal")
+            return
+        Fc = np.ascontiguousarray(F, dtype=np.float64)
+        Gc = np.ascontiguousarray(G, dtype=np.float64)
+        k = Fc.shape[1]
+        if Fc.shape[0] != self.n or Gc.shape != (k, k):
+            raise ValueError("F must be n x k and G k x k")
+        check(lib().hbsd_set_nonlocal(self.h, int(k), Fc.ctypes.data_as(_D), int(k), Gc.ctypes.data_as(_D)),
+              "hbsd_set_nonlocal")
 
     def close(self):
         if getattr(self, "h", None):
@@ -374,6 +393,12 @@ class Server:
             lb = hbsd_local_blocks(dn.ctypes.data_as(C.POINTER(C.c_int32)), None, (C.c_int32 * 3)(*p.grid))
             op = options_default(sigma_bar=float(p.eps_bar), **opts)
             keep += [rp, ci, hv, sv, dn, H, S, lb, op]
+            if getattr(p, "F", None) is not None:
+                Fc = np.ascontiguousarray(p.F, dtype=np.float64)
+                Gc = np.ascontiguousarray(p.G, dtype=np.float64)
+                keep += [Fc, Gc]
+                rq.nl_k, rq.nl_ldf = int(Fc.shape[1]), int(Fc.shape[1])
+                rq.nl_F, rq.nl_G = Fc.ctypes.data_as(_D), Gc.ctypes.data_as(_D)
             rq.H, rq.S, rq.lb, rq.opt = C.pointer(H), C.pointer(S), C.pointer(lb), C.pointer(op)
             rq.session_id = -1
             n = p.n

@@ -1,6 +1,7 @@
 """Write the stored expected values of the GPU parity tests by running the CPU oracle only.
 
-  python tests/golden/make_golden.py medium   -> tests/golden/medium_seed1.json
+  python tests/golden/make_golden.py medium            -> tests/golden/medium_seed1.json
+  python tests/golden/make_golden.py medium_nonlocal   -> tests/golden/medium_nonlocal_seed1.json
 
 The medium workload (32^3 Q1 elements, 8 atoms, 4 enrichment dofs per node, nev = 64) takes the
 oracle a few minutes, too long to rerun inside the test suite; every value in the file comes
@@ -18,11 +19,14 @@ from oracle import labpsd as L  # noqa: E402
 from paper_1308_2445_gb300 import pufe_inputs as pi  # noqa: E402
 
 
-def medium(seed=1):
-    p = pi.medium_case(seed)
+def medium(seed=1, nonlocal_term=False):
+    p = pi.medium_nonlocal_case(seed) if nonlocal_term else pi.medium_case(seed)
     t0 = time.time()
     r = L.labpsd(p, pi.MEDIUM_NEV, 1e-8, seed=seed)
-    return dict(workload="32^3 Q1, 8 atoms, 4 enrichment dofs/node, r_c 0.15", seed=seed, n=p.n, nnz=p.nnz,
+    name = "32^3 Q1, 8 atoms, 4 enrichment dofs/node, r_c 0.15"
+    if nonlocal_term:
+        name += ", s+p projectors per atom (k = 32)"
+    return dict(workload=name, seed=seed, n=p.n, nnz=p.nnz,
                 nev=pi.MEDIUM_NEV, tol=1e-8, eps_bar=p.eps_bar, lam=[float(x) for x in r.lam],
                 E_all=[float(x) for x in r.E_all], iters=r.iters, converged=bool(r.converged),
                 res_history=[float(x) for x in r.res_history], minres_total=int(sum(int(s.sum()) for s in r.minres_steps)),
@@ -31,8 +35,8 @@ def medium(seed=1):
 
 if __name__ == "__main__":
     which = sys.argv[1] if len(sys.argv) > 1 else "medium"
-    if which == "medium":
-        out = medium(1)
-        with open(os.path.join(HERE, "medium_seed1.json"), "w") as f:
+    if which in ("medium", "medium_nonlocal"):
+        out = medium(1, nonlocal_term=which == "medium_nonlocal")
+        with open(os.path.join(HERE, f"{which}_seed1.json"), "w") as f:
             json.dump(out, f, indent=1)
         print("iters", out["iters"], "seconds", out["oracle_seconds"])

@@ -1,0 +1,346 @@
+"""GPU parity of the nonlocal term H = H_loc + F G F^T (Sec. 4, Eq. fgf) and its
+Sherman-Morrison-Woodbury preconditioner (Sec. 4, steps 1-6) against the CPU oracle, through
+the C ABI.
+
+Bars as for the local-only steps: FP64 block products to 1e-12 of the block's magnitude (they
+differ from the oracle only in summation order); the preconditioner and MINRES, which act through
+(H - eps S)^{-1} with kappa up to ~1e9, to 1e-6; whole solves to 1e-9 in the eigenvalues with
+outer iterations within +-1 (FP64) or +-10% (32^3 case, stored oracle values).  The FP32 forms on
+the scaled pencil to 2e-5 (products) and 1e-2 in the energy norm (preconditioner).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import labpsd as L
+from paper_1308_2445_gb300 import pufe_inputs as pi
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1308_2445_gb300 import build_lib
+    if not os.path.exists(build_lib.LIB):
+        build_lib.build()
+
+
+def hb():
+    from paper_1308_2445_gb300 import hbsd
+    return hbsd
+
+
+def dbuf(n, k):
+    t = torch.zeros(n, k + (k % 2), dtype=torch.float64, device="cuda")
+    return t[:, :k]
+
+
+def dev(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        return torch.from_numpy(a).cuda()
+    t = dbuf(a.shape[0], a.shape[1])
+    t.copy_(torch.from_numpy(a))
+    return t
+
+
+def fbuf(n, k):
+    t = torch.zeros(n, (k + 3) // 4 * 4, dtype=torch.float32, device="cuda")
+    return t[:, :k]
+
+
+def fdev(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    t = fbuf(a.shape[0], a.shape[1])
+    t.copy_(torch.from_numpy(a))
+    return t
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def coupled_G(k, seed):
+    """Symmetric G coupling every projector with every other, one negative eigenvalue."""
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((k, k)))
+    ev = np.linspace(0.2, 1.5, k)
+    ev[0] = -0.3
+    G = (Q * ev) @ Q.T
+    return 0.5 * (G + G.T)
+
+
+def with_G(p, G):
+    return pi.Problem(**{**p.__dict__, "G": G})
+
+
+@pytest.fixture(scope="module")
+def cases():
+    small = pi.generate(8, 2, 2, 0.25, 1, n_proj=4)                  # n = 646, k = 8
+    mid = pi.generate(12, 2, 4, 0.15, 3, n_proj=4)                   # k = 8, several chunks per projector
+    big = pi.generate(16, 4, 2, 0.12, 5, n_proj=4)                   # k = 16
+    return {"small": small, "small_coupled": with_G(small, coupled_G(8, 5)), "mid": mid,
+            "mid_coupled": with_G(mid, coupled_G(8, 7)), "big": big}
+
+
+def session(p, **opts):
+    return hb().Session.from_problem(p, **opts)
+
+
+@pytest.mark.parametrize("case", ["small", "small_coupled", "mid"])
+@pytest.mark.parametrize("k", [1, 7, 64, 71])
+def test_spmm_pair_nonlocal(cases, case, k):
+    p = cases[case]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    X = pi.seed_normal_block(20 + k, p.n, k)
+    HX, SX = dbuf(p.n, k), dbuf(p.n, k)
+    s.spmm_pair(dev(X), HX, SX)
+    rH, rS = L.spmm_pair(Hs, S, X)
+    HXg = host(HX)
+    assert relerr(HXg, rH) <= 1e-12 and relerr(host(SX), rS) <= 1e-12
+    # the GPU's nonlocal part on its own: F G F^T X, to the rounding of the whole product
+    nl = p.F @ (p.G @ (p.F.T @ X))
+    assert np.abs(nl).max() > 0
+    assert np.abs((HXg - Hs.loc @ X) - nl).max() <= 1e-12 * np.abs(rH).max()
+
+
+def test_spmm_shifted_nonlocal(cases):
+    p = cases["mid_coupled"]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    X = pi.seed_normal_block(5, p.n, 9)
+    e = np.linspace(-0.5, 2.0, 9)
+    Y = dbuf(p.n, 9)
+    s.spmm_shifted(dev(X), dev(e), Y)
+    ref = Hs @ X - (S @ X) * e[None, :]
+    assert relerr(host(Y), ref) <= 1e-12
+
+
+def test_set_nonlocal_off_again_is_the_local_product(cases):
+    p = cases["mid"]
+    s = session(p)
+    s.set_nonlocal(None, None)
+    q = pi.generate(12, 2, 4, 0.15, 3)
+    s0 = session(q)
+    X = pi.seed_normal_block(3, p.n, 16)
+    a, b = dbuf(p.n, 16), dbuf(p.n, 16)
+    s.spmm_pair(dev(X), a, dbuf(p.n, 16))
+    s0.spmm_pair(dev(X), b, dbuf(p.n, 16))
+    assert torch.equal(a, b)
+
+
+def test_set_nonlocal_rejects_bad_input(cases):
+    p = cases["small"]
+    s = session(p)
+    G = p.G.copy()
+    G[0, 1] = 0.3
+    with pytest.raises(hb().HbsdError) as e:
+        s.set_nonlocal(p.F, G)
+    assert e.value.code == hb().HBSD_ERR_ARG
+    F = p.F.copy()
+    F[3, 2] = np.nan
+    with pytest.raises(hb().HbsdError):
+        s.set_nonlocal(F, p.G)
+
+
+@pytest.mark.parametrize("case", ["small", "small_coupled", "mid", "mid_coupled"])
+def test_smw_preconditioner(cases, case):
+    p = cases[case]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    R = pi.seed_normal_block(9, p.n, 13)
+    P = dbuf(p.n, 13)
+    s.precond_apply(dev(R), P)
+    Pg = host(P)
+    Po = L.GlobalPreconditioner(Hs, p.dof_node, p.grid).apply(R)
+    assert relerr(Pg, Po) <= 1e-6
+    # it inverts the full operator: (H_loc - eps_bar S + F G F^T) P = -R
+    A = Hs.toarray()
+    anorm = np.abs(A).sum(axis=1).max()
+    assert np.abs(A @ Pg + R).max() <= 1e-10 * anorm * np.abs(Pg).max()
+
+
+def test_smw_preconditioner_f32_scaled(cases):
+    """FP32 on the scaled pencil: P = -(D A D)^{-1} R with A = H_loc - eps_bar S + F G F^T,
+    compared in the energy norm of D A D (A positive definite for the generator's G)."""
+    p = cases["mid"]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    d = s.dscale()
+    K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
+    R = pi.seed_normal_block(51, p.n, 13)
+    P = fbuf(p.n, 13)
+    s.precond_apply_f32(fdev(R), P)
+    Pg = host(P).astype(np.float64)
+    ref = K.apply(R / d[:, None]) / d[:, None]
+    Ah = Hs.toarray() * d[:, None] * d[None, :]
+    err = Pg - ref
+    num = np.sqrt(np.einsum("ij,ij->j", err, Ah @ err))
+    den = np.sqrt(np.einsum("ij,ij->j", ref, Ah @ ref))
+    assert np.isfinite(Pg).all()
+    assert (num / den).max() <= 1e-2, (num / den).max()
+
+
+@pytest.mark.parametrize("k", [1, 16, 71])
+def test_spmm_pair_f32_nonlocal(cases, k):
+    p = cases["mid"]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    d = s.dscale()
+    X = pi.seed_normal_block(60 + k, p.n, k)
+    HX, SX = fbuf(p.n, k), fbuf(p.n, k)
+    s.spmm_pair_f32(fdev(X), HX, SX)
+    rH = d[:, None] * (Hs @ (d[:, None] * X))
+    assert relerr(host(HX), rH) <= 2e-5
+
+
+@pytest.mark.parametrize("case", ["mid", "mid_coupled", "big"])
+def test_minres_nonlocal(cases, case):
+    p = cases[case]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    r = L.labpsd(p, 10, 1e-8, seed=3, opts=L.Options(max_outer=6))
+    K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
+    E = r.E_all - r.sigma0
+    PH, PS = L.spmm_pair(Hs, S, r.X)
+    R, res = L.residual(PH, PS, E, 10)
+    P0 = K.apply(R)
+    e = E[:10]
+    steps = torch.zeros(10, dtype=torch.int32, device="cuda")
+    Pd = dbuf(p.n, 10)
+    Pd.copy_(dev(P0))
+    s.minres(dev(R), dev(e), Pd, 0.25, 20, steps)
+    Pg, sg = host(Pd), host(steps)
+    same = 0
+    for j in range(10):
+        xo, ko, _ = L.refine(Hs, S, e[j], R[:, j], P0[:, j], 0.25, 20)
+        assert abs(int(sg[j]) - ko) <= 1, (j, sg[j], ko)
+        if int(sg[j]) == ko:
+            same += 1
+            assert np.abs(Pg[:, j] - xo).max() <= 1e-6 * np.abs(xo).max()
+        rr = np.linalg.norm(Hs @ Pg[:, j] - e[j] * (S @ Pg[:, j]) + R[:, j])
+        if int(sg[j]) < 20:
+            assert rr <= 0.25 * np.linalg.norm(R[:, j]) * (1 + 1e-6)
+    assert same >= 8
+    assert int(sg.sum()) > 0
+
+
+def test_minres_nonlocal_long_run(cases):
+    """Tight tolerance: every column runs the full 20 steps; the iterate must match the oracle's
+    (a missing or misplaced nonlocal term in any step moves it)."""
+    p = cases["mid_coupled"]
+    s = session(p)
+    Hs, S, _ = L.make_shifted(p)
+    R = pi.seed_normal_block(77, p.n, 5)
+    e = np.array([0.1, 0.4, 0.9, 1.7, 3.0])
+    steps = torch.zeros(5, dtype=torch.int32, device="cuda")
+    Pd = dbuf(p.n, 5)
+    s.minres(dev(R), dev(e), Pd, 1e-14, 20, steps)
+    Pg = host(Pd)
+    assert (host(steps) == 20).all()
+    for j in range(5):
+        xo, ko, _ = L.refine(Hs, S, e[j], R[:, j], np.zeros(p.n), 1e-14, 20)
+        assert ko == 20
+        assert np.abs(Pg[:, j] - xo).max() <= 1e-8 * np.abs(xo).max()
+
+
+def host_res(p, lam, X, sigma0):
+    Hs, S, _ = L.make_shifted(p)
+    HX = Hs @ X
+    R = HX - (S @ X) * (lam - sigma0)[None, :]
+    return np.linalg.norm(R, axis=0) / np.linalg.norm(HX, axis=0)
+
+
+@pytest.mark.parametrize("case", ["small", "small_coupled", "big"])
+def test_solve_nonlocal_fp64(cases, case):
+    p = cases[case]
+    nev = 16
+    X0 = pi.seed_normal_block(4, p.n, nev + L.default_m0(nev))
+    s = session(p)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0)
+    assert rc == 0 and ro.converged
+    scale = np.abs(ro.lam).max()
+    assert np.abs(lam - ro.lam).max() <= 1e-9 * scale
+    assert abs(it - ro.iters) <= 1, (it, ro.iters)
+    assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+    assert st["local_cols"] > 0
+
+
+@pytest.mark.parametrize("case", ["small", "big"])
+def test_solve_nonlocal_mixed(cases, case):
+    p = cases[case]
+    nev = 16
+    X0 = pi.seed_normal_block(4, p.n, nev + L.default_m0(nev))
+    s = session(p, precision=hb().PRECISION_MIXED)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0)
+    assert rc == 0
+    assert np.abs(lam - ro.lam).max() <= 1e-9 * np.abs(ro.lam).max()
+    assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+
+
+def test_solve_nonlocal_global_and_local_modes(cases):
+    p = cases["small"]
+    nev = 16
+    X0 = pi.seed_normal_block(4, p.n, 19)
+    s = session(p, precond=hb().PRECOND_GLOBAL)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0, opts=L.Options(local=False))
+    assert rc == 0 and abs(it - ro.iters) <= 1
+    assert np.abs(lam - ro.lam).max() <= 1e-9 * np.abs(ro.lam).max()
+    s = session(p, precond=hb().PRECOND_LOCAL, max_outer=15)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0, opts=L.Options(use_global=False, max_outer=15))
+    assert it == ro.iters == 15
+    assert np.abs(lam - ro.lam).max() <= 1e-7 * np.abs(ro.lam).max()
+
+
+def test_medium_nonlocal_against_stored_oracle():
+    """32^3 Q1, 8 atoms with s and p projectors (k = 32), nev = 64: FP64 and mixed forms."""
+    path = os.path.join(HERE, "golden", "medium_nonlocal_seed1.json")
+    g = json.load(open(path))
+    p = pi.medium_nonlocal_case(1)
+    assert p.n == g["n"] and p.nnz == g["nnz"]
+    nev = g["nev"]
+    X0 = pi.seed_normal_block(1, p.n, nev + L.default_m0(nev))
+    ref = np.array(g["lam"])
+    for prec in (hb().PRECISION_FP64, hb().PRECISION_MIXED):
+        s = session(p, precision=prec)
+        lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+        assert rc == 0
+        assert np.abs(lam - ref).max() <= 1e-9 * np.abs(ref).max()
+        assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+        if prec == hb().PRECISION_FP64:
+            assert abs(it - g["iters"]) <= max(1, int(0.1 * g["iters"])), (it, g["iters"])
+        s.close()
+
+
+def test_server_nonlocal_alone_and_in_the_mix(cases):
+    probs = [cases["small"], cases["mid"], pi.small_case(2)]
+    nev = 16
+    ref = []
+    for i, p in enumerate(probs):
+        X0 = pi.seed_normal_block(30 + i, p.n, nev + L.default_m0(nev))
+        s = session(p)
+        lam, X, it, rc, _ = s.solve(nev, 1e-8, X0=X0)
+        s.close()
+        ref.append((X0, lam, X, it))
+    sv = hb().Server(max_slots=3)
+    tickets = [sv.submit(nev, 1e-8, problem=p, X0=r[0]) for p, r in zip(probs, ref)]
+    outs = [sv.wait(t) for t in tickets]
+    sv.close()
+    for (res, lam, X), (_, lam0, X0v, it0) in zip(outs, ref):
+        assert res["status"] == 0 and res["iters"] == it0
+        assert np.array_equal(lam, lam0) and np.array_equal(X, X0v)

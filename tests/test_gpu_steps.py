@@ -132,7 +132,7 @@ def test_global_preconditioner(which, small, mid):
     K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
     Po = K.apply(R)
     # backward stability of the GPU solve, then agreement with the oracle's library solve
-    A = Hs
+    A = Hs.loc
     anorm = np.abs(A).sum(axis=1).max()
     assert np.abs(A @ Pg + R).max() <= 1e-12 * anorm * np.abs(Pg).max()
     assert relerr(Pg, Po) <= 1e-6
