@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 TOL = 1e-8
 WORKLOAD = "32^3 periodic Q1 elements, 8 atoms Z=4, 4 Gaussian enrichment dofs/node within r_c=0.15, nev=64, tol=1e-8"
+WORKLOAD_NL = WORKLOAD + ", nonlocal F G F^T with s+p projectors per atom (k=32, r_p=0.2)"
 
 
 def parse():
@@ -42,6 +43,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="mixed: FP32 LABPSD phase + FP64 refinement sweep to tol (default); fp64: FP64 throughout")
+    ap.add_argument("--workload", default="medium", choices=["medium", "medium-nonlocal"],
+                    help="medium-nonlocal: the same problem with the nonlocal term H_nl = F G F^T (Sec. 4)")
     return ap.parse_args()
 
 
@@ -91,17 +94,23 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def golden():
-    with open(os.path.join(ROOT, "tests", "golden", "medium_seed1.json")) as f:
+def golden(workload="medium"):
+    name = "medium_nonlocal_seed1.json" if workload == "medium-nonlocal" else "medium_seed1.json"
+    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
         return json.load(f)
 
 
-def cpu_baseline(nev, W_iters=2):
+def problem(workload):
+    from paper_1308_2445_gb300 import pufe_inputs as pi
+    return pi.medium_nonlocal_case(1) if workload == "medium-nonlocal" else pi.medium_case(1)
+
+
+def cpu_baseline(nev, W_iters=2, workload="medium"):
     """Time the CPU oracle, as it stands, on a bounded sample of the same workload."""
     import numpy as np
     from oracle import labpsd as L
     from paper_1308_2445_gb300 import pufe_inputs as pi
-    p = pi.medium_case(1)
+    p = problem(workload)
     w = nev + L.default_m0(nev)
     X0 = pi.seed_normal_block(1, p.n, w)
     t0 = time.perf_counter()
@@ -113,7 +122,7 @@ def cpu_baseline(nev, W_iters=2):
     L.labpsd(p, nev, TOL, X0=X0, precond=K, opts=L.Options(max_outer=W_iters),
              on_iteration=lambda it, res: marks.append(time.perf_counter()))
     per_iter = (marks[-1] - marks[0]) / max(1, len(marks) - 1) if len(marks) > 1 else marks[0] - t1
-    g = golden()
+    g = golden(workload)
     t_solve = per_iter * g["iters"]
     return {"value": nev / t_solve, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"medium workload: library factorisation ({t_factor:.1f} s, excluded like value's) + initial "
@@ -130,7 +139,7 @@ def run_reference(args):
     from oracle import labpsd as L
     from paper_1308_2445_gb300 import pufe_inputs as pi
     nev = pi.MEDIUM_NEV
-    p = pi.medium_case(1)
+    p = problem(args.workload)
     X0 = pi.seed_normal_block(1, p.n, nev + L.default_m0(nev))
     Hs, S, s0 = L.make_shifted(p)
     K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
@@ -140,13 +149,14 @@ def run_reference(args):
     d = [marks[i + 1] - marks[i] for i in range(len(marks) - 1)]
     timed = d[args.warmup:] or d
     per_iter = sum(timed) / len(timed)
-    g = golden()
+    g = golden(args.workload)
     value = nev / (per_iter * g["iters"])
     line = {"impl": "reference", "metric": "eigenpairs/s to 1e-8 residual (FP64 LABPSD)", "value": value,
             "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_iter * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "nev": nev, "precision": "fp64",
+            "config": {"workload": WORKLOAD_NL if args.workload == "medium-nonlocal" else WORKLOAD, "n": p.n,
+                       "nnz": p.nnz, "nev": nev, "precision": "fp64",
                        "step": "one BPSD iteration of the CPU oracle; value scaled to the oracle's full solve"},
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{len(timed)} timed BPSD iterations after {args.warmup} warm-up, "
@@ -173,7 +183,8 @@ def main():
     from paper_1308_2445_gb300 import hbsd, pufe_inputs as pi
 
     nev = pi.MEDIUM_NEV
-    p = pi.medium_case(1)
+    p = problem(args.workload)
+    nl_nnz = int(np.count_nonzero(p.F)) if p.F is not None else 0
     w = nev + max(3, -(-nev // 10))
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
@@ -221,6 +232,8 @@ def main():
     # ---- end to end through the public host API ----------------------------------------
     rp = np.ascontiguousarray(p.row_ptr)
     h2d = rp.nbytes + p.col_idx.nbytes + p.h_val.nbytes + p.s_val.nbytes + p.dof_node.nbytes + p.n * w * 8
+    if p.F is not None:
+        h2d += p.F.nbytes + p.G.nbytes
     d2h = nev * 8 + p.n * nev * 8
     X0n = pi.seed_normal_block(1, p.n, w)
     e2e_t = []
@@ -245,10 +258,12 @@ def main():
     classes = {
         "precond": (st["t_precond_ms"], 4.0 * st["nnz_L"] * st["precond_cols"], st["precond_calls"],
                     "supernodal triangular solves of step 6(a): 2 FMA per factor entry per column"),
-        "matvec": (st["t_matvec_ms"], 4.0 * p.nnz * st["matvec_cols"], None,
-                   "fused SpMM of steps 3/7: 2 FMA (h and s) per nonzero per column"),
-        "minres": (st["t_local_ms"], 4.0 * p.nnz * st["minres_spmm_cols"], None,
-                   "MINRES of step 6(b): shifted fused SpMM, 2 FMA per nonzero per column"),
+        "matvec": (st["t_matvec_ms"], (4.0 * p.nnz + 4.0 * nl_nnz) * st["matvec_cols"], None,
+                   "fused SpMM of steps 3/7: 2 FMA (h and s) per nonzero per column"
+                   + (" + 2 FMA per F entry (F^T X and F Z)" if nl_nnz else "")),
+        "minres": (st["t_local_ms"], (4.0 * p.nnz + 4.0 * nl_nnz) * st["minres_spmm_cols"], None,
+                   "MINRES of step 6(b): shifted fused SpMM, 2 FMA per nonzero per column"
+                   + (" + 2 FMA per F entry" if nl_nnz else "")),
     }
     dom = max(classes, key=lambda k: classes[k][0])
     t_ms, flops, _, what = classes[dom]
@@ -262,7 +277,8 @@ def main():
             "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "nev": nev, "precision": args.precision,
+            "config": {"workload": WORKLOAD_NL if args.workload == "medium-nonlocal" else WORKLOAD, "n": p.n,
+                       "nnz": p.nnz, "nev": nev, "precision": args.precision, "nonlocal_nnz": nl_nnz,
                        "iters": st["iters"], "iters_fp64": st["iters_fp64"], "t_factor_ms": st["t_factor_ms"],
                        "nnz_L": st["nnz_L"], "res_max": st["res_max"], "rr_fallbacks": st["rr_fallbacks"],
                        "minres_steps": st["minres_steps"],
@@ -271,7 +287,7 @@ def main():
             "roofline": roof, "e2e": e2e, "gpu_launches": int(sum(s["gpu_launches"] for s in stats)),
             "clocks": ck}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(nev)
+        line["cpu_baseline"] = cpu_baseline(nev, workload=args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -170,6 +170,12 @@ int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm,
 int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0,
                       double* lambda_dev, double* X_dev, int64_t ldx, int* iters, hbsd_stats* st);
 
+/* Res_max = max_i Res_i (Eq. res1) at every convergence test (step 5) of the session's last
+ * solve, in order: entry 0 follows the Rayleigh-Ritz on the start block, the last is the value
+ * that stopped the solve.  Writes at most cap values to out (host; NULL if cap = 0) and returns
+ * how many there are. */
+int hbsd_res_history(const hbsd_handle* h, double* out, int cap);
+
 void hbsd_destroy(hbsd_handle* h);
 const char* hbsd_status_string(int status);
 const char* hbsd_last_error(void);

@@ -239,8 +239,8 @@ struct Nonlocal {
     // fused-MINRES index for one grid size (see minres.cu)
     int mr_grid = -1, mr_version = -1, mr_nslots = 0, mr_nneed = 0;
     DBuf<int64_t> ch_row_off, pan_off;
-    DBuf<int32_t> ch_lptr, cl_ptr, cl_slot, nb_ptr, nb_napply, nb_l, lmap;
-    DBuf<double> pan, mr_part, zv, zg;
+    DBuf<int32_t> ch_rows, ch_lptr, cl_ptr, cl_slot, nb_ptr, nb_napply, nb_l, lmap, sf_ptr, sf_off;
+    DBuf<double> pan, mr_part, zv, zg, sf_val;
 };
 
 // ---- session -----------------------------------------------------------------------
@@ -286,6 +286,7 @@ struct Session {
     bool opt_df64 = true;       // mixed form: Gram and update in double-float (HBSD_NO_DF64=1 turns off)
     double dbg_rr_kernel_ms = 0.0, dbg_rr_host_ms = 0.0, dbg_rr_wake_ms = 0.0;   // Rayleigh-Ritz timing accounting (HBSD_RRDBG)
     int mr_blk_grid = 0;
+    int mr_blk_nl = -1;              // nonlocal version the partition was weighted for (-1: none)
     std::vector<int64_t> h_mr_blk;   // host copy of mr_blk
     // mixed-precision preconditioner buffers (FP32 scaled R and P)
     DBuf<float> r32, p32, xa32, ra32, sh32;
@@ -294,6 +295,7 @@ struct Session {
     int keep_w = 0;
     int64_t keep_ld = 0;
     Nonlocal nl;                // H_nl = F G F^T (k = 0: none)
+    std::vector<double> res_hist;   // Res_max at each convergence test of the last solve
 };
 
 // nonlocal term (nonlocal.cu)

@@ -113,7 +113,7 @@ struct MrArgs {
     const int64_t* nl_rptr;       // F by row (all n rows)
     const int32_t* nl_rcol;
     const double* nl_rval;
-    const int32_t* nl_frows;      // rows with F entries
+    const int32_t* nl_frows;      // rows with F entries, in chunk order
     const int64_t* nl_ch_row_off; // chunk c: frows[ch_row_off[c] .. ch_row_off[c+1])
     const int32_t* nl_ch_lptr;    // chunk c: projector slots [ch_lptr[c], ch_lptr[c+1])
     const double* nl_pan;         // chunk c: rows x slots panel at pan_off[c]
@@ -124,6 +124,9 @@ struct MrArgs {
     const int32_t* nl_nb_napply;
     const int32_t* nl_nb_l;
     const int32_t* nl_lmap;       // [b * nl_k + l]: local index of projector l in block b, or -1
+    const int32_t* nl_sf_ptr;     // per SELL slot: F entries sf_ptr[slot] .. sf_ptr[slot+1] with
+    const int32_t* nl_sf_off;     //   the zg row they read (nb_ptr[b] + local index)
+    const double* nl_sf_val;      //   and the value F(row, l)
     const int32_t* nl_gptr;       // G by rows
     const int32_t* nl_gcol;
     const double* nl_gval;
@@ -211,39 +214,80 @@ size_t mr_smem_bytes(int k) {
            (size_t)(MR_IFIELDS * k + 2) * sizeof(int);
 }
 
-// Nonlocal row term sum_e F(row, l_e) (G F^T v)(l_e, j) from this block's reduced values.
-__device__ __forceinline__ double nl_row(const MrArgs& a, int64_t row, int j) {
+// Nonlocal row term sum_e F(row, l_e) (G F^T v)(l_e, j) of one SELL slot, from this block's
+// reduced values: the slot's entries carry the row of zg they read.
+__device__ __forceinline__ double nl_slot(const MrArgs& a, int64_t slot, int j) {
     double s = 0.0;
-    const int64_t e1 = a.nl_rptr[row + 1];
-    const int64_t nb0 = a.nl_nb_ptr[blockIdx.x];
-    const int32_t* lm = a.nl_lmap + (int64_t)blockIdx.x * a.nl_k;
-    for (int64_t e = a.nl_rptr[row]; e < e1; ++e)
-        s = fma(a.nl_rval[e], a.nl_zg[(nb0 + lm[a.nl_rcol[e]]) * a.kp + j], s);
+    const int e1 = a.nl_sf_ptr[slot + 1];
+    for (int e = a.nl_sf_ptr[slot]; e < e1; ++e) s = fma(a.nl_sf_val[e], a.nl_zg[(int64_t)a.nl_sf_off[e] * a.kp + j], s);
     return s;
 }
 
 // Chunk partials of F^T Src for the columns jcol(0 .. cnt-1) with keep(j): block c writes
 // nl_part[(ch_lptr[c] + t) * kp + j] = scale(j) * sum_r panel(r, t) Src(frows[r], j).
+// Threads form groups of rs lanes (a power of two); a group takes one column and its lanes
+// interleave over the chunk's rows, four projectors at a time, then a shuffle tree sums the
+// group (fixed order).  One load of Src per (row, column) and group of four projectors.
 template <class J, class K, class Sc>
 __device__ void nl_chunk_partial(const MrArgs& a, const double* Src, int64_t lds, int cnt, J&& jcol, K&& keep,
                                  Sc&& scale) {
     const int c = blockIdx.x;
     const int l0 = a.nl_ch_lptr[c], nlc = a.nl_ch_lptr[c + 1] - l0;
-    const int64_t r0 = a.nl_ch_row_off[c], nr = a.nl_ch_row_off[c + 1] - r0;
+    const int64_t r0 = a.nl_ch_row_off[c];
+    const int nr = (int)(a.nl_ch_row_off[c + 1] - r0);
+    if (nlc == 0 || cnt == 0) return;
     const double* pan = a.nl_pan + a.nl_pan_off[c];
-    const int total = nlc * cnt;
-    for (int pidx = threadIdx.x; pidx < total; pidx += blockDim.x) {
-        const int t = pidx / cnt, q = pidx - t * cnt;
-        const int j = jcol(q);
-        if (!keep(j)) continue;
-        double a0 = 0.0, a1 = 0.0;
-        int64_t r = 0;
-        for (; r + 1 < nr; r += 2) {
-            a0 = fma(pan[r * nlc + t], Src[(int64_t)a.nl_frows[r0 + r] * lds + j], a0);
-            a1 = fma(pan[(r + 1) * nlc + t], Src[(int64_t)a.nl_frows[r0 + r + 1] * lds + j], a1);
+    int rs = 32;
+    while (rs > 1 && rs * cnt > (int)blockDim.x) rs >>= 1;
+    const int sub = threadIdx.x & (rs - 1);
+    const int ngrp = (int)blockDim.x / rs;
+    for (int q = threadIdx.x / rs; q - (int)threadIdx.x / rs < cnt; q += ngrp) {
+        // every lane of a warp runs the same trip count (its groups share the loop bounds), so
+        // the shuffles below see full warps; idle groups carry zeros
+        const bool on = q < cnt;
+        const int j = on ? jcol(q) : 0;
+        const bool use = on && keep(j);
+        for (int t0 = 0; t0 < nlc; t0 += 4) {
+            double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;
+            if (use) {
+                // four rows per trip: their index and value loads are issued together
+                for (int rb = sub; rb < nr; rb += 4 * rs) {
+                    int ri[4];
+                    double x[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = rb + u * rs;
+                        ri[u] = r < nr ? a.nl_frows[r0 + r] : -1;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) x[u] = ri[u] >= 0 ? Src[(int64_t)ri[u] * lds + j] : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int r = rb + u * rs;
+                        if (r >= nr) break;
+                        const double* pr = pan + (int64_t)r * nlc + t0;
+                        acc0 = fma(pr[0], x[u], acc0);
+                        if (t0 + 1 < nlc) acc1 = fma(pr[1], x[u], acc1);
+                        if (t0 + 2 < nlc) acc2 = fma(pr[2], x[u], acc2);
+                        if (t0 + 3 < nlc) acc3 = fma(pr[3], x[u], acc3);
+                    }
+                }
+            }
+            for (int o = rs >> 1; o > 0; o >>= 1) {
+                acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
+                acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+                acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+                acc3 += __shfl_xor_sync(0xffffffffu, acc3, o);
+            }
+            if (use && sub == 0) {
+                const double sc = scale(j);
+                double* out = a.nl_part + (int64_t)(l0 + t0) * a.kp + j;
+                out[0] = acc0 * sc;
+                if (t0 + 1 < nlc) out[a.kp] = acc1 * sc;
+                if (t0 + 2 < nlc) out[2 * a.kp] = acc2 * sc;
+                if (t0 + 3 < nlc) out[3 * a.kp] = acc3 * sc;
+            }
         }
-        if (r < nr) a0 = fma(pan[r * nlc + t], Src[(int64_t)a.nl_frows[r0 + r] * lds + j], a0);
-        a.nl_part[(int64_t)(l0 + t) * a.kp + j] = (a0 + a1) * scale(j);
     }
 }
 
@@ -254,13 +298,31 @@ __device__ void nl_reduce(const MrArgs& a, int cnt, J&& jcol) {
     const int b = blockIdx.x;
     const int n0 = a.nl_nb_ptr[b], nn = a.nl_nb_ptr[b + 1] - n0, napp = a.nl_nb_napply[b];
     if (nn == 0) return;
-    for (int pidx = threadIdx.x; pidx < nn * cnt; pidx += blockDim.x) {
-        const int t = pidx / cnt, q = pidx - t * cnt;
-        const int j = jcol(q);
-        const int l = a.nl_nb_l[n0 + t];
-        double s = 0.0;
-        for (int u = a.nl_cl_ptr[l]; u < a.nl_cl_ptr[l + 1]; ++u) s += a.nl_part[(int64_t)a.nl_cl_slot[u] * a.kp + j];
-        a.nl_zv[(int64_t)(n0 + t) * a.kp + j] = s;
+    // a group of g lanes (a power of two) per (projector, column): its lanes stride over the
+    // contributing chunks, then a shuffle tree; every warp runs the same trip count
+    const int pairs = nn * cnt;
+    int g = 32;
+    while (g > 1 && g * pairs > (int)blockDim.x) g >>= 1;
+    const int sub = threadIdx.x & (g - 1), g0 = threadIdx.x / g, ng = (int)blockDim.x / g;
+    for (int pidx = g0; pidx - g0 < pairs; pidx += ng) {
+        const bool on = pidx < pairs;
+        double s0 = 0.0, s1 = 0.0;
+        int t = 0, j = 0;
+        if (on) {
+            t = pidx / cnt;
+            j = jcol(pidx - t * cnt);
+            const int l = a.nl_nb_l[n0 + t];
+            const int u1 = a.nl_cl_ptr[l + 1];
+            int u = a.nl_cl_ptr[l] + sub;
+            for (; u + g < u1; u += 2 * g) {
+                s0 += a.nl_part[(int64_t)a.nl_cl_slot[u] * a.kp + j];
+                s1 += a.nl_part[(int64_t)a.nl_cl_slot[u + g] * a.kp + j];
+            }
+            if (u < u1) s0 += a.nl_part[(int64_t)a.nl_cl_slot[u] * a.kp + j];
+        }
+        s0 += s1;
+        for (int o = g >> 1; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        if (on && sub == 0) a.nl_zv[(int64_t)(n0 + t) * a.kp + j] = s0;
     }
     __syncthreads();
     const int32_t* lm = a.nl_lmap + (int64_t)b * a.nl_k;
@@ -304,7 +366,7 @@ __device__ __forceinline__ void spmm_pass(const MrArgs& a, const P* hs, const T*
         const int row = a.slot_row[slot];
         if (row >= 0) {
             T y = ah - ej * as;
-            if (a.nl_k) y += (T)nl_row(a, row, j);
+            if (a.nl_k) y += (T)nl_slot(a, slot, j);
             f((int64_t)row, j, y);
         }
     }
@@ -431,7 +493,10 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
     for (int step = 1; step <= a.maxit && S.nact()[0] > 0; ++step) {
         const int na = S.nact()[0];
         // ---- A: U = A_e V on the active columns, partial alpha ----
-        if (a.nl_k) nl_reduce(a, na, active_col);
+        if (a.nl_k) {
+            nl_reduce(a, na, active_col);
+            mark(6);
+        }
         for (int c0 = 0; c0 < na; c0 += MR_PASS) {
             const Pass p = make_pass(c0, na);
             double acc = 0.0;
@@ -497,9 +562,12 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
         }
         __syncthreads();
         // F^T v_{j+1} = F^T u_j / beta_{j+1} for the columns that go on (U is final here)
-        if (a.nl_k && step < a.maxit)
+        if (a.nl_k && step < a.maxit) {
+            mark(3);
             nl_chunk_partial(a, reinterpret_cast<const double*>(U), ld, na, active_col,
                              [&](int j) { return S.g(I_CONT)[j] != 0; }, [&](int j) { return S.f(F_BINV)[j]; });
+            mark(5);
+        }
         for (int c0 = 0; c0 < na; c0 += MR_PASS) {
             const Pass p = make_pass(c0, na);
             rows_pass(a, p, active_col, [&](int64_t i, int j) {
@@ -572,16 +640,21 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     init_lk.unlock();
     const int64_t kp = round_up(k, 4);
     HBSD_TRY(s->mr_red.alloc((size_t)2 * grid * kp));
-    if (s->mr_blk_grid != grid) {
-        // contiguous slot ranges per block with about equal stored entries (+2 per row for the
-        // per-row work outside the nonzero loop)
+    const bool nl = s->nl.k > 0 && s->nl.nnz > 0;
+    const int nl_ver = nl ? s->nl.version : -1;
+    if (s->mr_blk_grid != grid || s->mr_blk_nl != nl_ver) {
+        // contiguous slot ranges per block with about equal work: stored entries, +2 per row for
+        // the per-row work outside the nonzero loop, +2 per entry of F in the row (nonlocal term)
         const Sell& A = s->A;
         std::vector<int64_t> wcum(A.n_slots + 1, 0);
         for (int64_t sl = 0; sl < A.n_slices; ++sl) {
             const int64_t len = (A.h_slice_ptr[sl + 1] - A.h_slice_ptr[sl]) / A.C;
             for (int t = 0; t < A.C; ++t) {
                 const int64_t slot = sl * A.C + t;
-                if (slot < A.n_slots) wcum[slot + 1] = len + 2;
+                if (slot >= A.n_slots) continue;
+                wcum[slot + 1] = len + 2;
+                const int row = A.h_slot_row[slot];
+                if (nl && row >= 0) wcum[slot + 1] += 2 * (s->nl.h_rptr[row + 1] - s->nl.h_rptr[row]);
             }
         }
         for (int64_t i = 0; i < A.n_slots; ++i) wcum[i + 1] += wcum[i];
@@ -597,8 +670,9 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         HBSD_CUDA(cudaMemcpy(s->mr_blk.p, blk.data(), (grid + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
         s->h_mr_blk = std::move(blk);
         s->mr_blk_grid = grid;
+        s->mr_blk_nl = nl_ver;
+        s->nl.mr_grid = -1;   // the nonlocal index follows the partition
     }
-    const bool nl = s->nl.k > 0 && s->nl.nnz > 0;
     if (nl) HBSD_TRY(nl_minres_index(s, grid, s->h_mr_blk, kp));
     HBSD_CUDA(cudaMemsetAsync(s->mr_any.p, 0, 4 * sizeof(int), st));
     T* V = mr_vecs<T>(s).p;
@@ -642,11 +716,12 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     a.nl_k = nl ? s->nl.k : 0;
     {
         Nonlocal& q = s->nl;
-        a.nl_rptr = q.rptr.p; a.nl_rcol = q.rcol.p; a.nl_rval = q.rval.p; a.nl_frows = q.frows.p;
+        a.nl_rptr = q.rptr.p; a.nl_rcol = q.rcol.p; a.nl_rval = q.rval.p; a.nl_frows = q.ch_rows.p;
         a.nl_ch_row_off = q.ch_row_off.p; a.nl_ch_lptr = q.ch_lptr.p; a.nl_pan = q.pan.p; a.nl_pan_off = q.pan_off.p;
         a.nl_cl_ptr = q.cl_ptr.p; a.nl_cl_slot = q.cl_slot.p;
         a.nl_nb_ptr = q.nb_ptr.p; a.nl_nb_napply = q.nb_napply.p; a.nl_nb_l = q.nb_l.p; a.nl_lmap = q.lmap.p;
         a.nl_gptr = q.gptr.p; a.nl_gcol = q.gcol.p; a.nl_gval = q.gval.p;
+        a.nl_sf_ptr = q.sf_ptr.p; a.nl_sf_off = q.sf_off.p; a.nl_sf_val = q.sf_val.p;
         a.nl_part = q.mr_part.p; a.nl_zv = q.zv.p; a.nl_zg = q.zg.p;
     }
     void* args[] = {&a};
@@ -664,8 +739,9 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     if (trace) {
         unsigned long long t[8];
         HBSD_CUDA(cudaMemcpy(t, s->mr_stamps.p, sizeof(t), cudaMemcpyDeviceToHost));
-        std::fprintf(stderr, "[hbsd]   MINRES k %d grid %d steps max %d sum %lld | us: start %.0f A %.0f B %.0f C %.0f barriers %.0f\n",
-                     k, grid, mx, (long long)tot, t[0] * 1e-3, t[1] * 1e-3, t[2] * 1e-3, t[3] * 1e-3, t[4] * 1e-3);
+        std::fprintf(stderr, "[hbsd]   MINRES k %d grid %d steps max %d sum %lld | us: start %.0f A %.0f B %.0f C %.0f barriers %.0f nl-partial %.0f nl-reduce %.0f\n",
+                     k, grid, mx, (long long)tot, t[0] * 1e-3, t[1] * 1e-3, t[2] * 1e-3, t[3] * 1e-3, t[4] * 1e-3,
+                     t[5] * 1e-3, t[6] * 1e-3);
     }
     s->stats.minres_spmm_cols += tot + k;   // the start SpMM plus one column per step
     if (total_steps) *total_steps = tot;

@@ -461,7 +461,13 @@ int nl_minres_index(Session* s, int grid, const std::vector<int64_t>& blk, int64
     if (nl.mr_grid != grid || nl.mr_version != nl.version) {
         const std::vector<int64_t>& rptr = nl.h_rptr;
         const std::vector<int32_t>& rcol = nl.h_rcol;
-        const std::vector<int32_t>& frows = nl.h_frows;
+        // rows with F entries ordered by their first projector (then row): a chunk then covers
+        // the rows of one atom's projectors, so it meets few projectors and each projector's
+        // partials sit in few chunks
+        std::vector<int32_t> frows = nl.h_frows;
+        std::stable_sort(frows.begin(), frows.end(), [&](int32_t x, int32_t y) {
+            return rcol[rptr[x]] < rcol[rptr[y]];
+        });
         const int64_t nfr = (int64_t)frows.size();
         // chunks
         std::vector<int64_t> row_off(grid + 1, nfr);
@@ -537,6 +543,21 @@ int nl_minres_index(Session* s, int grid, const std::vector<int64_t>& blk, int64
             nb_l.insert(nb_l.end(), extra.begin(), extra.end());
             nb_ptr[b + 1] = (int32_t)nb_l.size();
         }
+        // F entries of every SELL slot with the zg row of its block they read
+        std::vector<int32_t> sf_ptr(A.n_slots + 1, 0), sf_off;
+        std::vector<double> sf_val;
+        for (int b = 0; b < grid; ++b)
+            for (int64_t slot = blk[b]; slot < blk[b + 1]; ++slot) {
+                const int row = A.h_slot_row[slot];
+                if (row >= 0)
+                    for (int64_t e = rptr[row]; e < rptr[row + 1]; ++e) {
+                        sf_off.push_back(nb_ptr[b] + lmap[(size_t)b * k + rcol[e]]);
+                        sf_val.push_back(nl.h_rval[e]);
+                    }
+                sf_ptr[slot + 1] = (int32_t)sf_off.size();
+            }
+        HBSD_TRY(upload(nl.sf_ptr, sf_ptr)); HBSD_TRY(upload(nl.sf_off, sf_off)); HBSD_TRY(upload(nl.sf_val, sf_val));
+        HBSD_TRY(upload(nl.ch_rows, frows));
         HBSD_TRY(upload(nl.ch_row_off, row_off)); HBSD_TRY(upload(nl.ch_lptr, lptr));
         HBSD_TRY(upload(nl.pan_off, pan_off)); HBSD_TRY(upload(nl.pan, pan));
         HBSD_TRY(upload(nl.cl_ptr, cl_ptr)); HBSD_TRY(upload(nl.cl_slot, cl_slot));

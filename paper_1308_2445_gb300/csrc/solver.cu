@@ -400,6 +400,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         ++iters;
     }
     *iters_done = iters;
+    S->res_hist = hist;
     return 0;
 }
 
@@ -707,6 +708,13 @@ int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out
 }
 
 // ---- step-level entry points ---------------------------------------------------------------
+int hbsd_res_history(const hbsd_handle* h, double* out, int cap) {
+    if (!h || cap < 0 || (cap > 0 && !out)) return fail(HBSD_ERR_ARG, "bad arguments");
+    const std::vector<double>& v = h->s.res_hist;
+    for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
+    return (int)v.size();
+}
+
 int hbsd_set_nonlocal(hbsd_handle* h, int k, const double* F, int64_t ldf, const double* G) {
     if (!h) return fail(HBSD_ERR_ARG, "bad arguments");
     HBSD_CUDA(cudaStreamSynchronize(h->s.stream));   // no work of this session reads the old term any more

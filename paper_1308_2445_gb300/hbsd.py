@@ -91,6 +91,7 @@ _SIGS = {
                               C.POINTER(hbsd_options), _P, C.POINTER(_P)]),
     "hbsd_update_H": (C.c_int, [_P, _D]),
     "hbsd_set_nonlocal": (C.c_int, [_P, C.c_int, _D, C.c_int64, _D]),
+    "hbsd_res_history": (C.c_int, [_P, _D, C.c_int]),
     "hbsd_solve": (C.c_int, [_P, C.c_int, C.c_double, _D, C.c_int, _D, _D, C.POINTER(C.c_int),
                              C.POINTER(hbsd_stats)]),
     "hbsd_solve_device": (C.c_int, [_P, C.c_int, C.c_double, _P, C.c_int64, _P, _P, C.c_int64,
@@ -214,6 +215,14 @@ class Session:
         if getattr(p, "F", None) is not None:
             s.set_nonlocal(p.F, p.G)
         return s
+
+    def res_history(self):
+        """Res_max at every convergence test of the last solve (hbsd_res_history)."""
+        cnt = lib().hbsd_res_history(self.h, None, 0)
+        check(cnt, "hbsd_res_history")
+        out = np.empty(max(cnt, 1))
+        check(lib().hbsd_res_history(self.h, out.ctypes.data_as(_D), cnt), "hbsd_res_history")
+        return out[:cnt]
 
     def set_nonlocal(self, F, G):
         """hbsd_set_nonlocal: H := H_loc + F G F^T (F n x k, G k x k symmetric); F = None removes it."""

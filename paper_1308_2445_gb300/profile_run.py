@@ -1,6 +1,6 @@
 """Run one LABPSD solve of a named workload through the C ABI, for profilers (ncu).
 
-  python -m paper_1308_2445_gb300.profile_run --workload small|medium [--precision fp64|mixed]
+  python -m paper_1308_2445_gb300.profile_run --workload small|medium|medium-nonlocal [--precision fp64|mixed]
          [--max-outer K] [--solves S]
 
 --max-outer is the library's own outer-iteration cap (hbsd_options.max_outer): with a small
@@ -19,7 +19,7 @@ if ROOT not in sys.path:
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="small", choices=["small", "medium"])
+    ap.add_argument("--workload", default="small", choices=["small", "medium", "medium-nonlocal"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--max-outer", type=int, default=1000)
     ap.add_argument("--solves", type=int, default=1)
@@ -28,7 +28,7 @@ def main():
     from paper_1308_2445_gb300 import build_lib, hbsd, pufe_inputs as pi
     if not os.path.exists(build_lib.LIB):
         build_lib.build()
-    p = pi.small_case(1) if a.workload == "small" else pi.medium_case(1)
+    p = {"small": pi.small_case, "medium": pi.medium_case, "medium-nonlocal": pi.medium_nonlocal_case}[a.workload](1)
     nev = pi.SMALL_NEV if a.workload == "small" else pi.MEDIUM_NEV
     prec = hbsd.PRECISION_MIXED if a.precision == "mixed" else hbsd.PRECISION_FP64
     s = hbsd.Session.from_problem(p, precision=prec, max_outer=a.max_outer)

