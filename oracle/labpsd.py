@@ -28,6 +28,11 @@ solve) as the only library steps.  Readings of points the paper leaves open:
   R12 max_outer default 1000.
   R13 Rayleigh-Ritz on the diagonally scaled pair; if the Cholesky of the scaled S_R breaks
       down or a pivot is below 1e-14, drop S_R eigen-directions below 1e-14 * max.
+  R18 the first-order one-step refinement of Sec. 6 (future work) iterates
+      p <- p - alpha d with d = (H - eps_i S) p + r_i, the residual of Eq. idealp (the printed
+      bracket carries -r_i, at odds with Eq. idealp's sign), alpha = (A d . d) / (A d . A d)
+      minimising ||d - alpha A d||, from the globally preconditioned p, with the stopping rule
+      of MINRES (||d|| <= eta ||r_i|| or max_minres steps); ||d|| is recomputed, not updated.
   R17 with a nonlocal term H = H_loc + F G F^H (Eq. fgf) the global factor is that of the
       local part H_loc^(1) - eps_bar S (Eq. ldl) and the nonlocal part enters through the
       Sherman-Morrison-Woodbury steps 1-6 of Sec. 4; every product with H (steps 3, 7 and the
@@ -56,6 +61,7 @@ class Options:
     m0: int | None = None      # R6
     local: bool = True         # False: global preconditioner only (step 6(a) alone)
     use_global: bool = True    # False: local only, Sec. 5 (6(b) without 6(a)), reading R16
+    local_solver: str = "minres"   # "one_step": the first-order one-step refinement, reading R18
 
 
 def default_m0(m: int) -> int:
@@ -282,6 +288,37 @@ def refine(Hs, S, eps_i, r_i, p0, eta, maxit):
     return minres(apply_A, -r_i, p0, tol_abs, maxit)
 
 
+def one_step(apply_A, b, x0, tol_abs, maxit):
+    """First-order one-step iteration with the residual-minimising step (R18): for A x = b,
+    d = A x - b, x <- x - alpha d with alpha = (A d . d) / (A d . A d).  Stops when
+    ||A x - b|| <= tol_abs or after maxit steps.  Returns (x, steps, ||d|| history)."""
+    x = np.array(x0, dtype=np.result_type(x0.dtype, b.dtype), copy=True)
+    d = apply_A(x) - b
+    dn = float(np.linalg.norm(d))
+    hist = [dn]
+    steps = 0
+    while dn > tol_abs and steps < maxit:
+        u = apply_A(d)
+        uu = float(np.real(np.vdot(u, u)))
+        if uu == 0.0:
+            break
+        alpha = float(np.real(np.vdot(u, d))) / uu
+        x = x - alpha * d
+        d = d - alpha * u
+        dn = float(np.linalg.norm(d))
+        steps += 1
+        hist.append(dn)
+    return x, steps, hist
+
+
+def refine_one_step(Hs, S, eps_i, r_i, p0, eta, maxit):
+    """Step 6(b) by the first-order one-step refinement of Sec. 6 (R18)."""
+    def apply_A(y):
+        return Hs @ y - eps_i * (S @ y)
+    tol_abs = eta * float(np.linalg.norm(r_i))
+    return one_step(apply_A, -r_i, p0, tol_abs, maxit)
+
+
 # ---------------------------------------------------------------------------------------
 # Steps 8-9: reduced GHEP and Rayleigh-Ritz (remark 6; R13)
 # ---------------------------------------------------------------------------------------
@@ -407,10 +444,11 @@ def labpsd(problem, nev, tol, X0=None, opts: Options | None = None, seed=1,
             P = -R[:, U]
         loc = localized(res, E, E_prev, opts.tau1, opts.tau2) if opts.local else np.zeros(m, bool)
         steps = []
+        solver = refine_one_step if opts.local_solver == "one_step" else refine
         for j, i in enumerate(U):
             if loc[i]:                                                  # 6(b)
                 p0 = P[:, j] if opts.use_global else np.zeros(n)
-                P[:, j], k, _ = refine(Hs, S, E[i], R[:, i], p0, opts.eta, opts.max_minres)
+                P[:, j], k, _ = solver(Hs, S, E[i], R[:, i], p0, opts.eta, opts.max_minres)
                 steps.append(k)
         minres_steps.append(np.array(steps, dtype=np.int64))
         n_precond.append(int(U.size))
