@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
                     help="mixed: FP32 LABPSD phase + FP64 refinement sweep to tol (default); fp64: FP64 throughout")
+    ap.add_argument("--local-solver", default="minres", choices=["minres", "onestep"],
+                    help="step 6(b): MINRES (default) or the first-order one-step refinement (Sec. 6)")
     ap.add_argument("--workload", default="medium", choices=["medium", "medium-nonlocal"],
                     help="medium-nonlocal: the same problem with the nonlocal term H_nl = F G F^T (Sec. 4)")
     return ap.parse_args()
@@ -189,7 +191,8 @@ def main():
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     prec = hbsd.PRECISION_MIXED if args.precision == "mixed" else hbsd.PRECISION_FP64
-    sess = hbsd.Session.from_problem(p, stream=stream.cuda_stream, precision=prec)
+    lsol = hbsd.LOCAL_ONESTEP if args.local_solver == "onestep" else hbsd.LOCAL_MINRES
+    sess = hbsd.Session.from_problem(p, stream=stream.cuda_stream, precision=prec, local_solver=lsol)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     X0h = torch.from_numpy(pi.seed_normal_block(1, p.n, w)).pin_memory()
@@ -241,7 +244,7 @@ def main():
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         ta = time.perf_counter()
-        s2 = hbsd.Session.from_problem(p, precision=prec)
+        s2 = hbsd.Session.from_problem(p, precision=prec, local_solver=lsol)
         lam_h, X_h, it2, rc2, st2 = s2.solve(nev, TOL, X0=X0n)
         s2.close()
         torch.cuda.synchronize()
@@ -279,6 +282,7 @@ def main():
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NL if args.workload == "medium-nonlocal" else WORKLOAD, "n": p.n,
                        "nnz": p.nnz, "nev": nev, "precision": args.precision, "nonlocal_nnz": nl_nnz,
+                       "local_solver": args.local_solver,
                        "iters": st["iters"], "iters_fp64": st["iters_fp64"], "t_factor_ms": st["t_factor_ms"],
                        "nnz_L": st["nnz_L"], "res_max": st["res_max"], "rr_fallbacks": st["rr_fallbacks"],
                        "minres_steps": st["minres_steps"],

@@ -80,6 +80,12 @@ typedef struct {
                                      localized columns refined by MINRES from zero; no
                                      global factor is built                              */
 
+/* Step 6(b) solvers (hbsd_options.local_solver) */
+#define HBSD_LOCAL_MINRES     0   /* MINRES (Sec. 4, Eq. indls; Paige-Saunders)             */
+#define HBSD_LOCAL_ONESTEP    1   /* first-order one-step iteration with the residual-
+                                     minimising step (Sec. 6): p -= alpha d, d = A p + r,
+                                     alpha = (A d . d) / (A d . A d); same stopping rule  */
+
 /* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
  * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,
  * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar). */
@@ -94,6 +100,7 @@ typedef struct {
     int precision;      /* HBSD_PRECISION_*                                                             */
     int precond;        /* HBSD_PRECOND_*                                                               */
     uint64_t seed;      /* seed of the SplitMix64 normals used when X0 is NULL                           */
+    int local_solver;   /* HBSD_LOCAL_* (default MINRES)                                                */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */
@@ -222,6 +229,13 @@ int hbsd_precond_apply(hbsd_handle* h, const double* R, int64_t ldr, int k, doub
  * taken per column. */
 int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k,
                 double eta, int max_minres, double* P, int64_t ldp, int* steps);
+
+/* The first-order one-step refinement (Sec. 6) with the arguments and the stopping rule of
+ * hbsd_minres: for column j, d = (Hs - e_j S) P(:, j) + R(:, j), P(:, j) -= alpha d with
+ * alpha = (A d . d) / (A d . A d), until ||d|| <= eta ||R(:, j)|| or max_steps steps (steps[j]
+ * steps taken, device, nullable).  Device pointers; synchronous. */
+int hbsd_onestep(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k,
+                 double eta, int max_steps, double* P, int64_t ldp, int* steps);
 
 /* Step 8: H_R = Z^T ZH and S_R = Z^T ZS (q x q, row-major, ld q), made exactly symmetric
  * as (A + A^T)/2; Z, ZH, ZS are n x q row-major blocks. */

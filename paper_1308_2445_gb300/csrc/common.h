@@ -200,9 +200,11 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
 template <class T>
 int residual(Session* s, const T* PH, int64_t ldh, const T* PS, int64_t lds, const double* E, int m,
              T* R, int64_t ldr, int64_t n, double* res, double* rnorm, cudaStream_t st);
+// step 6(b) for k columns: MINRES (solver = HBSD_LOCAL_MINRES) or the first-order one-step
+// refinement (HBSD_LOCAL_ONESTEP)
 template <class T>
 int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double eta, int maxit, T* X,
-                 int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st);
+                 int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st, int solver = HBSD_LOCAL_MINRES);
 
 // ---- nonlocal low-rank term H_nl = F G F^T (Eq. fgf) and its SMW data (Sec. 4) -----------
 // F is kept by its nonzero entries (projectors of compact support make it sparse) in two

@@ -603,6 +603,180 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
         for (int j = threadIdx.x; j < k; j += blockDim.x) a.steps_out[j] = S.g(I_STEPS)[j];
 }
 
+// First-order one-step refinement (Sec. 6, future work; reading R18): for each column j,
+// d = (H - e_j S) p + r_j, p <- p - alpha d with alpha = (A d . d) / (A d . A d), the step that
+// minimises ||d - alpha A d||; ||d|| is recomputed after each step and the column stops when it
+// is <= eta ||r_j|| (Eq. approxp) or after maxit steps.  Same launch, layout and barrier as
+// k_minres; each step is three phases:
+//   A. U = A d on the active columns, partials of A d . d and A d . A d;
+//   B. alpha, p -= alpha d, d -= alpha U, partials of ||d||^2;
+//   C. the stopping test, the nonlocal partials of F^T d for the next step, compaction.
+template <class T>
+__global__ void __launch_bounds__(MR_THREADS, 2) k_onestep(MrArgs a) {
+    using P = typename Pair<T>::P;
+    extern __shared__ __align__(16) double smem[];
+    __shared__ int ok_sm;
+    const int k = a.k;
+    ColState S = col_state(smem, k);
+    const T* R = static_cast<const T*>(a.R);
+    const T* E = static_cast<const T*>(a.e);
+    T* X = static_cast<T*>(a.X);
+    T* V = static_cast<T*>(a.V);   // d
+    T* U = static_cast<T*>(a.U);   // A d
+    const P* hs = static_cast<const P*>(a.hs);
+    const int64_t ld = a.ld;
+    double* partA = a.part;
+    double* partB = a.part + (int64_t)gridDim.x * a.kp;
+    double* rowA = partA + (int64_t)blockIdx.x * a.kp;
+    double* rowB = partB + (int64_t)blockIdx.x * a.kp;
+    unsigned gen = 0;
+    unsigned long long tmark = 0;
+    const bool tr = a.stamps != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+    if (tr) tmark = gtimer();
+    auto mark = [&](int slot) {
+        if (tr) {
+            const unsigned long long t = gtimer();
+            a.stamps[slot] += t - tmark;
+            tmark = t;
+        }
+    };
+    auto identity = [](int pos) { return pos; };
+    auto active_col = [&](int pos) { return S.g(I_ACT)[pos]; };
+
+    if (a.nl_k) {
+        nl_chunk_partial(a, reinterpret_cast<const double*>(X), a.ldx, k, identity, [](int) { return true; },
+                         [](int) { return 1.0; });
+        if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+        nl_reduce(a, k, identity);
+    }
+    // ---- start: d = A_e p + r into V, ||d||^2 and ||r||^2 per column ----
+    for (int c0 = 0; c0 < k; c0 += MR_PASS) {
+        const Pass p = make_pass(c0, k);
+        double acc1 = 0.0, acc2 = 0.0;
+        spmm_pass<T>(a, hs, E, X, a.ldx, p, identity, [&](int64_t row, int j, T u) {
+            const T r = R[row * a.ldr + j];
+            const T d = u + r;
+            V[row * ld + j] = d;
+            acc1 += (double)d * (double)d;
+            acc2 += (double)r * (double)r;
+        });
+        block_partials(acc1, p, S.red, rowA);
+        block_partials(acc2, p, S.red, rowB);
+    }
+    mark(0);
+    if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+    mark(4);
+    grid_sum(partA, a.kp, k, S.f(F_RED1));
+    grid_sum(partB, a.kp, k, S.f(F_RED2));
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double dn = sqrt(S.f(F_RED1)[j]);
+        S.f(F_TOL)[j] = a.eta * sqrt(S.f(F_RED2)[j]);
+        S.f(F_PHIBAR)[j] = dn;
+        S.g(I_STEPS)[j] = 0;
+        S.g(I_ACTIVE)[j] = (dn > S.f(F_TOL)[j] && a.maxit > 0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (a.nl_k)
+        nl_chunk_partial(a, reinterpret_cast<const double*>(V), ld, k, identity,
+                         [&](int j) { return S.g(I_ACTIVE)[j] != 0; }, [](int) { return 1.0; });
+    if (threadIdx.x == 0) {
+        int na = 0;
+        for (int j = 0; j < k; ++j)
+            if (S.g(I_ACTIVE)[j]) S.g(I_ACT)[na++] = j;
+        S.nact()[0] = na;
+    }
+    mark(0);
+    if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+    mark(4);
+
+    for (int step = 1; step <= a.maxit && S.nact()[0] > 0; ++step) {
+        const int na = S.nact()[0];
+        // ---- A: U = A d, partials of A d . d and A d . A d ----
+        if (a.nl_k) {
+            nl_reduce(a, na, active_col);
+            mark(6);
+        }
+        for (int c0 = 0; c0 < na; c0 += MR_PASS) {
+            const Pass p = make_pass(c0, na);
+            double acc1 = 0.0, acc2 = 0.0;
+            spmm_pass<T>(a, hs, E, V, ld, p, active_col, [&](int64_t row, int j, T u) {
+                U[row * ld + j] = u;
+                acc1 += (double)u * (double)V[row * ld + j];
+                acc2 += (double)u * (double)u;
+            });
+            block_partials(acc1, p, S.red, rowA);
+            block_partials(acc2, p, S.red, rowB);
+        }
+        mark(1);
+        if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+        mark(4);
+        // ---- B: alpha, p -= alpha d, d -= alpha A d, partial ||d||^2 ----
+        grid_sum(partA, a.kp, na, S.f(F_RED1));
+        grid_sum(partB, a.kp, na, S.f(F_RED2));
+        for (int q = threadIdx.x; q < na; q += blockDim.x) {
+            const int j = S.g(I_ACT)[q];
+            const double uu = S.f(F_RED2)[q];
+            S.g(I_UPD)[j] = uu > 0.0 ? 1 : 0;
+            S.f(F_ALPHA)[j] = uu > 0.0 ? S.f(F_RED1)[q] / uu : 0.0;
+        }
+        __syncthreads();
+        for (int c0 = 0; c0 < na; c0 += MR_PASS) {
+            const Pass p = make_pass(c0, na);
+            double acc = 0.0;
+            rows_pass(a, p, active_col, [&](int64_t i, int j) {
+                if (!S.g(I_UPD)[j]) return;
+                const int64_t o = i * ld + j;
+                const double al = S.f(F_ALPHA)[j];
+                const double d = (double)V[o];
+                T* xp = X + i * a.ldx + j;
+                *xp = (T)((double)*xp - al * d);
+                const double dn = d - al * (double)U[o];
+                V[o] = (T)dn;
+                acc += dn * dn;
+            });
+            block_partials(acc, p, S.red, rowA);
+        }
+        mark(2);
+        if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+        mark(4);
+        // ---- C: stopping test, F^T d for the next step, compaction ----
+        grid_sum(partA, a.kp, na, S.f(F_RED1));
+        for (int q = threadIdx.x; q < na; q += blockDim.x) {
+            const int j = S.g(I_ACT)[q];
+            int cont = 0;
+            if (S.g(I_UPD)[j]) {
+                const double dn = sqrt(S.f(F_RED1)[q]);
+                S.f(F_PHIBAR)[j] = dn;
+                S.g(I_STEPS)[j] = step;
+                cont = dn > S.f(F_TOL)[j] && step < a.maxit;
+            }
+            S.g(I_CONT)[j] = cont;
+            if (!cont) S.g(I_ACTIVE)[j] = 0;
+        }
+        __syncthreads();
+        if (a.nl_k && step < a.maxit) {
+            mark(3);
+            nl_chunk_partial(a, reinterpret_cast<const double*>(V), ld, na, active_col,
+                             [&](int j) { return S.g(I_CONT)[j] != 0; }, [](int) { return 1.0; });
+            mark(5);
+        }
+        if (threadIdx.x == 0) {
+            int nn = 0;
+            for (int q = 0; q < na; ++q)
+                if (S.g(I_ACTIVE)[S.g(I_ACT)[q]]) S.g(I_ACT)[nn++] = S.g(I_ACT)[q];
+            S.nact()[0] = nn;
+        }
+        __syncthreads();
+        mark(3);
+        if (S.nact()[0] > 0 && step < a.maxit) {
+            if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
+            mark(4);
+        }
+    }
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < k; j += blockDim.x) a.steps_out[j] = S.g(I_STEPS)[j];
+}
+
 }  // namespace
 
 template <class T> static DBuf<T>& mr_vecs(Session* s);
@@ -612,7 +786,9 @@ template <> DBuf<double>& mr_vecs<double>(Session* s) { return s->mr_d; }
 // e: shifts eps_j relative to sigma0 (device, k entries of T).  steps: device ints (nullable).
 template <class T>
 int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double eta, int maxit, T* X,
-                 int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st) {
+                 int64_t ldx, int* steps, int64_t* total_steps, cudaStream_t st, int solver) {
+    if (solver != HBSD_LOCAL_MINRES && solver != HBSD_LOCAL_ONESTEP) return fail(HBSD_ERR_ARG, "unknown local solver");
+    const void* kern = solver == HBSD_LOCAL_ONESTEP ? (const void*)k_onestep<T> : (const void*)k_minres<T>;
     if (k <= 0) return 0;
     const size_t smem = mr_smem_bytes(k);
     if (smem > MR_SMEM_MAX) return fail(HBSD_ERR_ARG, "minres: too many columns for one launch");
@@ -630,10 +806,13 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         int dev = 0;
         HBSD_CUDA(cudaGetDevice(&dev));
         HBSD_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+        // one grid size for both kernels (the slot partition and the nonlocal index follow it)
         HBSD_CUDA(cudaFuncSetAttribute(k_minres<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_MAX));
-        int nb = 0;
+        HBSD_CUDA(cudaFuncSetAttribute(k_onestep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MR_SMEM_MAX));
+        int nb = 0, nb2 = 0;
         HBSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_minres<T>, MR_THREADS, MR_SMEM_MAX));
-        blocks_per_sm[ti] = nb;
+        HBSD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, k_onestep<T>, MR_THREADS, MR_SMEM_MAX));
+        blocks_per_sm[ti] = std::min(nb, nb2);
     }
     if (blocks_per_sm[ti] < 1) return fail(HBSD_ERR_UNSUPPORTED, "minres: kernel cannot be resident");
     const int grid = blocks_per_sm[ti] * num_sms;
@@ -725,7 +904,7 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         a.nl_part = q.mr_part.p; a.nl_zv = q.zv.p; a.nl_zg = q.zg.p;
     }
     void* args[] = {&a};
-    HBSD_CUDA(cudaLaunchCooperativeKernel((const void*)k_minres<T>, dim3(grid), dim3(MR_THREADS), args, smem, st));
+    HBSD_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(MR_THREADS), args, smem, st));
     HBSD_LAUNCHED(s);
     std::vector<int> h(k);
     int flags[4] = {0, 0, 0, 0};
@@ -739,8 +918,8 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     if (trace) {
         unsigned long long t[8];
         HBSD_CUDA(cudaMemcpy(t, s->mr_stamps.p, sizeof(t), cudaMemcpyDeviceToHost));
-        std::fprintf(stderr, "[hbsd]   MINRES k %d grid %d steps max %d sum %lld | us: start %.0f A %.0f B %.0f C %.0f barriers %.0f nl-partial %.0f nl-reduce %.0f\n",
-                     k, grid, mx, (long long)tot, t[0] * 1e-3, t[1] * 1e-3, t[2] * 1e-3, t[3] * 1e-3, t[4] * 1e-3,
+        std::fprintf(stderr, "[hbsd]   %s k %d grid %d steps max %d sum %lld | us: start %.0f A %.0f B %.0f C %.0f barriers %.0f nl-partial %.0f nl-reduce %.0f\n",
+                     solver == HBSD_LOCAL_ONESTEP ? "ONESTEP" : "MINRES", k, grid, mx, (long long)tot, t[0] * 1e-3, t[1] * 1e-3, t[2] * 1e-3, t[3] * 1e-3, t[4] * 1e-3,
                      t[5] * 1e-3, t[6] * 1e-3);
     }
     s->stats.minres_spmm_cols += tot + k;   // the start SpMM plus one column per step
@@ -749,6 +928,6 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
 }
 
 template int minres_batch<double>(Session*, const double*, int64_t, const double*, int, double, int, double*,
-                                  int64_t, int*, int64_t*, cudaStream_t);
+                                  int64_t, int*, int64_t*, cudaStream_t, int);
 
 }  // namespace hbsd

@@ -351,7 +351,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             k_gather_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.RU.p, ldp, C.Llist.p, a, n, B.Ra.p, ldp);
             HBSD_LAUNCHED(S);
             HBSD_TRY(minres_batch<T>(S, B.Ra.p, ldp, B.shifts.p, a, o.eta, o.max_minres, B.Xa.p, ldp, C.steps.p,
-                                     &msteps, st));
+                                     &msteps, st, o.local_solver));
             k_scatter_cols<T><<<grid_for(n * a), 256, 0, st>>>(B.Xa.p, ldp, C.Llist.p, a, n, B.P.p, ldp);
             HBSD_LAUNCHED(S);
             tm.end(ti, st);
@@ -544,6 +544,7 @@ void hbsd_options_default(hbsd_options* opt) {
     opt->precision = HBSD_PRECISION_FP64;
     opt->precond = HBSD_PRECOND_HYBRID;
     opt->seed = 1;
+    opt->local_solver = HBSD_LOCAL_MINRES;
 }
 
 const char* hbsd_status_string(int status) {
@@ -582,6 +583,8 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
     if (!std::isfinite(opt->sigma_bar)) return fail(HBSD_ERR_ARG, "sigma_bar must be set");
     if (opt->precond < HBSD_PRECOND_HYBRID || opt->precond > HBSD_PRECOND_LOCAL)
         return fail(HBSD_ERR_ARG, "unknown preconditioner mode");
+    if (opt->local_solver != HBSD_LOCAL_MINRES && opt->local_solver != HBSD_LOCAL_ONESTEP)
+        return fail(HBSD_ERR_ARG, "hbsd_create: local_solver must be HBSD_LOCAL_MINRES or HBSD_LOCAL_ONESTEP");
     if (!lb->dof_node || lb->grid[0] <= 0 || lb->grid[1] <= 0 || lb->grid[2] <= 0)
         return fail(HBSD_ERR_ARG, "local blocks need dof_node and a positive grid");
     hbsd_handle* h = new hbsd_handle();
@@ -771,6 +774,14 @@ int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, i
     Session* S = &h->s;
     HBSD_TRY(S->ws.alloc((size_t)304 * 2 * std::max(k, 1) + 64));
     return minres_batch<double>(S, R, ldr, e, k, eta, max_minres, P, ldp, steps, nullptr, S->stream);
+}
+
+int hbsd_onestep(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k, double eta, int max_steps,
+                 double* P, int64_t ldp, int* steps) {
+    if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+    Session* S = &h->s;
+    return minres_batch<double>(S, R, ldr, e, k, eta, max_steps, P, ldp, steps, nullptr, S->stream,
+                                HBSD_LOCAL_ONESTEP);
 }
 
 // Step-level calls without a session run on a temporary one that only carries scratch.

@@ -30,6 +30,8 @@ PRECISION_MIXED = 1
 PRECOND_HYBRID = 0
 PRECOND_GLOBAL = 1
 PRECOND_LOCAL = 2
+LOCAL_MINRES = 0
+LOCAL_ONESTEP = 1
 
 
 class hbsd_csr(C.Structure):
@@ -45,7 +47,7 @@ class hbsd_local_blocks(C.Structure):
 class hbsd_options(C.Structure):
     _fields_ = [("sigma_bar", C.c_double), ("sigma0", C.c_double), ("m0", C.c_int), ("tau1", C.c_double),
                 ("tau2", C.c_double), ("eta", C.c_double), ("max_minres", C.c_int), ("max_outer", C.c_int),
-                ("precision", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64)]
+                ("precision", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64), ("local_solver", C.c_int)]
 
 
 class hbsd_server_opts(C.Structure):
@@ -92,6 +94,7 @@ _SIGS = {
     "hbsd_update_H": (C.c_int, [_P, _D]),
     "hbsd_set_nonlocal": (C.c_int, [_P, C.c_int, _D, C.c_int64, _D]),
     "hbsd_res_history": (C.c_int, [_P, _D, C.c_int]),
+    "hbsd_onestep": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, C.c_double, C.c_int, _P, C.c_int64, _P]),
     "hbsd_solve": (C.c_int, [_P, C.c_int, C.c_double, _D, C.c_int, _D, _D, C.POINTER(C.c_int),
                              C.POINTER(hbsd_stats)]),
     "hbsd_solve_device": (C.c_int, [_P, C.c_int, C.c_double, _P, C.c_int64, _P, _P, C.c_int64,
@@ -320,6 +323,10 @@ class Session:
     def minres(self, R, e, P, eta, max_minres, steps):
         check(lib().hbsd_minres(self.h, ptr(R), ld(R), ptr(e), R.shape[1], eta, max_minres, ptr(P), ld(P),
                                 ptr(steps)), "hbsd_minres")
+
+    def onestep(self, R, e, P, eta, max_steps, steps):
+        check(lib().hbsd_onestep(self.h, ptr(R), ld(R), ptr(e), R.shape[1], eta, max_steps, ptr(P), ld(P),
+                                 ptr(steps)), "hbsd_onestep")
 
 
 def gram(Z, ZH, ZS, HR, SR, stream=0):
