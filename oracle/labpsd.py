@@ -13,9 +13,11 @@ solve) as the only library steps.  Readings of points the paper leaves open:
   R1  refinement residual: step 6(b) prints delta r_i = (H - eps_bar S) p_i + r_i; read as
       (H - eps_i S) p_i + r_i, i.e. MINRES on (H - eps_i S) p = -r_i started from the
       globally preconditioned p_i (Eq. indls / approxp).
-  R3  the global factor is a Cholesky-type factorisation (eps_bar is below the spectrum, so
-      H - eps_bar S is positive definite); the oracle uses a library sparse LU without
-      pivoting under a nested-dissection ordering (equivalent to LL^T up to rounding).
+  R3  the global factor is LDL^T with 1 x 1 pivots in a nested-dissection order (Eq. ldl without
+      the 2 x 2 Bunch-Kaufman blocks): for eps_bar below the spectrum every pivot is positive
+      and it is a Cholesky factorisation; for eps_bar inside it the negative pivots count the
+      eigenvalues below eps_bar (Sylvester).  The oracle uses a library sparse LU without
+      pivoting under that ordering (the same factorisation up to rounding); a zero pivot fails.
   R4  sigma0 = eps_bar (Sec. 5 shift making H positive definite); E is held shifted.
   R5  eps_bar = V_min - 0.1 for the synthetic matrices (a rigorous lower bound).
   R6  m0 = max(3, ceil(m/10)) (remark 1).
@@ -196,8 +198,9 @@ class GlobalPreconditioner:
         self.lu = spla.splu(Ap, permc_spec="NATURAL", diag_pivot_thresh=0.0,
                             options=dict(SymmetricMode=True))
         d = self.lu.U.diagonal()
-        if np.any(d.real <= 0):
-            raise np.linalg.LinAlgError("H - eps_bar S is not positive definite")
+        if np.any(d == 0) or not np.all(np.isfinite(d)):
+            raise np.linalg.LinAlgError("H - eps_bar S met a zero or non-finite pivot")
+        self.neg_pivots = int(np.count_nonzero(d.real < 0))     # inertia (R3)
         # SMW steps 1-4 (Sec. 4), only with a nonlocal term
         self.Fhat = self.Fsmw = None
         if F is not None and F.shape[1] > 0:

@@ -324,3 +324,38 @@ def test_planted_mistakes_are_caught(monkeypatch):
     monkeypatch.setattr(L, "refine", orig_ref)
     good = L.labpsd(p, nev, 1e-9, seed=3)
     assert r.iters > good.iters
+
+
+# ---- global factor with eps_bar inside the spectrum (reading R3: LDL^T with 1 x 1 pivots) ----
+def _interior_shift(p, below):
+    H, S = p.scipy_pair()
+    lam = sla.eigh(H.toarray(), S.toarray(), eigvals_only=True)
+    return 0.5 * (lam[below - 1] + lam[below]), lam
+
+
+@pytest.mark.parametrize("below", [1, 5, 12])
+def test_interior_shift_factor_counts_the_eigenvalues_below(below):
+    # Sylvester's law of inertia: H - eps S (S positive definite) has as many negative pivots
+    # as the pencil has eigenvalues below eps
+    p = pi.small_case(1)
+    eps, lam = _interior_shift(p, below)
+    H, S = p.scipy_pair()
+    K = L.GlobalPreconditioner((H - eps * S).tocsr(), p.dof_node, p.grid)
+    assert K.neg_pivots == below == int(np.count_nonzero(lam < eps))
+    R = pi.seed_normal_block(3, p.n, 5)
+    A = (H - eps * S).toarray()
+    ref = -np.linalg.solve(A, R)
+    assert np.abs(K.apply(R) - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_labpsd_with_an_interior_global_shift_matches_dense_eigh():
+    # eps_bar in the gap above the second eigenvalue (a shift within a few 1e-3 of a cluster
+    # makes K nearly singular and the iteration stalls near 1e-9, as shift-and-invert would)
+    p = pi.small_case(1)
+    eps, lam = _interior_shift(p, 2)
+    Hs, S, s0 = L.make_shifted(p)          # sigma0 stays below the spectrum (R4)
+    K = L.GlobalPreconditioner((Hs.loc - (eps - s0) * S).tocsr(), p.dof_node, p.grid)
+    assert K.neg_pivots == 2
+    r = L.labpsd(p, 16, 1e-10, seed=2, precond=K)
+    assert r.converged
+    assert np.allclose(r.lam, lam[:16], rtol=0, atol=1e-8 * np.abs(lam[:16]).max())
