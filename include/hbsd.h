@@ -129,6 +129,9 @@ typedef struct {
     int64_t matvec_cols;     /* columns through steps 3 and 7                              */
     int64_t minres_spmm_cols;/* columns through the shifted SpMM of step 6(b)              */
     int precond_calls;       /* applications of step 6(a)                                   */
+    int64_t neg_pivots;      /* negative pivots of the LDL^T factor of H_loc - eps_bar S: the
+                                number of eigenvalues of the local pencil below eps_bar
+                                (Sylvester's inertia; 0 when eps_bar lies below the spectrum) */
 } hbsd_stats;
 
 typedef struct hbsd_handle hbsd_handle;
@@ -140,8 +143,12 @@ void hbsd_options_default(hbsd_options* opt);
  * H - sigma_bar S once (Sec. 4, Eq. ldl; remark: computed once and reused).  lb is required
  * (the ordering of the factorisation); opt may be NULL (defaults, sigma_bar must then be
  * set by hbsd_set_sigma, else HBSD_ERR_ARG).  stream: cudaStream_t as void* for all work of
- * the session (NULL = a stream the session creates).  Returns HBSD_ERR_NOT_SPD if the
- * factorisation meets a non-positive pivot, HBSD_ERR_UNSUPPORTED for complex input. */
+ * the session (NULL = a stream the session creates).  The factor is a Cholesky when
+ * sigma_bar lies below the spectrum; otherwise (a non-positive pivot) the factorisation is
+ * redone as LDL^T with 1 x 1 pivots in the same order (Eq. ldl without 2 x 2 blocks), whose
+ * negative pivots (hbsd_stats.neg_pivots) count the eigenvalues below sigma_bar; sigma0 must then
+ * be set below the spectrum.  Returns HBSD_ERR_NOT_SPD if a pivot is zero or not finite,
+ * HBSD_ERR_UNSUPPORTED for complex input. */
 int hbsd_create(const hbsd_csr* H, const hbsd_csr* S, const hbsd_local_blocks* lb,
                 const hbsd_options* opt, void* stream, hbsd_handle** out);
 

@@ -131,13 +131,20 @@ __global__ void k_extend_add_matrix(const SnDev* __restrict__ sn, const int* __r
 }
 
 // Cholesky of the diagonal block [k0, k0+kb) of each front in shared memory, plus its inverse.
+// SIGNED: the LDL^T form with 1 x 1 pivots, held as A = Lt Sg Lt^T with Sg = diag(+-1) and
+// Lt = L |D|^{1/2}: a pivot d gives Lt_cc = sqrt|d|, sign(d) goes to sgn[] (permuted order) and
+// the column below is divided by Lt_cc sign(d); negative pivots are counted in err[1].  Only a
+// zero or non-finite pivot fails (err[0]).  Without SIGNED a non-positive pivot fails.
+template <bool SIGNED>
 __global__ void __launch_bounds__(256) k_potrf_block(const SnDev* __restrict__ sn, const int* __restrict__ ids,
                                                      int nids, int k0, double* __restrict__ F,
-                                                     double* __restrict__ Dinv, int* __restrict__ err) {
+                                                     double* __restrict__ Dinv, int* __restrict__ err,
+                                                     double* __restrict__ sgn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto A = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
     auto X = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * NB * (NB + 1));
-    __shared__ int bad;
+    __shared__ int bad, nneg;
+    __shared__ double sg[NB];
     const SnDev s = sn[ids[blockIdx.x]];
     if (k0 >= s.ns) return;
     const int kb = min(NB, s.ns - k0);
@@ -148,26 +155,50 @@ __global__ void __launch_bounds__(256) k_potrf_block(const SnDev* __restrict__ s
         A[i][j] = (i < kb && j < kb && i >= j) ? Fb[(int64_t)j * nf + i] : 0.0;
         X[i][j] = 0.0;
     }
-    if (threadIdx.x == 0) bad = 0;
+    if (threadIdx.x == 0) bad = nneg = 0;
     __syncthreads();
     for (int c = 0; c < kb; ++c) {
         if (threadIdx.x == 0) {
             const double piv = A[c][c];
-            if (!(piv > 0.0)) { bad = 1; A[c][c] = 1.0; }
-            else A[c][c] = sqrt(piv);
+            if constexpr (SIGNED) {
+                if (!(fabs(piv) > 0.0) || !isfinite(piv)) { bad = 1; A[c][c] = 1.0; sg[c] = 1.0; }
+                else {
+                    A[c][c] = sqrt(fabs(piv));
+                    sg[c] = piv < 0.0 ? -1.0 : 1.0;
+                    if (piv < 0.0) ++nneg;
+                }
+            } else {
+                if (!(piv > 0.0)) { bad = 1; A[c][c] = 1.0; }
+                else A[c][c] = sqrt(piv);
+            }
         }
         __syncthreads();
         const double l = A[c][c];
-        for (int i = c + 1 + threadIdx.x; i < kb; i += blockDim.x) A[i][c] /= l;
-        __syncthreads();
-        const int m = kb - c - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int i = c + 1 + t % m, j = c + 1 + t / m;
-            if (i >= j) A[i][j] -= A[i][c] * A[j][c];
+        if constexpr (SIGNED) {
+            const double sc = sg[c];
+            for (int i = c + 1 + threadIdx.x; i < kb; i += blockDim.x) A[i][c] = A[i][c] / l * sc;
+            __syncthreads();
+            const int m = kb - c - 1;
+            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                const int i = c + 1 + t % m, j = c + 1 + t / m;
+                if (i >= j) A[i][j] -= (A[i][c] * sc) * A[j][c];
+            }
+        } else {
+            for (int i = c + 1 + threadIdx.x; i < kb; i += blockDim.x) A[i][c] /= l;
+            __syncthreads();
+            const int m = kb - c - 1;
+            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                const int i = c + 1 + t % m, j = c + 1 + t / m;
+                if (i >= j) A[i][j] -= A[i][c] * A[j][c];
+            }
         }
         __syncthreads();
     }
     if (bad && threadIdx.x == 0) atomicExch(err, 1);
+    if constexpr (SIGNED) {
+        if (threadIdx.x == 0 && nneg) atomicAdd(err + 1, nneg);
+        for (int c = threadIdx.x; c < kb; c += blockDim.x) sgn[s.first + k0 + c] = sg[c];
+    }
     // inverse of the lower-triangular block, one column per thread
     for (int c = threadIdx.x; c < kb; c += blockDim.x) {
         X[c][c] = 1.0 / A[c][c];
@@ -186,9 +217,12 @@ __global__ void __launch_bounds__(256) k_potrf_block(const SnDev* __restrict__ s
     }
 }
 
-// Panel: F[k0+kb : nf, k0 : k0+kb] := F[...] * L_kk^{-T}  (row tiles of 64)
+// Panel: F[k0+kb : nf, k0 : k0+kb] := F[...] * L_kk^{-T}  (row tiles of 64); SIGNED: then column
+// c times its pivot sign
+template <bool SIGNED>
 __global__ void __launch_bounds__(256) k_trsm_panel(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                                                    int k0, double* __restrict__ F, const double* __restrict__ Dinv) {
+                                                    int k0, double* __restrict__ F, const double* __restrict__ Dinv,
+                                                    const double* __restrict__ sgn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto Ar = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
     auto Di = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * 64 * (NB + 1));
@@ -213,13 +247,16 @@ __global__ void __launch_bounds__(256) k_trsm_panel(const SnDev* __restrict__ sn
         if (i >= rows || c >= kb) continue;
         double acc = 0.0;
         for (int u = 0; u <= c; ++u) acc += Ar[i][u] * Di[c][u];
+        if constexpr (SIGNED) acc *= sgn[s.first + k0 + c];
         Fc[(int64_t)c * nf + r0 + i] = acc;
     }
 }
 
-// Trailing update F22 -= L21 L21^T over 64 x 64 tiles of the lower triangle.
+// Trailing update F22 -= L21 L21^T over 64 x 64 tiles of the lower triangle (SIGNED:
+// F22 -= L21 Sg L21^T).
+template <bool SIGNED>
 __global__ void __launch_bounds__(256) k_syrk_update(const SnDev* __restrict__ sn, const int* __restrict__ ids,
-                                                     int k0, double* __restrict__ F) {
+                                                     int k0, double* __restrict__ F, const double* __restrict__ sgn) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto Li = reinterpret_cast<double(*)[NB + 1]>(smem_raw);
     auto Lj = reinterpret_cast<double(*)[NB + 1]>(smem_raw + sizeof(double) * 64 * (NB + 1));
@@ -251,6 +288,11 @@ __global__ void __launch_bounds__(256) k_syrk_update(const SnDev* __restrict__ s
         double a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) { a[u] = Li[tr + 16 * u][c]; b[u] = Lj[tc + 16 * u][c]; }
+        if constexpr (SIGNED) {
+            const double sc = sgn[s.first + k0 + c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] *= sc;
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -513,6 +555,17 @@ __global__ void k_solve_reduce(const SnDev* __restrict__ sn, const SolveItem* __
 }
 
 // P[perm[i]] = -x[i]
+// Y[i, j] *= sgn[i]
+template <class T>
+__global__ void k_scale_rows(const double* __restrict__ sgn, T* __restrict__ Y, int64_t ld, int64_t n, int k) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t - i * k);
+        Y[i * ld + j] *= (T)sgn[i];
+    }
+}
+
 template <class T>
 __global__ void k_unpermute_neg(const int32_t* __restrict__ perm, const T* __restrict__ xp, int64_t ldx,
                                 int64_t n, int k, T* __restrict__ P, int64_t ldp) {
@@ -827,13 +880,25 @@ int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const
     HBSD_TRY(fronts.alloc(std::max<int64_t>(1, fo)));
     HBSD_TRY(f.Dinv.alloc(std::max<int64_t>(1, f.dinv_total)));
     DBuf<int> err;
-    HBSD_TRY(err.alloc(1));
-    HBSD_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    HBSD_TRY(err.alloc(2));
     const SnDev* dsn = reinterpret_cast<const SnDev*>(f.d_sn.p);
-    HBSD_TRY(allow_smem(k_potrf_block, tile2_bytes<double>()));
-    HBSD_TRY(allow_smem(k_trsm_panel, tile2_bytes<double>()));
-    HBSD_TRY(allow_smem(k_syrk_update, tile2_bytes<double>()));
-    // ---- numeric factorisation, level by level ----
+    HBSD_TRY(allow_smem(k_potrf_block<false>, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_trsm_panel<false>, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_syrk_update<false>, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_potrf_block<true>, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_trsm_panel<true>, tile2_bytes<double>()));
+    HBSD_TRY(allow_smem(k_syrk_update<true>, tile2_bytes<double>()));
+    // ---- numeric factorisation, level by level: Cholesky; on a non-positive pivot (eps_bar
+    // inside the spectrum) once more in the signed LDL^T form ----
+    f.signed_form = false;
+    f.neg_pivots = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+    const bool sgnd = attempt == 1;
+    if (sgnd) {
+        HBSD_TRY(f.sgn.alloc(std::max<int64_t>(1, n)));
+        f.signed_form = true;
+    }
+    HBSD_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int), st));
     for (int h = 0; h <= H; ++h) {
         const int64_t fb = level_front_begin[h], fe = level_front_begin[h + 1];
         k_zero<<<grid_for(fe - fb), 256, 0, st>>>(fronts.p + fb, fe - fb);
@@ -857,23 +922,31 @@ int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const
         const int* lid = LL.ids.p + LL.offs[h];
         const int cnt = LL.counts[h];
         for (int k0 = 0; k0 < LL.max_ns[h]; k0 += NB) {
-            k_potrf_block<<<cnt, 256, tile2_bytes<double>(), st>>>(dsn, lid, cnt, k0, fronts.p, f.Dinv.p, err.p);
+            if (sgnd) k_potrf_block<true><<<cnt, 256, tile2_bytes<double>(), st>>>(dsn, lid, cnt, k0, fronts.p, f.Dinv.p, err.p, f.sgn.p);
+            else k_potrf_block<false><<<cnt, 256, tile2_bytes<double>(), st>>>(dsn, lid, cnt, k0, fronts.p, f.Dinv.p, err.p, nullptr);
             HBSD_LAUNCHED(s);
             int rem = 0, pairs = 0;
             level_extent(f, h, k0, &rem, &pairs);
             if (rem <= 0) continue;
             dim3 gt(ceil_div(rem, 64), cnt);
-            k_trsm_panel<<<gt, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p, f.Dinv.p);
+            if (sgnd) k_trsm_panel<true><<<gt, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p, f.Dinv.p, f.sgn.p);
+            else k_trsm_panel<false><<<gt, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p, f.Dinv.p, nullptr);
             HBSD_LAUNCHED(s);
             dim3 gs(pairs, cnt);
-            k_syrk_update<<<gs, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p);
+            if (sgnd) k_syrk_update<true><<<gs, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p, f.sgn.p);
+            else k_syrk_update<false><<<gs, 256, tile2_bytes<double>(), st>>>(dsn, lid, k0, fronts.p, nullptr);
             HBSD_LAUNCHED(s);
         }
     }
-    int herr = 0;
-    HBSD_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int herr[2] = {0, 0};
+    HBSD_CUDA(cudaMemcpyAsync(herr, err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     HBSD_CUDA(cudaStreamSynchronize(st));
-    if (herr) return fail(HBSD_ERR_NOT_SPD, "factorisation of H - sigma_bar S met a non-positive pivot");
+    if (!herr[0]) {
+        f.neg_pivots = herr[1];
+        break;
+    }
+    if (sgnd) return fail(HBSD_ERR_NOT_SPD, "factorisation of H - sigma_bar S met a zero or non-finite pivot");
+    }
     HBSD_TRY(f.L.alloc(std::max<int64_t>(1, L_tot)));
     {
         int64_t maxp = 1;
@@ -956,6 +1029,7 @@ int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const
     auto t1 = std::chrono::steady_clock::now();
     s->stats.t_factor_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     s->stats.nnz_L = f.nnz_L;
+    s->stats.neg_pivots = f.neg_pivots;
     s->stats.n_supernodes = nsn;
     return 0;
 }
@@ -1050,6 +1124,10 @@ int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, in
         k_fwd_assemble<T><<<gi, 256, 0, st>>>(dsn, LL.ids.p + LL.offs[h], f.perm.p, f.src.p, R, ldr, k, fv, ld);
         HBSD_LAUNCHED(s);
         HBSD_TRY(gemm(h, false));
+    }
+    if (f.signed_form) {   // x = Lt^{-T} Sg Lt^{-1} r: the pivot signs between the sweeps
+        k_scale_rows<T><<<grid_for(f.n * k), 256, 0, st>>>(f.sgn.p, Y, ld, f.n, k);
+        HBSD_LAUNCHED(s);
     }
     for (int h = H; h >= 0; --h) HBSD_TRY(gemm(h, true));
     k_unpermute_neg<T><<<grid_for(f.n * k), 256, 0, st>>>(f.perm.p, X, ld, f.n, k, P, ldp);

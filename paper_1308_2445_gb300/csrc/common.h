@@ -164,6 +164,10 @@ struct Factor {
     // solve workspace: front vectors | y | x | partials
     DBuf<double> sws;
     DBuf<float> sws32;
+    // signed LDL^T form (eps_bar inside the spectrum): pivot signs in permuted order
+    bool signed_form = false;
+    int64_t neg_pivots = 0;
+    DBuf<double> sgn;
 };
 
 int factor_build(Session* s, Factor& f, int64_t n, const int64_t* row_ptr, const int32_t* col_idx,

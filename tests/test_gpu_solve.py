@@ -166,10 +166,15 @@ def test_scf_follow_up_keeps_first_factor():
     assert it2 < it                                 # and the warm start pays
 
 
-def test_not_spd_is_reported():
+def test_failed_factorisation_is_reported():
+    # a non-finite diagonal entry gives a non-finite pivot in both the Cholesky and the signed
+    # LDL^T attempt (an eps_bar inside the spectrum is not an error: tests/test_gpu_ldlt.py)
     p = pi.small_case(1)
+    hv = p.h_val.copy()
+    d0 = int(np.nonzero(p.col_idx[p.row_ptr[0]:p.row_ptr[1]] == 0)[0][0])
+    hv[p.row_ptr[0] + d0] = np.nan
     with pytest.raises(hb().HbsdError) as ei:
-        hb().Session(p.n, p.row_ptr, p.col_idx, p.h_val, p.s_val, p.dof_node, p.grid, sigma_bar=30.0)
+        hb().Session(p.n, p.row_ptr, p.col_idx, hv, p.s_val, p.dof_node, p.grid, sigma_bar=p.eps_bar)
     assert ei.value.code == hb().HBSD_ERR_NOT_SPD
 
 
