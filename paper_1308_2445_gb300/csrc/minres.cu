@@ -21,10 +21,12 @@
 // sums the rows of its chunk of F against U into per-chunk partials; after the barrier each
 // block reduces, in a fixed order, only the projectors its own rows meet (and those coupled to
 // them through G), so the step keeps its three barriers.  The start takes one more.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "common.h"
 
@@ -497,6 +499,7 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
             nl_reduce(a, na, active_col);
             mark(6);
         }
+        const unsigned long long ta = (a.stamps && threadIdx.x == 0) ? gtimer() : 0ull;
         for (int c0 = 0; c0 < na; c0 += MR_PASS) {
             const Pass p = make_pass(c0, na);
             double acc = 0.0;
@@ -506,6 +509,7 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
             });
             block_partials(acc, p, S.red, rowA);
         }
+        if (a.stamps && threadIdx.x == 0) a.stamps[8 + blockIdx.x] += gtimer() - ta;   // per-block phase A (tracing)
         mark(1);
         if (!grid_barrier(a.bar, gridDim.x, gen, a.err, &ok_sm)) return;
         mark(4);
@@ -888,8 +892,8 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
     static const bool trace = std::getenv("HBSD_TRACE") != nullptr;
     a.stamps = nullptr;
     if (trace) {
-        HBSD_TRY(s->mr_stamps.alloc(8));
-        HBSD_CUDA(cudaMemsetAsync(s->mr_stamps.p, 0, 8 * sizeof(unsigned long long), st));
+        HBSD_TRY(s->mr_stamps.alloc(8 + grid));
+        HBSD_CUDA(cudaMemsetAsync(s->mr_stamps.p, 0, (8 + grid) * sizeof(unsigned long long), st));
         a.stamps = s->mr_stamps.p;
     }
     a.nl_k = nl ? s->nl.k : 0;
@@ -921,6 +925,22 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         std::fprintf(stderr, "[hbsd]   %s k %d grid %d steps max %d sum %lld | us: start %.0f A %.0f B %.0f C %.0f barriers %.0f nl-partial %.0f nl-reduce %.0f\n",
                      solver == HBSD_LOCAL_ONESTEP ? "ONESTEP" : "MINRES", k, grid, mx, (long long)tot, t[0] * 1e-3, t[1] * 1e-3, t[2] * 1e-3, t[3] * 1e-3, t[4] * 1e-3,
                      t[5] * 1e-3, t[6] * 1e-3);
+        std::vector<unsigned long long> pb(grid);
+        HBSD_CUDA(cudaMemcpy(pb.data(), s->mr_stamps.p + 8, grid * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        std::vector<unsigned long long> srt(pb);
+        std::sort(srt.begin(), srt.end());
+        double mean = 0.0;
+        for (auto v : pb) mean += (double)v;
+        mean /= grid;
+        int imax = (int)(std::max_element(pb.begin(), pb.end()) - pb.begin());
+        std::fprintf(stderr, "[hbsd]     phase A per block us: min %.0f p10 %.0f median %.0f p90 %.0f max %.0f (block %d) mean %.0f\n",
+                     srt[0] * 1e-3, srt[grid / 10] * 1e-3, srt[grid / 2] * 1e-3, srt[grid * 9 / 10] * 1e-3, srt[grid - 1] * 1e-3,
+                     imax, mean * 1e-3);
+        if (std::getenv("HBSD_TRACE_BLOCKS")) {
+            std::fprintf(stderr, "[hbsd]     phase A blocks:");
+            for (int b = 0; b < grid; ++b) std::fprintf(stderr, " %.0f", pb[b] * 1e-3);
+            std::fprintf(stderr, "\n");
+        }
     }
     s->stats.minres_spmm_cols += tot + k;   // the start SpMM plus one column per step
     if (total_steps) *total_steps = tot;

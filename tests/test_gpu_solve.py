@@ -244,3 +244,38 @@ def test_medium_solve_mixed_against_stored_oracle():
     assert rc == 0
     assert np.abs(lam - ref).max() <= 1e-9 * np.abs(ref).max()
     assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+
+
+# ------------------------------------------------------------------ full size (64^3, nev = 256)
+def test_full_size_mixed_against_fp64_with_inertia_check():
+    """64^3 Q1, 32 atoms, 4 enrichment dofs per node, nev = 256 (n = 334,272): too large for the
+    oracle, so checked by properties that hold at any size.  Mixed and FP64 forms agree per
+    eigenvalue; the mixed eigenpairs meet Res <= tol recomputed on the host and are
+    S-orthonormal; and the factor of H - sigma S at a shift in the widest gap of the computed
+    spectrum has exactly as many negative pivots as computed eigenvalues below it (Sylvester's
+    law of inertia), so no eigenvalue below the shift was missed."""
+    import scipy.sparse as sp
+    p = pi.large_case(1)
+    nev = pi.LARGE_NEV
+    X0 = pi.seed_normal_block(1, p.n, nev + L.default_m0(nev))
+    sm = hb().Session.from_problem(p, precision=hb().PRECISION_MIXED)
+    lam_m, X, it_m, rc_m, st_m = sm.solve(nev, 1e-8, X0=X0)
+    sig0 = sm.sigma0
+    sm.close()
+    sd = hb().Session.from_problem(p)
+    lam_d, _, it_d, rc_d, _ = sd.solve(nev, 1e-8, X0=X0, want_vectors=False)
+    sd.close()
+    assert rc_m == 0 and rc_d == 0
+    scale = np.abs(lam_d).max()
+    assert np.abs(lam_m - lam_d).max() <= 1e-9 * scale
+    assert host_res(p, lam_m, X, sig0).max() <= 1e-8 * 1.001
+    H, S = p.scipy_pair()
+    G = X.T @ (S @ X)
+    assert np.abs(G - np.eye(nev)).max() <= 1e-9
+    gaps = np.diff(lam_m)
+    i = int(np.argmax(gaps[nev // 2:])) + nev // 2          # lam[i] < sigma < lam[i + 1]
+    sigma = 0.5 * (lam_m[i] + lam_m[i + 1])
+    si = hb().Session(p.n, p.row_ptr, p.col_idx, p.h_val, p.s_val, p.dof_node, p.grid, sigma_bar=sigma,
+                      sigma0=p.eps_bar)
+    assert si.stats()["neg_pivots"] == i + 1
+    si.close()

@@ -264,7 +264,8 @@ def test_gram_df64(q, n):
     assert np.array_equal(h, h.T) and np.array_equal(sr, sr.T)
 
 
-@pytest.mark.parametrize("q,k,n", [(19, 19, 646), (35, 19, 1000), (135, 71, 3001), (8, 3, 5), (282, 30, 700)])
+@pytest.mark.parametrize("q,k,n", [(19, 19, 646), (35, 19, 1000), (135, 71, 3001), (8, 3, 5), (282, 30, 700),
+                                   (300, 282, 1001), (538, 282, 777)])   # the last two tile W
 def test_update_df64(q, k, n):
     Z = pi.seed_normal_block(q * 3, n, q) * np.logspace(-4, 4, q)
     W = pi.seed_normal_block(q * 5, q, k)
