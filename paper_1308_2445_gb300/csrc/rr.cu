@@ -26,6 +26,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <mutex>
+#include <vector>
 
 #include "common.h"
 
@@ -121,19 +122,28 @@ __device__ RRWork rr_work(double* ws, int q, int k, int nc) {
 struct RRLayout {
     int64_t fixed, p26, p5, total;
 };
-inline RRLayout rr_layout(int q, int k, int rb, int nwr, int stage_l, int scr_sm) {
+// grows: the row blocks A, Qr, cb2 and the phase-5 G, Vr live in a per-CTA region of the global
+// workspace instead (large q); shared memory keeps the q-vectors and the per-warp buffers.
+inline RRLayout rr_layout(int q, int k, int rb, int nwr, int stage_l, int scr_sm, int grows = 0) {
     RRLayout L;
-    L.fixed = (int64_t)2 * rb * q + 2 * (q + 1) + q + (int64_t)2 * rb * (q + 2) + 5 * q + 2 * q + 64 + 2 * k;
+    L.fixed = (grows ? 0 : (int64_t)2 * rb * q + (int64_t)2 * rb * (q + 2)) + 2 * (q + 1) + q + 5 * q + 2 * q + 64 +
+              2 * k;
     L.p26 = (stage_l ? (int64_t)q * q : 0) + (int64_t)RR_NW * q;
-    L.p5 = (int64_t)k * k + (int64_t)rb * k + (int64_t)RR_NW * k + (scr_sm ? (int64_t)nwr * 6 * q : 0);
+    L.p5 = (grows ? 0 : (int64_t)k * k + (int64_t)rb * k) + (int64_t)RR_NW * k + (scr_sm ? (int64_t)nwr * 6 * q : 0);
     L.total = L.fixed + (L.p26 > L.p5 ? L.p26 : L.p5);
     return L;
+}
+// doubles of one CTA's global row region (grows): A | Qr | cb2 | G | Vr
+__host__ __device__ inline int64_t rr_grows_per(int q, int k, int rb) {
+    return (int64_t)2 * rb * q + (int64_t)2 * rb * (q + 2) + (int64_t)k * k + (int64_t)rb * k;
 }
 
 }  // namespace
 
-int64_t rr_cluster_ws_doubles(int q, int k, int nc) {
-    return rr_stamp_offset(q, k, nc) + 16 + (int64_t)nc * RR_NW * 6 * q + 64;
+__host__ __device__ int64_t rr_cluster_ws_doubles(int q, int k, int nc, int grows) {
+    const int rb = (q + nc - 1) / nc;
+    return rr_stamp_offset(q, k, nc) + 16 + (int64_t)nc * RR_NW * 6 * q + 64 +
+           (grows ? (int64_t)nc * rr_grows_per(q, k, rb) : 0) + 3 * k;   // + per-vector diagnostics
 }
 
 // drop_tol = 0: a pivot below PIVOT_MIN stops the kernel (info[3]) for the caller's fallback.
@@ -143,7 +153,7 @@ int64_t rr_cluster_ws_doubles(int q, int k, int nc) {
 __global__ void __launch_bounds__(RR_THREADS_C, 1)
     k_rr_cluster(const double* __restrict__ HR, const double* __restrict__ SR, int q, int k,
                  double* __restrict__ theta, double* __restrict__ Wout, double* __restrict__ ws,
-                 int* __restrict__ info, double drop_tol, int stage_l, int scr_sm) {
+                 int* __restrict__ info, double drop_tol, int stage_l, int scr_sm, int grows) {
     cg::cluster_group cluster = cg::this_cluster();
     const int NC = (int)cluster.num_blocks();
     const int rank = (int)cluster.block_rank();
@@ -153,12 +163,33 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
     const int lane = tid & 31, warp = tid >> 5;
     const int nwr = min((k + NC - 1) / NC, RR_NW);   // inverse-iteration warps per CTA
     extern __shared__ __align__(16) double sm[];
-    double* A = sm;                               // rb x q: row i at (i - r0) * q
-    double* Qr = A + (int64_t)rb * q;             // rb x q: rows of Q
-    double* vb2 = Qr + (int64_t)rb * q;           // [2][q+1]: Householder vector, tau at [q]
-    double* pb = vb2 + 2 * (q + 1);               // [q]
-    double* cb2 = pb + q;                         // [2][rb][q+2]: Cholesky panels, code at [q], 1/l_cc at [q+1]
-    double* dv = cb2 + (int64_t)2 * rb * (q + 2);
+    RRWork W = rr_work(ws, q, k, NC);
+    // global row regions of the CTAs (grows): A | Qr | cb2 | G | Vr, one region per rank
+    double* const Rg = W.scratch + (int64_t)NC * RR_NW * 6 * q;
+    const int64_t rper = rr_grows_per(q, k, rb);
+    // per-vector diagnostics of the eigenvector phase (read by the host under HBSD_RRDBG=2)
+    double* const vdiag = ws + rr_cluster_ws_doubles(q, k, 16, 1) - 3 * k;
+    double* A;                                    // rb x q: row i at (i - r0) * q
+    double* Qr;                                   // rb x q: rows of Q
+    double* vb2;                                  // [2][q+1]: Householder vector, tau at [q]
+    double* pb;                                   // [q]
+    double* cb2;                                  // [2][rb][q+2]: Cholesky panels, code at [q], 1/l_cc at [q+1]
+    double* dv;
+    if (grows) {
+        A = Rg + (int64_t)rank * rper;
+        Qr = A + (int64_t)rb * q;
+        cb2 = Qr + (int64_t)rb * q;
+        vb2 = sm;
+        pb = vb2 + 2 * (q + 1);
+        dv = pb + q;
+    } else {
+        A = sm;
+        Qr = A + (int64_t)rb * q;
+        vb2 = Qr + (int64_t)rb * q;
+        pb = vb2 + 2 * (q + 1);
+        cb2 = pb + q;
+        dv = cb2 + (int64_t)2 * rb * (q + 2);
+    }
     double* dr = dv + q;                          // 1.0 where a column was dropped
     double* rinv = dr + q;                        // 1 / L_ii
     double* dd = rinv + q;                        // tridiagonal
@@ -170,7 +201,6 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
     double* rinvG = red + 64;                     // [k]
     int* ord = reinterpret_cast<int*>(rinvG + k); // [k]
     double* big = rinvG + 2 * k;
-    RRWork W = rr_work(ws, q, k, NC);
     const bool stamp = rank == 0 && tid == 0;
 
     for (int i = tid; i < q; i += nt) {
@@ -226,8 +256,9 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
         cluster.sync();
         if (rank != b) {
             // pull L(j, c), j >= p1, and the codes and 1/l_cc of the panel rows from CTA b
-            const double* srcA = cluster.map_shared_rank(A, b);
-            const double* srcP = cluster.map_shared_rank(pbk, b);
+            const double* srcA = grows ? Rg + (int64_t)b * rper : cluster.map_shared_rank(A, b);
+            const double* srcP = grows ? Rg + (int64_t)b * rper + (int64_t)2 * rb * q + (int64_t)(b & 1) * rb * (q + 2)
+                                       : cluster.map_shared_rank(pbk, b);
             const int w = (rank > b ? q - p1 : 0) + 2;
             for (int idx = tid; idx < (p1 - p0) * w; idx += nt) {
                 const int c = p0 + idx / w, jj = idx % w;
@@ -534,9 +565,10 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
     // the Rayleigh quotient theta = x^T T x.  Pivoted tridiagonal LU with reciprocal pivots,
     // sequential on lane 0; pivots below eps ||T|| are raised to it, so that a shift on an
     // eigenvalue amplifies the wanted direction by about 1/eps instead of overflowing.
-    double* G = big;                                   // phase-5 region
+    const int64_t goff = (int64_t)2 * rb * q + (int64_t)2 * rb * (q + 2);   // G in a global row region
+    double* G = grows ? Rg + (int64_t)rank * rper + goff : big;   // phase-5 region
     double* Vr = G + (int64_t)k * k;
-    double* yw = Vr + (int64_t)rb * k;
+    double* yw = grows ? big : Vr + (int64_t)rb * k;
     double* scr_base = yw + (int64_t)RR_NW * k;
     {
         double* scr = scr_sm ? scr_base + (int64_t)warp * 6 * q : W.scratch + ((int64_t)rank * RR_NW + warp) * 6 * q;
@@ -589,10 +621,16 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
             }
             __syncwarp();
         };
-        // x / ||x||; false (x untouched) when x is not finite
+        // x / ||x||; false (x untouched) when an entry of x is not finite or x is zero
+        // (fmax drops NaN, so the entries are tested one by one)
         auto normalise = [&]() {
             double mx = 0.0;
-            for (int i = lane; i < q; i += 32) mx = fmax(mx, fabs(x[i]));
+            bool bad = false;
+            for (int i = lane; i < q; i += 32) {
+                bad |= !isfinite(x[i]);
+                mx = fmax(mx, fabs(x[i]));
+            }
+            if (__any_sync(0xffffffffu, bad)) return false;
             for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
             if (!(mx > 0.0 && isfinite(mx))) return false;
             const double sc = 1.0 / mx;
@@ -623,8 +661,62 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
             th = wsum(th);
             __syncwarp();
             solve64(th);
-            if (normalise())
+            bool ok2 = normalise();
+            if (ok2)
                 for (int i = lane; i < q; i += 32) W.V[(int64_t)i * k + j] = x[i];
+            // Rayleigh-quotient iteration until the residual ||T x - theta x|| is below
+            // 1e-12 ||T|| (a start vector nearly orthogonal to the wanted eigenvector leaves a
+            // neighbour's component after the first solve): at most three more solves
+            // only for a separated eigenvalue: inside a cluster narrower than 1e-6 ||T|| further
+            // solves would pull several vectors onto one eigenvector, while the mixing they
+            // remove there costs almost nothing (it is weighted by the cluster width).  A vector
+            // is accepted only while its quotient stays in eigenvalue j's interval (midpoints to
+            // the neighbouring coarse eigenvalues): unguarded, the iteration can settle on a
+            // neighbour and duplicate its vector.
+            double gapj = DBL_MAX;
+            if (j > 0) gapj = fmin(gapj, fabs(W.lam[j] - W.lam[j - 1]));
+            if (j + 1 < k) gapj = fmin(gapj, fabs(W.lam[j + 1] - W.lam[j]));
+            const bool separated = gapj > 1e-6 * tnorm;
+            const double lo_j = j > 0 ? 0.5 * (W.lam[j - 1] + W.lam[j]) : -DBL_MAX;
+            const double hi_j = j + 1 < k ? 0.5 * (W.lam[j] + W.lam[j + 1]) : DBL_MAX;
+            auto rayleigh = [&]() {
+                double t2 = 0.0;
+                for (int i = lane; i < q; i += 32) {
+                    t2 = fma(dd[i] * x[i], x[i], t2);
+                    if (i + 1 < q) t2 = fma(2.0 * ee[i] * x[i], x[i + 1], t2);
+                }
+                return wsum(t2);
+            };
+            int extra = 0;
+            if (ok2 && separated) {
+                double th2 = rayleigh();
+                while (extra < 3 && th2 >= lo_j && th2 <= hi_j) {
+                    double r2 = 0.0;
+                    for (int i = lane; i < q; i += 32) {
+                        double ti = fma(dd[i] - th2, x[i], 0.0);
+                        if (i > 0) ti = fma(ee[i - 1], x[i - 1], ti);
+                        if (i + 1 < q) ti = fma(ee[i], x[i + 1], ti);
+                        r2 = fma(ti, ti, r2);
+                    }
+                    r2 = wsum(r2);
+                    __syncwarp();
+                    th = th2;
+                    if (r2 <= (1e-12 * tnorm) * (1e-12 * tnorm)) break;   // far below what the caller resolves
+                    solve64(th);
+                    ++extra;
+                    if (!normalise()) break;               // W.V keeps the last accepted vector
+                    th2 = rayleigh();
+                    __syncwarp();
+                    if (th2 < lo_j || th2 > hi_j) break;   // left the interval: rejected
+                    for (int i = lane; i < q; i += 32) W.V[(int64_t)i * k + j] = x[i];
+                    __syncwarp();
+                }
+            }
+            if (lane == 0) {
+                vdiag[j] = ok2 ? 1.0 + extra : 0.0;
+                vdiag[k + j] = th;
+                vdiag[2 * k + j] = W.lam[j];
+            }
             __syncwarp();
         }
     }
@@ -654,7 +746,7 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
                 double s = 0.0;
                 for (int c = 0; c < NC; ++c) s += W.Gpart[(int64_t)c * npairs + p];
                 for (int c = 0; c < NC; ++c) {
-                    double* Gc = cluster.map_shared_rank(G, c);
+                    double* Gc = grows ? Rg + (int64_t)c * rper + goff : cluster.map_shared_rank(G, c);
                     Gc[(int64_t)a * k + b] = s;
                     Gc[(int64_t)b * k + a] = s;
                 }
@@ -791,7 +883,7 @@ static int cluster_size_for(int q) {
 int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q, int k, double* theta, double* W,
                           int* info_host, cudaStream_t st, double drop_tol) {
     if (q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "rayleigh_ritz: need 0 < k <= q");
-    HBSD_TRY(s->rr_ws.alloc((size_t)std::max<int64_t>(rr_cluster_ws_doubles(q, k, 16), (int64_t)4 * q * q + 3 * q + 64)));
+    HBSD_TRY(s->rr_ws.alloc((size_t)std::max<int64_t>(rr_cluster_ws_doubles(q, k, 16, 1), (int64_t)4 * q * q + 3 * q + 64)));
     HBSD_TRY(s->rr_info.alloc(4));
     static const bool trace = std::getenv("HBSD_TRACE") != nullptr || std::getenv("HBSD_RRDBG") != nullptr;
     static thread_local cudaEvent_t tev[4];
@@ -805,18 +897,20 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
     // candidate cluster sizes, preferred first; a size whose shared-memory layout does not fit
     // or that the device cannot co-schedule is skipped
     const int pref = cluster_size_for(q);
-    const int cands[5] = {16, 8, 4, 2, 1};
+    // candidates: shared-memory rows on 16, 8, 4, 2, 1 CTAs, then global rows on 16 CTAs (large q)
+    const int cands[6] = {16, 8, 4, 2, 1, 16};
     bool launched = false;
     int used_nc = 0, used_stage = 0;
-    for (int ci = 0; ci < 5 && !launched; ++ci) {
+    for (int ci = 0; ci < 6 && !launched; ++ci) {
         const int NC = cands[ci];
-        if (NC > pref || NC > q) continue;
+        const int grows = ci == 5 ? 1 : 0;
+        if ((!grows && NC > pref) || NC > q) continue;
         const int rb = (q + NC - 1) / NC;
         const int nwr = std::min((k + NC - 1) / NC, RR_NW);
-        int stage_l = 1, scr_sm = 1;
-        RRLayout L = rr_layout(q, k, rb, nwr, stage_l, scr_sm);
-        if ((size_t)L.total * sizeof(double) > RR_SMEM_MAX) { scr_sm = 0; L = rr_layout(q, k, rb, nwr, stage_l, scr_sm); }
-        if ((size_t)L.total * sizeof(double) > RR_SMEM_MAX) { stage_l = 0; L = rr_layout(q, k, rb, nwr, stage_l, scr_sm); }
+        int stage_l = grows ? 0 : 1, scr_sm = 1;
+        RRLayout L = rr_layout(q, k, rb, nwr, stage_l, scr_sm, grows);
+        if ((size_t)L.total * sizeof(double) > RR_SMEM_MAX) { scr_sm = 0; L = rr_layout(q, k, rb, nwr, stage_l, scr_sm, grows); }
+        if ((size_t)L.total * sizeof(double) > RR_SMEM_MAX) { stage_l = 0; L = rr_layout(q, k, rb, nwr, stage_l, scr_sm, grows); }
         if ((size_t)L.total * sizeof(double) > RR_SMEM_MAX) continue;
         const size_t smem = (size_t)L.total * sizeof(double);
         // attribute and co-scheduling checks are host calls of tens of microseconds: once per
@@ -856,7 +950,7 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
         }
         if (ok_cache[NC] < 0) continue;
         cudaError_t le = cudaLaunchKernelEx(&cfg, k_rr_cluster, HR, SR, q, k, theta, W, s->rr_ws.p, s->rr_info.p,
-                                            drop_tol, stage_l, scr_sm);
+                                            drop_tol, stage_l, scr_sm, grows);
         if (le != cudaSuccess) return fail(HBSD_ERR_CUDA, std::string("rayleigh_ritz launch: ") + cudaGetErrorString(le));
         count_launch(s);
         if (trace) cudaEventRecord(tev[1], st);
@@ -867,6 +961,18 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
     if (!launched) return rayleigh_ritz(s, HR, SR, q, k, theta, W, info_host, st);
     int info[4] = {0, 0, 0, 0};
     HBSD_CUDA(cudaMemcpyAsync(info, s->rr_info.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    {
+        static const char* dbg = std::getenv("HBSD_RRDBG");
+        if (dbg && dbg[0] == '2') {
+            std::vector<double> vd(3 * (size_t)k);
+            HBSD_CUDA(cudaMemcpyAsync(vd.data(), s->rr_ws.p + rr_cluster_ws_doubles(q, k, 16, 1) - 3 * k,
+                                      3 * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+            HBSD_CUDA(cudaStreamSynchronize(st));
+            for (int j = 0; j < k; ++j)
+                std::fprintf(stderr, "[hbsd]   RR vec %d solves-after-first %d theta %.12e coarse %.12e\n", j, (int)vd[j],
+                             vd[k + j], vd[2 * k + j]);
+        }
+    }
     if (trace) cudaEventRecord(tev[2], st);
     HBSD_CUDA(cudaStreamSynchronize(st));
     if (trace) {
