@@ -29,6 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 TOL = 1e-8
+# DRAM bytes (read + write) per column product of the fused MINRES kernel, from one ncu capture of a
+# 57-column, 99-step launch on this workload (profiles/k_minres_medium.md); the roofline's traffic
+# scales it by the column products of the average launch of the timed solve
+MINRES_DRAM_BYTES_PER_COLUMN_PRODUCT = (1212.506368e6 + 438.241536e6) / 156
 WORKLOAD = "32^3 periodic Q1 elements, 8 atoms Z=4, 4 Gaussian enrichment dofs/node within r_c=0.15, nev=64, tol=1e-8"
 WORKLOAD_NL = WORKLOAD + ", nonlocal F G F^T with s+p projectors per atom (k=32, r_p=0.2)"
 
@@ -271,8 +275,13 @@ def main():
     dom = max(classes, key=lambda k: classes[k][0])
     t_ms, flops, _, what = classes[dom]
     achieved = flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+    traffic = None
+    if dom == "minres" and st["local_calls"] > 0 and args.workload == "medium":
+        traffic = MINRES_DRAM_BYTES_PER_COLUMN_PRODUCT * st["minres_spmm_cols"] / st["local_calls"]
     roof = {"bound": "alu", "achieved": achieved, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / (peak64 / 1e12) if peak64 > 0 else None, "traffic": None,
+            "frac": achieved / (peak64 / 1e12) if peak64 > 0 else None, "traffic": traffic,
+            "traffic_note": "DRAM bytes per launch: ncu bytes per column product x the average launch's column products"
+            if traffic is not None else None,
             "kernel": dom, "what": what, "peak_source": "FP64 FMA probe (hbsd_probe_peak) measured in this run",
             "step_ms": {k: st[f"t_{k}_ms"] for k in ("matvec", "resid", "precond", "local", "gram", "rr", "update")}}
 
