@@ -129,6 +129,8 @@ typedef struct {
     int64_t matvec_cols;     /* columns through steps 3 and 7                              */
     int64_t minres_spmm_cols;/* columns through the shifted SpMM of step 6(b)              */
     int precond_calls;       /* applications of step 6(a)                                   */
+    int64_t local_calls;     /* launches of step 6(b) (one fused kernel per iteration with
+                                localized columns)                                          */
     int64_t neg_pivots;      /* negative pivots of the LDL^T factor of H_loc - eps_bar S: the
                                 number of eigenvalues of the local pencil below eps_bar
                                 (Sylvester's inertia; 0 when eps_bar lies below the spectrum) */

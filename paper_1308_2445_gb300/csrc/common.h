@@ -280,7 +280,6 @@ struct Session {
     DBuf<int> rr_info;
     // MINRES workspace (minres.cu)
     DBuf<double> mr_d;
-    DBuf<float> mr_f;
     DBuf<double> mr_red;        // per-block partial sums of the fused MINRES kernel
     DBuf<int> mr_any, mr_steps; // grid barrier + error flag; per-column step counts
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing

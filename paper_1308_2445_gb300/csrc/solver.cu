@@ -357,6 +357,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             tm.end(ti, st);
             stt.minres_steps += msteps;
             stt.local_cols += a;
+            stt.local_calls += 1;
         }
         if (fp32_dirs && a == 0) {   // P = D P^ (no refinement this iteration)
             k_convert_block<float, T><<<grid_for(n * p), 256, 0, st>>>(S->p32.p, ldp, p, n, B.P.p, ldp,
@@ -471,6 +472,7 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     stt.minres_steps = stt.precond_cols = stt.local_cols = 0;
     stt.rr_fallbacks = 0;
     stt.matvec_cols = stt.minres_spmm_cols = 0;
+    stt.local_calls = 0;
     stt.precond_calls = 0;
     StepTimer tm;
     std::vector<double> E(w), Eprev;
