@@ -378,6 +378,14 @@ int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out
  * Synchronous. */
 int hbsd_probe_peak(int which, void* stream, double* flops_per_s);
 
+/* Failure path of the device-side waits (no counterpart in the paper): launches the bounded grid
+ * barrier of the fused MINRES kernel on two blocks that wait for a third arrival that never
+ * comes, with a wait limit of limit_s seconds (clamped to [1 ms, 5 s]).  Both blocks give up,
+ * raise the error flag and return, and the call returns HBSD_ERR_TIMEOUT -- the status a solve
+ * reports when a MINRES barrier times out; the CUDA context stays usable.  Any other outcome
+ * returns HBSD_ERR_CUDA.  Synchronous. */
+int hbsd_probe_barrier_timeout(double limit_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

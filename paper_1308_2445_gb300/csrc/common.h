@@ -310,6 +310,7 @@ int nl_apply_add(Session* s, const T* X, int64_t ldx, int w, T* Y, int64_t ldy, 
 template <class T>   // SMW step 6 on P = -K R (T = float: scaled P^ of the mixed form)
 int nl_smw_correct(Session* s, T* P, int64_t ldp, int p, cudaStream_t st);
 int nl_minres_index(Session* s, int grid, const std::vector<int64_t>& blk, int64_t kp);
+int barrier_timeout_probe(double limit_s, cudaStream_t st);
 
 // ---- small utilities -----------------------------------------------------------------
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }

@@ -57,7 +57,8 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
 
 // bar[0]: arrivals, bar[1]: generation.  Returns false (for the whole block) when the wait
 // timed out here or another block has raised the error flag.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* err, int* ok_sm) {
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* err, int* ok_sm,
+                             uint64_t wait_ns = MR_WAIT_NS) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -71,7 +72,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int
             const uint64_t t0 = gtimer();
             while (ld_acquire(&bar[1]) == gen) {
                 if (ld_relaxed(err)) { ok = 0; break; }
-                if (gtimer() - t0 > MR_WAIT_NS) { atomicExch(err, 1); ok = 0; break; }
+                if (gtimer() - t0 > wait_ns) { atomicExch(err, 1); ok = 0; break; }
                 __nanosleep(64);
             }
         }
@@ -81,6 +82,16 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int
     }
     __syncthreads();
     return *ok_sm != 0;
+}
+
+// Failure path of the grid barrier: the blocks of this launch wait for one more arrival than
+// there are blocks, so the wait can only end by its time limit; each block then raises the error
+// flag and returns (err[1] counts the blocks that returned).
+__global__ void k_barrier_probe(unsigned* bar, int* err, uint64_t wait_ns) {
+    __shared__ int ok_sm;
+    unsigned gen = 0;
+    const bool ok = grid_barrier(bar, gridDim.x + 1, gen, err, &ok_sm, wait_ns);
+    if (!ok && threadIdx.x == 0) atomicAdd(err + 1, 1);
 }
 
 struct MrArgs {
@@ -782,6 +793,22 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_onestep(MrArgs a) {
 }
 
 }  // namespace
+
+// Runs k_barrier_probe on two blocks with a wait limit of limit_s seconds: HBSD_ERR_TIMEOUT when
+// both blocks gave up and returned (the expected outcome), HBSD_ERR_CUDA otherwise.
+int barrier_timeout_probe(double limit_s, cudaStream_t st) {
+    DBuf<int> w;
+    HBSD_TRY(w.alloc(4));
+    HBSD_CUDA(cudaMemsetAsync(w.p, 0, 4 * sizeof(int), st));
+    const uint64_t ns = (uint64_t)(std::max(0.001, std::min(limit_s, 5.0)) * 1e9);
+    k_barrier_probe<<<2, 64, 0, st>>>(reinterpret_cast<unsigned*>(w.p), w.p + 2, ns);
+    HBSD_CUDA(cudaPeekAtLastError());
+    int h[4] = {0, 0, 0, 0};
+    HBSD_CUDA(cudaMemcpyAsync(h, w.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    HBSD_CUDA(cudaStreamSynchronize(st));
+    if (h[2] == 1 && h[3] == 2) return fail(HBSD_ERR_TIMEOUT, "barrier probe: the wait ran out as expected");
+    return fail(HBSD_ERR_CUDA, "barrier probe: unexpected outcome");
+}
 
 template <class T> static DBuf<T>& mr_vecs(Session* s);
 template <> DBuf<double>& mr_vecs<double>(Session* s) { return s->mr_d; }

@@ -706,6 +706,10 @@ int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm, 
     return rc;
 }
 
+int hbsd_probe_barrier_timeout(double limit_s, void* stream) {
+    return barrier_timeout_probe(limit_s, (cudaStream_t)stream);
+}
+
 int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out) {
     if (!out || count < 0) return fail(HBSD_ERR_ARG, "bad arguments");
     seed_normals(seed, stream, count, out);

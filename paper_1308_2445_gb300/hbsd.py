@@ -94,6 +94,7 @@ _SIGS = {
     "hbsd_update_H": (C.c_int, [_P, _D]),
     "hbsd_set_nonlocal": (C.c_int, [_P, C.c_int, _D, C.c_int64, _D]),
     "hbsd_res_history": (C.c_int, [_P, _D, C.c_int]),
+    "hbsd_probe_barrier_timeout": (C.c_int, [C.c_double, _P]),
     "hbsd_onestep": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, C.c_double, C.c_int, _P, C.c_int64, _P]),
     "hbsd_solve": (C.c_int, [_P, C.c_int, C.c_double, _D, C.c_int, _D, _D, C.POINTER(C.c_int),
                              C.POINTER(hbsd_stats)]),

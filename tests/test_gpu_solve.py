@@ -280,3 +280,18 @@ def test_full_size_mixed_against_fp64_with_inertia_check():
                       sigma0=p.eps_bar)
     assert si.stats()["neg_pivots"] == i + 1
     si.close()
+
+
+def test_device_wait_times_out_and_the_context_survives():
+    # the bounded grid barrier of MINRES, made to wait for an arrival that never comes: it gives
+    # up after its limit and the library reports HBSD_ERR_TIMEOUT; a solve then runs normally
+    import time
+    t0 = time.perf_counter()
+    rc = hb().lib().hbsd_probe_barrier_timeout(0.2, None)
+    dt = time.perf_counter() - t0
+    assert rc == hb().HBSD_ERR_TIMEOUT
+    assert 0.15 <= dt <= 5.0
+    p = pi.small_case(1)
+    s = hb().Session.from_problem(p)
+    lam, X, it, rc2, st = s.solve(16, 1e-8, X0=pi.seed_normal_block(1, p.n, 19))
+    assert rc2 == 0
