@@ -110,22 +110,38 @@ __global__ void __launch_bounds__(256) k_gram_df64(Seg2d Z, Seg2d ZH, Seg2d ZS, 
 }
 
 // Sum the chunks in order; entry (a, b), a <= b, of Z^T X Z is used for both (a, b) and (b, a).
-__global__ void k_gram_final_upper(const double* __restrict__ partial, int nchunks, int q, double* __restrict__ HR,
-                                   double* __restrict__ SR) {
+__global__ void __launch_bounds__(256) k_gram_final_upper(const double* __restrict__ partial, int nchunks, int q,
+                                                          double* __restrict__ HR, double* __restrict__ SR) {
+    // 32 entries per block (lanes), the chunks split over the 8 warps, then summed in warp order:
+    // the order is fixed, so the result is deterministic.  Entries a <= b are summed and mirrored.
+    __shared__ double rh[8][33], rs[8][33];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int64_t qq = (int64_t)q * q;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= qq) return;
-    int a = (int)(idx / q), b = (int)(idx % q);
-    if (a > b) { const int t = a; a = b; b = t; }
-    const int64_t src = (int64_t)a * q + b;
-    double h = 0, s = 0;
-    for (int c = 0; c < nchunks; ++c) {
-        const double* ph = partial + (int64_t)c * 2 * qq;
-        h += ph[src];
-        s += ph[qq + src];
+    const int64_t idx = (int64_t)blockIdx.x * 32 + lane;
+    const int a = (int)(idx / q), b = (int)(idx - (int64_t)(idx / q) * q);
+    const bool on = idx < qq && a <= b;
+    double h = 0.0, sv = 0.0;
+    if (on)
+        for (int c = g; c < nchunks; c += 8) {
+            const double* ph = partial + (int64_t)c * 2 * qq;
+            h += ph[idx];
+            sv += ph[qq + idx];
+        }
+    rh[g][lane] = h;
+    rs[g][lane] = sv;
+    __syncthreads();
+    if (g == 0 && on) {
+        double H = 0.0, S = 0.0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            H += rh[t][lane];
+            S += rs[t][lane];
+        }
+        HR[idx] = H;
+        SR[idx] = S;
+        HR[(int64_t)b * q + a] = H;
+        SR[(int64_t)b * q + a] = S;
     }
-    HR[idx] = h;
-    SR[idx] = s;
 }
 
 // W (q x k, FP64) -> pairs
@@ -268,7 +284,7 @@ int gram2_df64(Session* s, const double* Z0, int64_t ld0, int q0, const double* 
     k_gram_df64<<<dim3(ntile, nch), 256, 0, st>>>(Z, ZH, ZS, q, n, rpc, s->ws.p);
     HBSD_LAUNCHED(s);
     const int64_t qq = (int64_t)q * q;
-    k_gram_final_upper<<<ceil_div(qq, 256), 256, 0, st>>>(s->ws.p, nch, q, HR, SR);
+    k_gram_final_upper<<<ceil_div(qq, 32), 256, 0, st>>>(s->ws.p, nch, q, HR, SR);
     HBSD_LAUNCHED(s);
     return 0;
 }
