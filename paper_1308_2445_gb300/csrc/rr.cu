@@ -941,7 +941,7 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if (ok_smem[NC] == 0 || smem > ok_smem[NC]) {   // co-scheduling verdict for this size
+        if (ok_smem[NC] == 0 || smem > ok_smem[NC]) {   // co-scheduling check for this size
             int nclusters = 0;
             cudaError_t oe = cudaOccupancyMaxActiveClusters(&nclusters, k_rr_cluster, &cfg);
             if (oe != cudaSuccess) (void)cudaGetLastError();

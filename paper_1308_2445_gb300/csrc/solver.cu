@@ -26,7 +26,7 @@ void count_launch(Session* s) {
     if (s) s->launches++;
 }
 
-// ---- small kernels of the driver ---------------------------------------------------------
+// ---- small kernels of the outer loop -----------------------------------------------------
 namespace {
 
 inline int grid_for(int64_t work) {
