@@ -295,3 +295,25 @@ def test_device_wait_times_out_and_the_context_survives():
     s = hb().Session.from_problem(p)
     lam, X, it, rc2, st = s.solve(16, 1e-8, X0=pi.seed_normal_block(1, p.n, 19))
     assert rc2 == 0
+
+
+def test_argument_edges():
+    # empty and out-of-range requests are refused with HBSD_ERR_ARG; empty step calls are no-ops
+    p = pi.small_case(1)
+    s = hb().Session.from_problem(p)
+    for nev in (0, p.n):                       # nev + m0 must lie in [1, n]
+        with pytest.raises(hb().HbsdError) as e:
+            s.solve(nev, 1e-8)
+        assert e.value.code == hb().HBSD_ERR_ARG
+    with pytest.raises(hb().HbsdError) as e:   # a warm start needs a previous solve of this session
+        s.solve(16, 1e-8, warm=True)
+    assert e.value.code == hb().HBSD_ERR_ARG
+    # k = 0 with valid pointers writes nothing; a NULL block is refused whatever k is
+    X = torch.ones(p.n, 2, dtype=torch.float64, device="cuda")
+    Y = torch.full((p.n, 2), 7.0, dtype=torch.float64, device="cuda")
+    assert hb().lib().hbsd_spmm_pair(s.h, hb().ptr(X), 2, 0, hb().ptr(Y), 2, hb().ptr(Y), 2) == 0
+    torch.cuda.synchronize()
+    assert bool((Y == 7.0).all())
+    assert hb().lib().hbsd_spmm_pair(s.h, None, 2, 0, hb().ptr(Y), 2, hb().ptr(Y), 2) == hb().HBSD_ERR_ARG
+    lam, Xv, it, rc, st = s.solve(1, 1e-8, X0=pi.seed_normal_block(5, p.n, 4))   # the smallest block
+    assert rc == 0 and lam.shape == (1,)
