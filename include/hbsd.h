@@ -356,8 +356,8 @@ void hbsd_server_destroy(hbsd_server* sv);
  * term, TwoProd / TwoSum), the Gram sums accumulated in FP64 across 128-row tiles.  hbsd_gram_df64
  * computes the entries a <= b of Z^T ZH and Z^T ZS and mirrors them (no averaging).  Arguments,
  * layouts and errors as hbsd_gram / hbsd_update; FP64 values enter the products with ~47 bits
- * above 2^-96 in magnitude, at least 24 bits down to 2^-126, and as zero below; q * (k + 8 * max(1, min(256 / min(k, 256), 8))) pairs must fit in 220 KB of
- * shared memory for hbsd_update_df64 (HBSD_ERR_ARG otherwise). */
+ * above 2^-96 in magnitude, at least 24 bits down to 2^-126, and as zero below.  hbsd_update_df64
+ * takes q <= 3520 (8 rows of q pairs staged in 220 KB of shared memory; HBSD_ERR_ARG otherwise). */
 int hbsd_gram_df64(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
                    int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream);
 int hbsd_update_df64(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream);

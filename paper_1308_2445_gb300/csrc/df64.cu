@@ -150,20 +150,22 @@ __global__ void k_split_w(const double* __restrict__ W, int64_t cnt, float2* __r
         W2[t] = split_d(W[t]);
 }
 
-// Z0(:, 0:k) <- [Z0 Z1] W.  Threads are flattened over (row group, column): kc = min(kw, 256)
-// columns per pass, ng = min(256 / kc, 8) row groups of UR rows, so a CTA covers ng * UR rows.
-// The rows (split) are staged in shared memory once; W (q x k pairs) in column tiles of kw
-// (all of W when it fits), so any q whose rows fit can be updated in place.
+// Z0(:, 0:k) <- [Z0 Z1] W.  Threads are flattened over (row group, column): kc = min(k, 256)
+// columns per pass, ng = min(256 / kc, 8) row groups of UR rows, so a CTA covers ng * UR rows;
+// the rows (split) and W (q x k pairs) are staged in shared memory, W shared by the row groups.
+// Every output sums its q terms in column order, the running pair renormalised after each
+// term whose index is 7 mod 8 (the loops run in blocks of RN = 8 terms and a short tail).
 constexpr int UR = 8;
+constexpr int RN = 8;
 
 __global__ void __launch_bounds__(256) k_update_df64(double* __restrict__ Z0, int64_t ld0, int q0,
                                                      const double* __restrict__ Z1, int64_t ld1, int q1, int64_t n,
-                                                     const float2* __restrict__ W2, int k, int ng, int kw) {
+                                                     const float2* __restrict__ W2, int k, int ng) {
     extern __shared__ __align__(16) float2 smu[];
     const int q = q0 + q1;
     const int rows = ng * UR;
     float2* zrow = smu;                      // [rows][q]
-    float2* wsm = smu + (int64_t)rows * q;   // [q][kw]
+    float2* wsm = smu + (int64_t)rows * q;   // [q][k]
     const int64_t i0 = (int64_t)blockIdx.x * rows;
     for (int t = threadIdx.x; t < rows * q; t += 256) {
         const int rr = t / q, c = t % q;
@@ -172,96 +174,94 @@ __global__ void __launch_bounds__(256) k_update_df64(double* __restrict__ Z0, in
         if (i < n) v = c < q0 ? Z0[i * ld0 + c] : Z1[i * ld1 + (c - q0)];
         zrow[t] = split_d(v);
     }
-    for (int jw = 0; jw < k; jw += kw) {
-        const int kwc = min(kw, k - jw);
-        __syncthreads();   // the rows are staged / the previous tile's readers are done
-        for (int t = threadIdx.x; t < q * kwc; t += 256) {
-            const int c = t / kwc, j = t - c * kwc;
-            wsm[t] = W2[(int64_t)c * k + jw + j];
+    for (int t = threadIdx.x; t < q * k; t += 256) wsm[t] = W2[t];
+    __syncthreads();
+    const int kc = min(k, 256);
+    const int g = threadIdx.x / kc, cl = threadIdx.x % kc;
+    if (g >= ng) return;
+    const float2* zr = zrow + (int64_t)g * UR * q;
+    for (int jb = 0; jb < k; jb += kc) {
+        const int j = jb + cl;
+        if (j >= k) continue;
+        float ah[UR], al[UR];
+#pragma unroll
+        for (int u = 0; u < UR; ++u) { ah[u] = 0.f; al[u] = 0.f; }
+        const float2* wc = wsm + j;
+        int c = 0;
+        for (; c + RN <= q; c += RN) {
+#pragma unroll
+            for (int cc = 0; cc < RN; ++cc) {
+                const float2 wv = wc[(c + cc) * k];
+#pragma unroll
+                for (int u = 0; u < UR; ++u) dfma(zr[u * q + c + cc], wv, ah[u], al[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < UR; ++u) renorm(ah[u], al[u]);
         }
-        __syncthreads();
-        const int kc = min(kwc, 256);
-        const int g = threadIdx.x / kc, cl = threadIdx.x % kc;
-        if (g >= ng) continue;
-        for (int jb = 0; jb < kwc; jb += kc) {
-            const int j = jb + cl;
-            if (j >= kwc) continue;
-            float ah[UR], al[UR];
+        for (; c < q; ++c) {
+            const float2 wv = wc[c * k];
 #pragma unroll
-            for (int u = 0; u < UR; ++u) { ah[u] = 0.f; al[u] = 0.f; }
-            const float2* zr = zrow + (int64_t)g * UR * q;
-            for (int c = 0; c < q; ++c) {
-                const float2 wv = wsm[c * kwc + j];
+            for (int u = 0; u < UR; ++u) dfma(zr[u * q + c], wv, ah[u], al[u]);
+        }
 #pragma unroll
-                for (int u = 0; u < UR; ++u) dfma(zr[u * q + c], wv, ah[u], al[u]);
-                if ((c & 7) == 7) {
-#pragma unroll
-                    for (int u = 0; u < UR; ++u) renorm(ah[u], al[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < UR; ++u) {
-                const int64_t i = i0 + g * UR + u;
-                if (i < n) Z0[i * ld0 + jw + j] = to_d(ah[u], al[u]);
-            }
+        for (int u = 0; u < UR; ++u) {
+            const int64_t i = i0 + g * UR + u;
+            if (i < n) Z0[i * ld0 + j] = to_d(ah[u], al[u]);
         }
     }
 }
 
-// The same product for q too large to stage W whole: UR rows per CTA staged once (split), W
-// streamed through shared memory in tiles of UR_KT rows x 256 columns (a K-tiled product), one
-// output column per thread, outputs written after each pass over the columns (in place: the
-// later passes read the staged rows, never Z0).  Renormalisation every 8 terms of the global
-// column index, as above.
-constexpr int UR_KT = 64;
-
-__global__ void __launch_bounds__(256) k_update_df64_kt(double* __restrict__ Z0, int64_t ld0, int q0,
+// The same product for q too large to stage W with the rows: UR rows per CTA staged once
+// (split), one output column per thread (blockDim.x columns per pass, a multiple of 32 chosen so
+// the passes are even), each thread reading its own column of W straight from L2, RN terms at a
+// time (no other thread of the CTA reads it, so staging it would buy nothing).  Same term order
+// and renormalisation as above.  In place: the outputs are written only after every row of the
+// CTA was staged, and only the staged copy is read.
+__global__ void __launch_bounds__(512) k_update_df64_kt(double* __restrict__ Z0, int64_t ld0, int q0,
                                                         const double* __restrict__ Z1, int64_t ld1, int q1, int64_t n,
                                                         const float2* __restrict__ W2, int k) {
     extern __shared__ __align__(16) float2 smu[];
     const int q = q0 + q1;
+    const int nt = blockDim.x;
     float2* zrow = smu;                     // [UR][q]
-    float2* wt = smu + (int64_t)UR * q;     // [UR_KT][256]
     const int64_t i0 = (int64_t)blockIdx.x * UR;
-    for (int t = threadIdx.x; t < UR * q; t += 256) {
+    for (int t = threadIdx.x; t < UR * q; t += nt) {
         const int rr = t / q, c = t % q;
         const int64_t i = i0 + rr;
         double v = 0.0;
         if (i < n) v = c < q0 ? Z0[i * ld0 + c] : Z1[i * ld1 + (c - q0)];
         zrow[t] = split_d(v);
     }
-    for (int jb = 0; jb < k; jb += 256) {
-        const int kc = min(256, k - jb);
-        const bool on = (int)threadIdx.x < kc;
+    __syncthreads();
+    for (int jb = 0; jb < k; jb += nt) {
+        const int j = jb + threadIdx.x;
+        if (j >= k) break;   // no barrier follows
         float ah[UR], al[UR];
 #pragma unroll
         for (int u = 0; u < UR; ++u) { ah[u] = 0.f; al[u] = 0.f; }
-        for (int c0 = 0; c0 < q; c0 += UR_KT) {
-            const int cn = min(UR_KT, q - c0);
-            __syncthreads();   // rows staged / previous tile consumed
-            for (int t = threadIdx.x; t < cn * 256; t += 256) {
-                const int c = t >> 8, j = t & 255;
-                if (j < kc) wt[t] = W2[(int64_t)(c0 + c) * k + jb + j];
-            }
-            __syncthreads();
-            if (on) {
-                for (int c = 0; c < cn; ++c) {
-                    const float2 wv = wt[c * 256 + threadIdx.x];
+        const float2* wc = W2 + j;
+        int c = 0;
+        for (; c + RN <= q; c += RN) {
+            float2 wv[RN];
 #pragma unroll
-                    for (int u = 0; u < UR; ++u) dfma(zrow[u * q + c0 + c], wv, ah[u], al[u]);
-                    if (((c0 + c) & 7) == 7) {
+            for (int cc = 0; cc < RN; ++cc) wv[cc] = __ldg(wc + (int64_t)(c + cc) * k);
 #pragma unroll
-                        for (int u = 0; u < UR; ++u) renorm(ah[u], al[u]);
-                    }
-                }
+            for (int cc = 0; cc < RN; ++cc) {
+#pragma unroll
+                for (int u = 0; u < UR; ++u) dfma(zrow[u * q + c + cc], wv[cc], ah[u], al[u]);
             }
+#pragma unroll
+            for (int u = 0; u < UR; ++u) renorm(ah[u], al[u]);
         }
-        if (on) {
+        for (; c < q; ++c) {
+            const float2 wv = __ldg(wc + (int64_t)c * k);
 #pragma unroll
-            for (int u = 0; u < UR; ++u) {
-                const int64_t i = i0 + u;
-                if (i < n) Z0[i * ld0 + jb + threadIdx.x] = to_d(ah[u], al[u]);
-            }
+            for (int u = 0; u < UR; ++u) dfma(zrow[u * q + c], wv, ah[u], al[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UR; ++u) {
+            const int64_t i = i0 + u;
+            if (i < n) Z0[i * ld0 + j] = to_d(ah[u], al[u]);
         }
     }
 }
@@ -293,14 +293,17 @@ int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, 
                  const double* W, int k, cudaStream_t st, bool split_w) {
     const int q = q0 + q1;
     if (k > q0) return fail(HBSD_ERR_ARG, "update: k must not exceed the first segment width");
-    // W staged whole when it fits with the rows (kernel k_update_df64), else streamed in K-tiles
-    // (k_update_df64_kt)
+    // W staged whole when it fits with the rows (kernel k_update_df64), else read by each
+    // thread from L2 (k_update_df64_kt: passes of nt <= 512 columns, as even as multiples of 32
+    // allow, one pass for k <= 512)
     const int kc0 = std::min(k, 256);
     const int ng = std::max(1, std::min(256 / kc0, 8));
     const int rows = ng * UR;
     const size_t smem_whole = ((size_t)rows * q + (size_t)q * k) * sizeof(float2);
     const bool whole = smem_whole <= 220 * 1024;
-    const size_t smem = whole ? smem_whole : ((size_t)UR * q + (size_t)UR_KT * 256) * sizeof(float2);
+    const int npass = ceil_div(k, 512);
+    const int nt = (int)round_up(ceil_div(k, npass), 32);
+    const size_t smem = whole ? smem_whole : (size_t)UR * q * sizeof(float2);
     if (smem > 220 * 1024) return fail(HBSD_ERR_ARG, "update: q too large for the double-float kernel");
     {
         static std::mutex attr_mu;
@@ -318,8 +321,8 @@ int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, 
         k_split_w<<<ceil_div(cnt, 256), 256, 0, st>>>(W, cnt, s->df_w.p);
         HBSD_LAUNCHED(s);
     }
-    if (whole) k_update_df64<<<ceil_div(n, rows), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, s->df_w.p, k, ng, k);
-    else k_update_df64_kt<<<ceil_div(n, UR), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, s->df_w.p, k);
+    if (whole) k_update_df64<<<ceil_div(n, rows), 256, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, s->df_w.p, k, ng);
+    else k_update_df64_kt<<<ceil_div(n, UR), nt, smem, st>>>(Z0, ld0, q0, Z1, ld1, q1, n, s->df_w.p, k);
     HBSD_LAUNCHED(s);
     return 0;
 }

@@ -265,7 +265,8 @@ def test_gram_df64(q, n):
 
 
 @pytest.mark.parametrize("q,k,n", [(19, 19, 646), (35, 19, 1000), (135, 71, 3001), (8, 3, 5), (282, 30, 700),
-                                   (300, 282, 1001), (538, 282, 777)])   # the last two tile W
+                                   (300, 282, 1001), (538, 282, 777), (600, 520, 301)])
+# the last three read W per thread (q too large to stage it with the rows); the last in two passes
 def test_update_df64(q, k, n):
     Z = pi.seed_normal_block(q * 3, n, q) * np.logspace(-4, 4, q)
     W = pi.seed_normal_block(q * 5, q, k)
