@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -14,6 +16,26 @@ namespace hbsd {
 // ---- errors -------------------------------------------------------------------------
 void set_error(const std::string& msg);
 int fail(int code, const std::string& msg);
+
+// Runs the body of a C entry point so that no exception crosses the ABI: std::bad_alloc becomes
+// HBSD_ERR_OOM (with a message short enough to need no allocation), any other exception
+// HBSD_ERR_ARG.
+template <class F>
+int guarded(F&& body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc&) {
+        return fail(HBSD_ERR_OOM, "no host memory");
+    } catch (const std::exception& e) {
+        try {
+            return fail(HBSD_ERR_ARG, std::string("host exception: ") + e.what());
+        } catch (...) {
+            return HBSD_ERR_ARG;
+        }
+    } catch (...) {
+        return fail(HBSD_ERR_ARG, "host exception");
+    }
+}
 
 #define HBSD_CUDA(call)                                                                  \
     do {                                                                                 \

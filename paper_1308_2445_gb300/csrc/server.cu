@@ -245,10 +245,25 @@ void worker(hbsd_server* sv) {
             ++sv->running;
         }
         bury(sv);
-        run_request(sv, *rq);
+        const int rc = guarded([&]() -> int {
+            run_request(sv, *rq);
+            return HBSD_OK;
+        });
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             --sv->running;
+            if (rc < 0) {   // a host exception before the result was recorded: record the failure
+                auto s = sv->sessions.find(rq->session_id);
+                if (s != sv->sessions.end()) s->second.busy = false;
+                auto it = sv->results.find(rq->ticket);
+                if (it != sv->results.end() && !it->second.done) {
+                    it->second.r = hbsd_result{};
+                    it->second.r.ticket = rq->ticket;
+                    it->second.r.status = rc;
+                    it->second.r.session_id = -1;
+                    it->second.done = true;
+                }
+            }
         }
         sv->cv.notify_all();
     }
@@ -269,118 +284,137 @@ void hbsd_server_opts_default(hbsd_server_opts* o) {
 }
 
 int hbsd_server_create(const hbsd_server_opts* opts, hbsd_server** out) {
-    if (!out) return fail(HBSD_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    hbsd_server_opts o;
-    hbsd_server_opts_default(&o);
-    if (opts) o = *opts;
-    if (o.max_slots < 1 || o.max_slots > 64) return fail(HBSD_ERR_ARG, "max_slots must lie in [1, 64]");
-    if (o.hbm_budget_bytes == 0) {
-        size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(HBSD_ERR_CUDA, "cudaMemGetInfo failed");
-        o.hbm_budget_bytes = fr / 10 * 8;
-    }
-    hbsd_server* sv = new hbsd_server();
-    sv->opts = o;
-    for (int i = 0; i < o.max_slots; ++i) sv->workers.emplace_back(worker, sv);
-    *out = sv;
-    return HBSD_OK;
+    return guarded([&]() -> int {
+        if (!out) return fail(HBSD_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        hbsd_server_opts o;
+        hbsd_server_opts_default(&o);
+        if (opts) o = *opts;
+        if (o.max_slots < 1 || o.max_slots > 64) return fail(HBSD_ERR_ARG, "max_slots must lie in [1, 64]");
+        if (o.hbm_budget_bytes == 0) {
+            size_t fr = 0, tot = 0;
+            if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return fail(HBSD_ERR_CUDA, "cudaMemGetInfo failed");
+            o.hbm_budget_bytes = fr / 10 * 8;
+        }
+        hbsd_server* sv = new hbsd_server();
+        sv->opts = o;
+        try {
+            for (int i = 0; i < o.max_slots; ++i) sv->workers.emplace_back(worker, sv);
+        } catch (...) {   // a thread could not start: stop and join the ones that did
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                sv->stop = true;
+            }
+            sv->cv.notify_all();
+            for (auto& t : sv->workers) t.join();
+            delete sv;
+            throw;
+        }
+        *out = sv;
+        return HBSD_OK;
+    });
 }
 
 int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, double* X_out, uint64_t* ticket) {
-    if (!sv || !rq || !lambda_out || !ticket) return fail(HBSD_ERR_ARG, "NULL argument");
-    if (rq->nev < 1 || !(rq->tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
-    auto r = std::make_unique<Request>();
-    r->nev = rq->nev;
-    r->tol = rq->tol;
-    r->lam_out = lambda_out;
-    r->X_out = X_out;
-    r->warm = rq->warm;
-    int64_t n = 0;
-    if (rq->session_id < 0) {   // new problem: H, S, local blocks and options copied here
-        if (!rq->H || !rq->S || !rq->lb || !rq->opt) return fail(HBSD_ERR_ARG, "a new problem needs H, S, lb, opt");
-        if (rq->H->n <= 0 || rq->H->n != rq->S->n || rq->H->nnz != rq->S->nnz || rq->H->is_complex || rq->S->is_complex)
-            return fail(HBSD_ERR_ARG, "H and S must be real with the same n and nnz");
-        if (!rq->lb->dof_node || !rq->H->row_ptr || !rq->H->col_idx || !rq->H->val || !rq->S->val)
-            return fail(HBSD_ERR_ARG, "NULL array in the problem");
-        if (rq->warm) return fail(HBSD_ERR_ARG, "a new problem cannot warm-start");
-        n = rq->H->n;
-        r->is_new = true;
-        r->n = n;
-        r->nnz = rq->H->nnz;
-        r->row_ptr.assign(rq->H->row_ptr, rq->H->row_ptr + n + 1);
-        r->col_idx.assign(rq->H->col_idx, rq->H->col_idx + r->nnz);
-        r->hval.assign(rq->H->val, rq->H->val + r->nnz);
-        r->sval.assign(rq->S->val, rq->S->val + r->nnz);
-        r->dof_node.assign(rq->lb->dof_node, rq->lb->dof_node + n);
-        if (rq->lb->dof_cluster) r->dof_cluster.assign(rq->lb->dof_cluster, rq->lb->dof_cluster + n);
-        std::memcpy(r->grid, rq->lb->grid, sizeof(r->grid));
-        r->opt = *rq->opt;
-        if (rq->nl_k < 0 || (rq->nl_k > 0 && (!rq->nl_F || !rq->nl_G || rq->nl_ldf < rq->nl_k)))
-            return fail(HBSD_ERR_ARG, "nonlocal term: nl_F, nl_G required and nl_ldf >= nl_k");
-        if (rq->nl_k > 0) {
-            r->nl_k = rq->nl_k;
-            r->nl_F.resize((size_t)n * rq->nl_k);
-            for (int64_t i = 0; i < n; ++i)
-                std::memcpy(r->nl_F.data() + i * rq->nl_k, rq->nl_F + i * rq->nl_ldf, rq->nl_k * sizeof(double));
-            r->nl_G.assign(rq->nl_G, rq->nl_G + (size_t)rq->nl_k * rq->nl_k);
+    return guarded([&]() -> int {
+        if (!sv || !rq || !lambda_out || !ticket) return fail(HBSD_ERR_ARG, "NULL argument");
+        if (rq->nev < 1 || !(rq->tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
+        auto r = std::make_unique<Request>();
+        r->nev = rq->nev;
+        r->tol = rq->tol;
+        r->lam_out = lambda_out;
+        r->X_out = X_out;
+        r->warm = rq->warm;
+        int64_t n = 0;
+        if (rq->session_id < 0) {   // new problem: H, S, local blocks and options copied here
+            if (!rq->H || !rq->S || !rq->lb || !rq->opt) return fail(HBSD_ERR_ARG, "a new problem needs H, S, lb, opt");
+            if (rq->H->n <= 0 || rq->H->n != rq->S->n || rq->H->nnz != rq->S->nnz || rq->H->is_complex || rq->S->is_complex)
+                return fail(HBSD_ERR_ARG, "H and S must be real with the same n and nnz");
+            if (!rq->lb->dof_node || !rq->H->row_ptr || !rq->H->col_idx || !rq->H->val || !rq->S->val)
+                return fail(HBSD_ERR_ARG, "NULL array in the problem");
+            if (rq->warm) return fail(HBSD_ERR_ARG, "a new problem cannot warm-start");
+            n = rq->H->n;
+            r->is_new = true;
+            r->n = n;
+            r->nnz = rq->H->nnz;
+            r->row_ptr.assign(rq->H->row_ptr, rq->H->row_ptr + n + 1);
+            r->col_idx.assign(rq->H->col_idx, rq->H->col_idx + r->nnz);
+            r->hval.assign(rq->H->val, rq->H->val + r->nnz);
+            r->sval.assign(rq->S->val, rq->S->val + r->nnz);
+            r->dof_node.assign(rq->lb->dof_node, rq->lb->dof_node + n);
+            if (rq->lb->dof_cluster) r->dof_cluster.assign(rq->lb->dof_cluster, rq->lb->dof_cluster + n);
+            std::memcpy(r->grid, rq->lb->grid, sizeof(r->grid));
+            r->opt = *rq->opt;
+            if (rq->nl_k < 0 || (rq->nl_k > 0 && (!rq->nl_F || !rq->nl_G || rq->nl_ldf < rq->nl_k)))
+                return fail(HBSD_ERR_ARG, "nonlocal term: nl_F, nl_G required and nl_ldf >= nl_k");
+            if (rq->nl_k > 0) {
+                r->nl_k = rq->nl_k;
+                r->nl_F.resize((size_t)n * rq->nl_k);
+                for (int64_t i = 0; i < n; ++i)
+                    std::memcpy(r->nl_F.data() + i * rq->nl_k, rq->nl_F + i * rq->nl_ldf, rq->nl_k * sizeof(double));
+                r->nl_G.assign(rq->nl_G, rq->nl_G + (size_t)rq->nl_k * rq->nl_k);
+            }
+            r->est_bytes = estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
+            if (r->est_bytes > sv->opts.hbm_budget_bytes) return fail(HBSD_ERR_OOM, "request exceeds the server's memory budget");
+        } else {   // follow-up of a resident session: new H values (optional), warm start or X0
+            std::lock_guard<std::mutex> lk(sv->mu);
+            auto s = sv->sessions.find(rq->session_id);
+            if (s == sv->sessions.end()) return fail(HBSD_ERR_ARG, "unknown or evicted session");
+            const Session& ses = s->second.h->s;
+            n = ses.n;
+            r->session_id = rq->session_id;
+            if (rq->H_val) r->hval_new.assign(rq->H_val, rq->H_val + ses.nnz);
+            if (rq->X0) {
+                const int64_t w = rq->nev + (ses.opt.m0 >= 0 ? ses.opt.m0 : std::max(3, (rq->nev + 9) / 10));
+                r->X0.assign(rq->X0, rq->X0 + (size_t)n * w);
+            }
         }
-        r->est_bytes = estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
-        if (r->est_bytes > sv->opts.hbm_budget_bytes) return fail(HBSD_ERR_OOM, "request exceeds the server's memory budget");
-    } else {   // follow-up of a resident session: new H values (optional), warm start or X0
-        std::lock_guard<std::mutex> lk(sv->mu);
-        auto s = sv->sessions.find(rq->session_id);
-        if (s == sv->sessions.end()) return fail(HBSD_ERR_ARG, "unknown or evicted session");
-        const Session& ses = s->second.h->s;
-        n = ses.n;
-        r->session_id = rq->session_id;
-        if (rq->H_val) r->hval_new.assign(rq->H_val, rq->H_val + ses.nnz);
-        if (rq->X0) {
-            const int64_t w = rq->nev + (ses.opt.m0 >= 0 ? ses.opt.m0 : std::max(3, (rq->nev + 9) / 10));
+        if (rq->X0 && r->is_new) {
+            const int64_t w = rq->nev + (rq->opt->m0 >= 0 ? rq->opt->m0 : std::max(3, (rq->nev + 9) / 10));
             r->X0.assign(rq->X0, rq->X0 + (size_t)n * w);
         }
-    }
-    if (rq->X0 && r->is_new) {
-        const int64_t w = rq->nev + (rq->opt->m0 >= 0 ? rq->opt->m0 : std::max(3, (rq->nev + 9) / 10));
-        r->X0.assign(rq->X0, rq->X0 + (size_t)n * w);
-    }
-    r->t_submit = Clock::now();
-    {
-        std::lock_guard<std::mutex> lk(sv->mu);
-        r->ticket = sv->next_ticket++;
-        *ticket = r->ticket;
-        sv->results[r->ticket] = ResultRec{};
-        sv->queue.push_back(std::move(r));
-    }
-    sv->cv.notify_all();
-    return HBSD_OK;
+        r->t_submit = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            r->ticket = sv->next_ticket++;
+            *ticket = r->ticket;
+            sv->results[r->ticket] = ResultRec{};
+            sv->queue.push_back(std::move(r));
+        }
+        sv->cv.notify_all();
+        return HBSD_OK;
+    });
 }
 
 int hbsd_poll(hbsd_server* sv, uint64_t ticket, hbsd_result* out) {
-    if (!sv || !out) return fail(HBSD_ERR_ARG, "NULL argument");
-    std::lock_guard<std::mutex> lk(sv->mu);
-    auto it = sv->results.find(ticket);
-    if (it == sv->results.end()) return fail(HBSD_ERR_ARG, "unknown ticket");
-    if (!it->second.done) return HBSD_BUSY;
-    *out = it->second.r;
-    sv->results.erase(it);
-    return HBSD_OK;
+    return guarded([&]() -> int {
+        if (!sv || !out) return fail(HBSD_ERR_ARG, "NULL argument");
+        std::lock_guard<std::mutex> lk(sv->mu);
+        auto it = sv->results.find(ticket);
+        if (it == sv->results.end()) return fail(HBSD_ERR_ARG, "unknown ticket");
+        if (!it->second.done) return HBSD_BUSY;
+        *out = it->second.r;
+        sv->results.erase(it);
+        return HBSD_OK;
+    });
 }
 
 int hbsd_session_release(hbsd_server* sv, int64_t session_id) {
-    if (!sv) return fail(HBSD_ERR_ARG, "NULL server");
-    std::unique_lock<std::mutex> lk(sv->mu);
-    auto s = sv->sessions.find(session_id);
-    if (s == sv->sessions.end()) return fail(HBSD_ERR_ARG, "unknown session");
-    if (s->second.busy) return HBSD_BUSY;
-    SessionRec rec = s->second;
-    sv->sessions.erase(s);
-    sv->used -= std::min(sv->used, rec.bytes);
-    sv->graveyard.push_back(rec);
-    lk.unlock();
-    bury(sv);
-    sv->cv.notify_all();
-    return HBSD_OK;
+    return guarded([&]() -> int {
+        if (!sv) return fail(HBSD_ERR_ARG, "NULL server");
+        std::unique_lock<std::mutex> lk(sv->mu);
+        auto s = sv->sessions.find(session_id);
+        if (s == sv->sessions.end()) return fail(HBSD_ERR_ARG, "unknown session");
+        if (s->second.busy) return HBSD_BUSY;
+        SessionRec rec = s->second;
+        sv->sessions.erase(s);
+        sv->used -= std::min(sv->used, rec.bytes);
+        sv->graveyard.push_back(rec);
+        lk.unlock();
+        bury(sv);
+        sv->cv.notify_all();
+        return HBSD_OK;
+    });
 }
 
 void hbsd_server_destroy(hbsd_server* sv) {

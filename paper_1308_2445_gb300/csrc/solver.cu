@@ -569,62 +569,66 @@ const char* hbsd_last_error(void) { return g_last_error.c_str(); }
 
 int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* lb, const hbsd_options* opt,
                 void* stream, hbsd_handle** out) {
-    if (!out) return fail(HBSD_ERR_ARG, "out is NULL");
-    *out = nullptr;
-    if (!H || !Sm || !lb || !opt) return fail(HBSD_ERR_ARG, "H, S, local blocks and options are required");
-    if (H->is_complex || Sm->is_complex) return fail(HBSD_ERR_UNSUPPORTED, "complex Hermitian input is not built yet");
-    if (H->n <= 0 || H->n != Sm->n || H->nnz != Sm->nnz || H->nnz != H->row_ptr[H->n])
-        return fail(HBSD_ERR_ARG, "H and S must have the same n and nnz");
-    if (!H->row_ptr || !H->col_idx || !H->val || !Sm->val || !Sm->row_ptr || !Sm->col_idx)
-        return fail(HBSD_ERR_ARG, "NULL CSR array");
-    if (std::memcmp(H->row_ptr, Sm->row_ptr, (H->n + 1) * 8) != 0 ||
-        std::memcmp(H->col_idx, Sm->col_idx, H->nnz * 4) != 0)
-        return fail(HBSD_ERR_ARG, "H and S must share one sparsity pattern");
-    for (int64_t e = 0; e < H->nnz; ++e)
-        if (H->col_idx[e] < 0 || H->col_idx[e] >= H->n) return fail(HBSD_ERR_ARG, "column index out of range");
-    if (!std::isfinite(opt->sigma_bar)) return fail(HBSD_ERR_ARG, "sigma_bar must be set");
-    if (opt->precond < HBSD_PRECOND_HYBRID || opt->precond > HBSD_PRECOND_LOCAL)
-        return fail(HBSD_ERR_ARG, "unknown preconditioner mode");
-    if (opt->local_solver != HBSD_LOCAL_MINRES && opt->local_solver != HBSD_LOCAL_ONESTEP)
-        return fail(HBSD_ERR_ARG, "hbsd_create: local_solver must be HBSD_LOCAL_MINRES or HBSD_LOCAL_ONESTEP");
-    if (!lb->dof_node || lb->grid[0] <= 0 || lb->grid[1] <= 0 || lb->grid[2] <= 0)
-        return fail(HBSD_ERR_ARG, "local blocks need dof_node and a positive grid");
-    hbsd_handle* h = new hbsd_handle();
-    Session* S = &h->s;
-    S->n = H->n;
-    S->nnz = H->nnz;
-    S->opt = *opt;
-    {
-        const char* e = std::getenv("HBSD_NO_DF64");
-        S->opt_df64 = !(e && e[0] && e[0] != '0');
-    }
-    S->sigma0 = std::isnan(opt->sigma0) ? opt->sigma_bar : opt->sigma0;
-    if (stream) {
-        S->stream = (cudaStream_t)stream;
-    } else {
-        if (cudaStreamCreate(&S->stream) != cudaSuccess) {  // blocking: ordered with the legacy default stream
-            delete h;
-            return fail(HBSD_ERR_CUDA, "cudaStreamCreate failed");
+    return guarded([&]() -> int {
+        if (!out) return fail(HBSD_ERR_ARG, "out is NULL");
+        *out = nullptr;
+        if (!H || !Sm || !lb || !opt) return fail(HBSD_ERR_ARG, "H, S, local blocks and options are required");
+        if (H->is_complex || Sm->is_complex) return fail(HBSD_ERR_UNSUPPORTED, "complex Hermitian input is not built yet");
+        if (!H->row_ptr || !H->col_idx || !H->val || !Sm->val || !Sm->row_ptr || !Sm->col_idx)
+            return fail(HBSD_ERR_ARG, "NULL CSR array");
+        if (H->n <= 0 || H->n != Sm->n || H->nnz != Sm->nnz || H->nnz != H->row_ptr[H->n])
+            return fail(HBSD_ERR_ARG, "H and S must have the same n and nnz");
+        if (std::memcmp(H->row_ptr, Sm->row_ptr, (H->n + 1) * 8) != 0 ||
+            std::memcmp(H->col_idx, Sm->col_idx, H->nnz * 4) != 0)
+            return fail(HBSD_ERR_ARG, "H and S must share one sparsity pattern");
+        for (int64_t e = 0; e < H->nnz; ++e)
+            if (H->col_idx[e] < 0 || H->col_idx[e] >= H->n) return fail(HBSD_ERR_ARG, "column index out of range");
+        if (!std::isfinite(opt->sigma_bar)) return fail(HBSD_ERR_ARG, "sigma_bar must be set");
+        if (opt->precond < HBSD_PRECOND_HYBRID || opt->precond > HBSD_PRECOND_LOCAL)
+            return fail(HBSD_ERR_ARG, "unknown preconditioner mode");
+        if (opt->local_solver != HBSD_LOCAL_MINRES && opt->local_solver != HBSD_LOCAL_ONESTEP)
+            return fail(HBSD_ERR_ARG, "hbsd_create: local_solver must be HBSD_LOCAL_MINRES or HBSD_LOCAL_ONESTEP");
+        if (!lb->dof_node || lb->grid[0] <= 0 || lb->grid[1] <= 0 || lb->grid[2] <= 0)
+            return fail(HBSD_ERR_ARG, "local blocks need dof_node and a positive grid");
+        hbsd_handle* h = new hbsd_handle();
+        Session* S = &h->s;
+        S->n = H->n;
+        S->nnz = H->nnz;
+        S->opt = *opt;
+        {
+            const char* e = std::getenv("HBSD_NO_DF64");
+            S->opt_df64 = !(e && e[0] && e[0] != '0');
         }
-        S->own_stream = true;
-    }
-    int rc = sell_build(S->A, S->n, H->row_ptr, H->col_idx, H->val, Sm->val, S->sigma0);
-    if (rc < 0) { hbsd_destroy(h); return rc; }
-    S->h_sval.assign(Sm->val, Sm->val + S->nnz);
-    std::vector<double> aval(S->nnz);
-    for (int64_t e = 0; e < S->nnz; ++e) aval[e] = H->val[e] - opt->sigma_bar * Sm->val[e];
-    if (opt->precond != HBSD_PRECOND_LOCAL) {   // the local-only mode has no global step
-        rc = factor_build(S, S->F, S->n, H->row_ptr, H->col_idx, aval.data(), lb->dof_node, lb->grid, S->stream);
-        if (rc < 0) { std::string keep = g_last_error; hbsd_destroy(h); g_last_error = keep; return rc; }
-        S->has_factor = true;
-    }
-    *out = h;
-    return HBSD_OK;
+        S->sigma0 = std::isnan(opt->sigma0) ? opt->sigma_bar : opt->sigma0;
+        if (stream) {
+            S->stream = (cudaStream_t)stream;
+        } else {
+            if (cudaStreamCreate(&S->stream) != cudaSuccess) {  // blocking: ordered with the legacy default stream
+                delete h;
+                return fail(HBSD_ERR_CUDA, "cudaStreamCreate failed");
+            }
+            S->own_stream = true;
+        }
+        int rc = sell_build(S->A, S->n, H->row_ptr, H->col_idx, H->val, Sm->val, S->sigma0);
+        if (rc < 0) { hbsd_destroy(h); return rc; }
+        S->h_sval.assign(Sm->val, Sm->val + S->nnz);
+        std::vector<double> aval(S->nnz);
+        for (int64_t e = 0; e < S->nnz; ++e) aval[e] = H->val[e] - opt->sigma_bar * Sm->val[e];
+        if (opt->precond != HBSD_PRECOND_LOCAL) {   // the local-only mode has no global step
+            rc = factor_build(S, S->F, S->n, H->row_ptr, H->col_idx, aval.data(), lb->dof_node, lb->grid, S->stream);
+            if (rc < 0) { std::string keep = g_last_error; hbsd_destroy(h); g_last_error = keep; return rc; }
+            S->has_factor = true;
+        }
+        *out = h;
+        return HBSD_OK;
+    });
 }
 
 int hbsd_update_H(hbsd_handle* h, const double* H_val) {
-    if (!h || !H_val) return fail(HBSD_ERR_ARG, "NULL argument");
-    return sell_update_h(h->s.A, H_val, h->s.h_sval.data(), h->s.sigma0);
+    return guarded([&]() -> int {
+        if (!h || !H_val) return fail(HBSD_ERR_ARG, "NULL argument");
+        return sell_update_h(h->s.A, H_val, h->s.h_sval.data(), h->s.sigma0);
+    });
 }
 
 void hbsd_destroy(hbsd_handle* h) {
@@ -644,150 +648,180 @@ static int m0_of(const Session& S, int nev) { return S.opt.m0 >= 0 ? S.opt.m0 : 
 
 int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0, double* lambda_dev,
                       double* X_dev, int64_t ldx, int* iters, hbsd_stats* st) {
-    if (!h) return fail(HBSD_ERR_ARG, "NULL handle");
-    Session* S = &h->s;
-    if (nev < 1 || !(tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
-    const int w = nev + m0_of(*S, nev);
-    if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
-    if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
-        return fail(HBSD_ERR_ARG, "unknown precision mode");
-    if (!X0_dev) {
-        std::vector<double> hx((size_t)S->n * w);
-        seed_normals(S->opt.seed, 2, (int64_t)hx.size(), hx.data());
-        HBSD_TRY(S->io_x0.alloc(hx.size()));
-        HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice, S->stream));
-        HBSD_CUDA(cudaStreamSynchronize(S->stream));   // hx is released at the end of this block
-        X0_dev = S->io_x0.p;
-        ldx0 = w;
-    } else if (ldx0 < w) {
-        return fail(HBSD_ERR_ARG, "ldx0 < nev + m0");
-    }
-    S->launches = 0;
-    auto t0 = std::chrono::steady_clock::now();
-    int rc = labpsd_solve(S, nev, tol, X0_dev, ldx0, lambda_dev, X_dev, ldx, iters);
-    auto t1 = std::chrono::steady_clock::now();
-    S->stats.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    S->stats.gpu_launches = S->launches;
-    if (st) *st = S->stats;
-    return rc;
+    return guarded([&]() -> int {
+        if (!h) return fail(HBSD_ERR_ARG, "NULL handle");
+        Session* S = &h->s;
+        if (nev < 1 || !(tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
+        const int w = nev + m0_of(*S, nev);
+        if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
+        if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
+            return fail(HBSD_ERR_ARG, "unknown precision mode");
+        if (!X0_dev) {
+            std::vector<double> hx((size_t)S->n * w);
+            seed_normals(S->opt.seed, 2, (int64_t)hx.size(), hx.data());
+            HBSD_TRY(S->io_x0.alloc(hx.size()));
+            HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice, S->stream));
+            HBSD_CUDA(cudaStreamSynchronize(S->stream));   // hx is released at the end of this block
+            X0_dev = S->io_x0.p;
+            ldx0 = w;
+        } else if (ldx0 < w) {
+            return fail(HBSD_ERR_ARG, "ldx0 < nev + m0");
+        }
+        S->launches = 0;
+        auto t0 = std::chrono::steady_clock::now();
+        int rc = labpsd_solve(S, nev, tol, X0_dev, ldx0, lambda_dev, X_dev, ldx, iters);
+        auto t1 = std::chrono::steady_clock::now();
+        S->stats.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        S->stats.gpu_launches = S->launches;
+        if (st) *st = S->stats;
+        return rc;
+    });
 }
 
 int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm, double* lambda, double* X, int* iters,
                hbsd_stats* st) {
-    if (!h || !lambda) return fail(HBSD_ERR_ARG, "NULL handle or lambda");
-    Session* S = &h->s;
-    if (nev < 1) return fail(HBSD_ERR_ARG, "nev >= 1 required");
-    const int w = nev + m0_of(*S, nev);
-    if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
-    // host <-> device traffic goes through session-resident buffers on the session's stream
-    // (no allocation after the first solve of a size, no legacy-stream synchronisation)
-    const double* x0p = nullptr;
-    int64_t ld0 = w;
-    if (warm) {
-        if (X0) return fail(HBSD_ERR_ARG, "warm start takes X0 = NULL");
-        if (!S->psi_keep.p || S->keep_w != w) return fail(HBSD_ERR_ARG, "no previous block of this width to warm-start from");
-        // the solve overwrites psi_keep; start from a copy
-        HBSD_TRY(S->io_x0.alloc(S->psi_keep.n));
-        HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, S->psi_keep.p, S->psi_keep.n * 8, cudaMemcpyDeviceToDevice, S->stream));
-        x0p = S->io_x0.p;
-        ld0 = S->keep_ld;
-    } else if (X0) {
-        HBSD_TRY(S->io_x0.alloc((size_t)S->n * w));
-        HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, X0, (size_t)S->n * w * 8, cudaMemcpyHostToDevice, S->stream));
-        x0p = S->io_x0.p;
-    }
-    HBSD_TRY(S->io_lam.alloc(nev));
-    if (X) HBSD_TRY(S->io_x.alloc((size_t)S->n * nev));
-    int rc = hbsd_solve_device(h, nev, tol, x0p, ld0, S->io_lam.p, X ? S->io_x.p : nullptr, nev, iters, st);
-    if (rc < 0) return rc;
-    HBSD_CUDA(cudaMemcpyAsync(lambda, S->io_lam.p, nev * 8, cudaMemcpyDeviceToHost, S->stream));
-    if (X) HBSD_CUDA(cudaMemcpyAsync(X, S->io_x.p, (size_t)S->n * nev * 8, cudaMemcpyDeviceToHost, S->stream));
-    HBSD_CUDA(cudaStreamSynchronize(S->stream));
-    return rc;
+    return guarded([&]() -> int {
+        if (!h || !lambda) return fail(HBSD_ERR_ARG, "NULL handle or lambda");
+        Session* S = &h->s;
+        if (nev < 1) return fail(HBSD_ERR_ARG, "nev >= 1 required");
+        const int w = nev + m0_of(*S, nev);
+        if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
+        // host <-> device traffic goes through session-resident buffers on the session's stream
+        // (no allocation after the first solve of a size, no legacy-stream synchronisation)
+        const double* x0p = nullptr;
+        int64_t ld0 = w;
+        if (warm) {
+            if (X0) return fail(HBSD_ERR_ARG, "warm start takes X0 = NULL");
+            if (!S->psi_keep.p || S->keep_w != w) return fail(HBSD_ERR_ARG, "no previous block of this width to warm-start from");
+            // the solve overwrites psi_keep; start from a copy
+            HBSD_TRY(S->io_x0.alloc(S->psi_keep.n));
+            HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, S->psi_keep.p, S->psi_keep.n * 8, cudaMemcpyDeviceToDevice, S->stream));
+            x0p = S->io_x0.p;
+            ld0 = S->keep_ld;
+        } else if (X0) {
+            HBSD_TRY(S->io_x0.alloc((size_t)S->n * w));
+            HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, X0, (size_t)S->n * w * 8, cudaMemcpyHostToDevice, S->stream));
+            x0p = S->io_x0.p;
+        }
+        HBSD_TRY(S->io_lam.alloc(nev));
+        if (X) HBSD_TRY(S->io_x.alloc((size_t)S->n * nev));
+        int rc = hbsd_solve_device(h, nev, tol, x0p, ld0, S->io_lam.p, X ? S->io_x.p : nullptr, nev, iters, st);
+        if (rc < 0) return rc;
+        HBSD_CUDA(cudaMemcpyAsync(lambda, S->io_lam.p, nev * 8, cudaMemcpyDeviceToHost, S->stream));
+        if (X) HBSD_CUDA(cudaMemcpyAsync(X, S->io_x.p, (size_t)S->n * nev * 8, cudaMemcpyDeviceToHost, S->stream));
+        HBSD_CUDA(cudaStreamSynchronize(S->stream));
+        return rc;
+    });
 }
 
 int hbsd_probe_barrier_timeout(double limit_s, void* stream) {
-    return barrier_timeout_probe(limit_s, (cudaStream_t)stream);
+    return guarded([&]() -> int {
+        return barrier_timeout_probe(limit_s, (cudaStream_t)stream);
+    });
 }
 
 int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out) {
-    if (!out || count < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    seed_normals(seed, stream, count, out);
-    return HBSD_OK;
+    return guarded([&]() -> int {
+        if (!out || count < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        seed_normals(seed, stream, count, out);
+        return HBSD_OK;
+    });
 }
 
 // ---- step-level entry points ---------------------------------------------------------------
 int hbsd_res_history(const hbsd_handle* h, double* out, int cap) {
-    if (!h || cap < 0 || (cap > 0 && !out)) return fail(HBSD_ERR_ARG, "bad arguments");
-    const std::vector<double>& v = h->s.res_hist;
-    for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
-    return (int)v.size();
+    return guarded([&]() -> int {
+        if (!h || cap < 0 || (cap > 0 && !out)) return fail(HBSD_ERR_ARG, "bad arguments");
+        const std::vector<double>& v = h->s.res_hist;
+        for (int i = 0; i < cap && i < (int)v.size(); ++i) out[i] = v[i];
+        return (int)v.size();
+    });
 }
 
 int hbsd_set_nonlocal(hbsd_handle* h, int k, const double* F, int64_t ldf, const double* G) {
-    if (!h) return fail(HBSD_ERR_ARG, "bad arguments");
-    HBSD_CUDA(cudaStreamSynchronize(h->s.stream));   // no work of this session reads the old term any more
-    return nl_set(&h->s, k, F, ldf, G);
+    return guarded([&]() -> int {
+        if (!h) return fail(HBSD_ERR_ARG, "bad arguments");
+        HBSD_CUDA(cudaStreamSynchronize(h->s.stream));   // no work of this session reads the old term any more
+        return nl_set(&h->s, k, F, ldf, G);
+    });
 }
 
 int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx, double* SX,
                    int64_t ldsx) {
-    if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    return spmm_pair<double>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+    return guarded([&]() -> int {
+        if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        return spmm_pair<double>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+    });
 }
 
 int hbsd_spmm_pair_f32(hbsd_handle* h, const float* X, int64_t ldx, int k, float* HX, int64_t ldhx, float* SX,
                        int64_t ldsx) {
-    if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    return spmm_pair<float>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+    return guarded([&]() -> int {
+        if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        return spmm_pair<float>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+    });
 }
 
 int hbsd_precond_apply_f32(hbsd_handle* h, const float* R, int64_t ldr, int k, float* P, int64_t ldp) {
-    if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    HBSD_TRY(factor_make_fp32(h->s.F, h->s.A.dscale.p, h->s.stream));
-    HBSD_TRY(factor_solve<float>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
-    return nl_smw_correct<float>(&h->s, P, ldp, k, h->s.stream);
+    return guarded([&]() -> int {
+        if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        HBSD_TRY(factor_make_fp32(h->s.F, h->s.A.dscale.p, h->s.stream));
+        HBSD_TRY(factor_solve<float>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
+        return nl_smw_correct<float>(&h->s, P, ldp, k, h->s.stream);
+    });
 }
 
 int hbsd_dscale(const hbsd_handle* h, double* d_host) {
-    if (!h || !d_host) return fail(HBSD_ERR_ARG, "bad arguments");
-    std::memcpy(d_host, h->s.A.h_dscale.data(), h->s.n * sizeof(double));
-    return HBSD_OK;
+    return guarded([&]() -> int {
+        if (!h || !d_host) return fail(HBSD_ERR_ARG, "bad arguments");
+        std::memcpy(d_host, h->s.A.h_dscale.data(), h->s.n * sizeof(double));
+        return HBSD_OK;
+    });
 }
 
 int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e, double* Y, int64_t ldy) {
-    if (!h || !X || !e || !Y || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    return spmm_shifted<double>(&h->s, h->s.A, X, ldx, k, e, Y, ldy, h->s.stream);
+    return guarded([&]() -> int {
+        if (!h || !X || !e || !Y || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        return spmm_shifted<double>(&h->s, h->s.A, X, ldx, k, e, Y, ldy, h->s.stream);
+    });
 }
 
 int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double* PsiS, int64_t lds, const double* E,
                   int m, double* R, int64_t ldr, double* res) {
-    if (!h || !PsiH || !PsiS || !E || !res || m <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    Session* S = &h->s;
-    HBSD_TRY(S->ws.alloc((size_t)304 * 2 * m + 64));
-    return residual<double>(S, PsiH, ldh, PsiS, lds, E, m, R, ldr, S->n, res, nullptr, S->stream);
+    return guarded([&]() -> int {
+        if (!h || !PsiH || !PsiS || !E || !res || m <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        Session* S = &h->s;
+        HBSD_TRY(S->ws.alloc((size_t)304 * 2 * m + 64));
+        return residual<double>(S, PsiH, ldh, PsiS, lds, E, m, R, ldr, S->n, res, nullptr, S->stream);
+    });
 }
 
 int hbsd_precond_apply(hbsd_handle* h, const double* R, int64_t ldr, int k, double* P, int64_t ldp) {
-    if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    HBSD_TRY(factor_solve<double>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
-    return nl_smw_correct<double>(&h->s, P, ldp, k, h->s.stream);
+    return guarded([&]() -> int {
+        if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        HBSD_TRY(factor_solve<double>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
+        return nl_smw_correct<double>(&h->s, P, ldp, k, h->s.stream);
+    });
 }
 
 int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k, double eta, int max_minres,
                 double* P, int64_t ldp, int* steps) {
-    if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    Session* S = &h->s;
-    HBSD_TRY(S->ws.alloc((size_t)304 * 2 * std::max(k, 1) + 64));
-    return minres_batch<double>(S, R, ldr, e, k, eta, max_minres, P, ldp, steps, nullptr, S->stream);
+    return guarded([&]() -> int {
+        if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        Session* S = &h->s;
+        HBSD_TRY(S->ws.alloc((size_t)304 * 2 * std::max(k, 1) + 64));
+        return minres_batch<double>(S, R, ldr, e, k, eta, max_minres, P, ldp, steps, nullptr, S->stream);
+    });
 }
 
 int hbsd_onestep(hbsd_handle* h, const double* R, int64_t ldr, const double* e, int k, double eta, int max_steps,
                  double* P, int64_t ldp, int* steps) {
-    if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    Session* S = &h->s;
-    return minres_batch<double>(S, R, ldr, e, k, eta, max_steps, P, ldp, steps, nullptr, S->stream,
-                                HBSD_LOCAL_ONESTEP);
+    return guarded([&]() -> int {
+        if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        Session* S = &h->s;
+        return minres_batch<double>(S, R, ldr, e, k, eta, max_steps, P, ldp, steps, nullptr, S->stream,
+                                    HBSD_LOCAL_ONESTEP);
+    });
 }
 
 // Step-level calls without a session run on a temporary one that only carries scratch.
@@ -799,49 +833,61 @@ static Session* scratch_session() {
 
 int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs, int64_t n,
               int q, double* HR, double* SR, void* stream) {
-    if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    Session* S = scratch_session();
-    const int tiles = ceil_div(q, 32);
-    HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + 1024));
-    return gram2<double>(S, Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR, SR,
-                         (cudaStream_t)stream);
+    return guarded([&]() -> int {
+        if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        Session* S = scratch_session();
+        const int tiles = ceil_div(q, 32);
+        HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + 1024));
+        return gram2<double>(S, Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR, SR,
+                             (cudaStream_t)stream);
+    });
 }
 
 int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
                       int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream) {
-    if (!Z || !ZH || !ZS || !HR || !SR) return fail(HBSD_ERR_ARG, "bad arguments");
-    return gram_noalloc(Z, ldz, ZH, ldzh, ZS, ldzs, n, q, HR, SR, (cudaStream_t)stream);
+    return guarded([&]() -> int {
+        if (!Z || !ZH || !ZS || !HR || !SR) return fail(HBSD_ERR_ARG, "bad arguments");
+        return gram_noalloc(Z, ldz, ZH, ldzh, ZS, ldzs, n, q, HR, SR, (cudaStream_t)stream);
+    });
 }
 
 int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double* theta, double* W, int* info,
                        void* stream) {
-    if (!HR || !SR || !theta || !W) return fail(HBSD_ERR_ARG, "bad arguments");
-    Session* S = scratch_session();
-    int hinfo[2] = {0, 0};
-    int rc = rayleigh_ritz_cluster(S, HR, SR, q, k, theta, W, hinfo, (cudaStream_t)stream);
-    if (info) {
-        int tmp[2] = {hinfo[0], hinfo[1]};
-        cudaError_t e = cudaMemcpy(info, tmp, sizeof(tmp), cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) return fail(HBSD_ERR_CUDA, cudaGetErrorString(e));
-    }
-    return rc;
+    return guarded([&]() -> int {
+        if (!HR || !SR || !theta || !W) return fail(HBSD_ERR_ARG, "bad arguments");
+        Session* S = scratch_session();
+        int hinfo[2] = {0, 0};
+        int rc = rayleigh_ritz_cluster(S, HR, SR, q, k, theta, W, hinfo, (cudaStream_t)stream);
+        if (info) {
+            int tmp[2] = {hinfo[0], hinfo[1]};
+            cudaError_t e = cudaMemcpy(info, tmp, sizeof(tmp), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return fail(HBSD_ERR_CUDA, cudaGetErrorString(e));
+        }
+        return rc;
+    });
 }
 
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
-    if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
-    return update2<double>(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
+    return guarded([&]() -> int {
+        if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
+        return update2<double>(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
+    });
 }
 
 int hbsd_gram_df64(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
                    int64_t n, int q, double* HR, double* SR, void* stream) {
-    if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
-    return gram2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR,
-                      SR, (cudaStream_t)stream);
+    return guarded([&]() -> int {
+        if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        return gram2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR,
+                          SR, (cudaStream_t)stream);
+    });
 }
 
 int hbsd_update_df64(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
-    if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
-    return update2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream, true);
+    return guarded([&]() -> int {
+        if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
+        return update2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream, true);
+    });
 }
 
 }  // extern "C"

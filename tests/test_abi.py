@@ -56,6 +56,42 @@ def test_create_rejects_bad_input_without_gpu(lib):
     rc = lib.hbsd_create(None, None, None, None, None, C.byref(h))
     assert rc == hbsd.HBSD_ERR_ARG
     assert b"required" in lib.hbsd_last_error()
+    # a 2 x 2 diagonal pair, then one defect at a time
+    rp = (C.c_int64 * 3)(0, 1, 2)
+    ci = (C.c_int32 * 2)(0, 1)
+    ci_bad = (C.c_int32 * 2)(0, 2)
+    ci_other = (C.c_int32 * 2)(1, 0)
+    hv = (C.c_double * 2)(1.0, 2.0)
+    sv = (C.c_double * 2)(1.0, 1.0)
+    dn = (C.c_int32 * 2)(0, 0)
+    lb = hbsd.hbsd_local_blocks(dof_node=C.cast(dn, C.POINTER(C.c_int32)))
+    lb.grid[:] = [1, 1, 1]
+    o = hbsd.options_default()
+    o.sigma_bar = -1.0
+
+    def csr(n, nnz, row_ptr, col_idx, val):
+        return hbsd.hbsd_csr(n=n, nnz=nnz, row_ptr=C.cast(row_ptr, C.POINTER(C.c_int64)) if row_ptr else None,
+                             col_idx=C.cast(col_idx, C.POINTER(C.c_int32)), val=C.cast(val, C.POINTER(C.c_double)),
+                             is_complex=0)
+
+    S = csr(2, 2, rp, ci, sv)
+    for H, words in ((csr(2, 2, None, ci, hv), b"NULL CSR array"),      # checked before row_ptr is read
+                     (csr(2, 3, rp, ci, hv), b"same n and nnz"),
+                     (csr(2, 2, rp, ci_other, hv), b"one sparsity pattern")):
+        assert lib.hbsd_create(C.byref(H), C.byref(S), C.byref(lb), C.byref(o), None, C.byref(h)) == hbsd.HBSD_ERR_ARG
+        assert words in lib.hbsd_last_error(), lib.hbsd_last_error()
+    Sb = csr(2, 2, rp, ci_bad, sv)
+    Hb = csr(2, 2, rp, ci_bad, hv)
+    assert lib.hbsd_create(C.byref(Hb), C.byref(Sb), C.byref(lb), C.byref(o), None, C.byref(h)) == hbsd.HBSD_ERR_ARG
+    assert b"column index out of range" in lib.hbsd_last_error()
+    H = csr(2, 2, rp, ci, hv)
+    o.sigma_bar = float("nan")
+    assert lib.hbsd_create(C.byref(H), C.byref(S), C.byref(lb), C.byref(o), None, C.byref(h)) == hbsd.HBSD_ERR_ARG
+    assert b"sigma_bar" in lib.hbsd_last_error()
+    o.sigma_bar = -1.0
+    o.precond = 9
+    assert lib.hbsd_create(C.byref(H), C.byref(S), C.byref(lb), C.byref(o), None, C.byref(h)) == hbsd.HBSD_ERR_ARG
+    assert h.value is None
 
 
 def test_library_start_block_generator_matches_inputs(lib):
