@@ -33,6 +33,30 @@ def test_closed_form_eigenvalues(nev):
     assert np.abs(r.lam - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
+def test_spmm_pair_on_fourier_modes():
+    # Steps 3 and 7 on the unenriched pair with V = v0: a discrete Fourier mode
+    # x(i, j, k) = c_a(i) c_b(j) c_c(k) with c_a(i) = cos(2 pi a i / N) is an exact eigenvector, so
+    # the two products of spmm_pair satisfy Hs x = (lambda - sigma0) S x, lambda = v0 plus the
+    # 1-D linear-element symbol 3 (1 - cos t) / (h^2 (2 + cos t)) summed over the three wavenumbers
+    N, v0 = 6, 0.3
+    q = pi.generate(N, 0, 0, 0.1, 1, v0=v0)
+    Hs, S, sigma0 = L.make_shifted(q)
+    i = np.arange(N ** 3)
+    ijk = (i % N, (i // N) % N, i // (N * N))
+    h = 1.0 / N
+    sym = lambda a: 3.0 * (1.0 - math.cos(2 * math.pi * a / N)) / (h * h * (2.0 + math.cos(2 * math.pi * a / N)))
+    waves = [(1, 1, 1), (1, 2, 0), (3, 0, 2), (0, 0, 0)]
+    X = np.stack([np.prod([np.cos(2 * math.pi * w[d] * ijk[d] / N) for d in range(3)], axis=0) for w in waves], 1)
+    lam = np.array([v0 + sum(sym(a) for a in w) for w in waves])
+    HX, SX = L.spmm_pair(Hs, S, X)
+    assert np.abs(SX).max() > 0.0
+    for j in range(len(waves)):
+        assert np.abs(HX[:, j] - (lam[j] - sigma0) * SX[:, j]).max() <= 1e-12 * np.abs(HX[:, j]).max() + 1e-13
+    # the shift: sigma0 = eps_bar, and the constant mode carries only the potential
+    assert sigma0 == q.eps_bar
+    assert np.allclose(HX[:, 3], (v0 - sigma0) * SX[:, 3], rtol=1e-10, atol=0)   # row sums of K round
+
+
 def test_closed_form_cluster_subspace():
     # the 6-fold cluster of the 6^3 mesh is spanned by the sampled cos/sin(2 pi x_d) modes
     N = 6
