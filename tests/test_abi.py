@@ -133,3 +133,14 @@ def test_server_host_bookkeeping_without_gpu():
     assert lib.hbsd_submit(h, ctypes.byref(rq), lam, None, ctypes.byref(t)) == hbsd.HBSD_ERR_ARG  # no problem
     assert lib.hbsd_session_release(h, ctypes.c_int64(0)) == hbsd.HBSD_ERR_ARG
     lib.hbsd_server_destroy(h)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    # no CPU fallback: with the shared library absent every call raises
+    from paper_1308_2445_gb300 import hbsd
+    monkeypatch.setattr(hbsd, "_lib", None)
+    monkeypatch.setattr(hbsd, "LIB_PATH", str(tmp_path / "libhbsd.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        hbsd.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        hbsd.options_default()
