@@ -305,6 +305,32 @@ def test_rayleigh_ritz_rank_deficient_fallback():
     assert np.allclose(g, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
 
 
+def test_residual_by_hand():
+    # steps 4-5 (Eq. res1): r_i = H psi_i - eps_i S psi_i and Res_i = ||r_i|| / ||H psi_i||, the
+    # columns beyond m ignored.  PsiH = [[3, 1, 9], [4, 0, 9]], PsiS = [[1, 1, 9], [0, 2, 9]],
+    # E = (2, 0.5, 7): r_1 = (3 - 2, 4 - 0) = (1, 4), r_2 = (1 - 0.5, 0 - 1) = (0.5, -1);
+    # ||H psi_1|| = 5, ||H psi_2|| = 1
+    PH = np.array([[3.0, 1.0, 9.0], [4.0, 0.0, 9.0]])
+    PS = np.array([[1.0, 1.0, 9.0], [0.0, 2.0, 9.0]])
+    R, res = L.residual(PH, PS, np.array([2.0, 0.5, 7.0]), 2)
+    assert R.shape == (2, 2)
+    assert np.array_equal(R, [[1.0, 0.5], [4.0, -1.0]])
+    assert res == pytest.approx([math.sqrt(17.0) / 5.0, math.sqrt(1.25)], rel=1e-15)
+
+
+def test_localized_by_hand():
+    # remark 4: a column is refined locally when Res_i <= tau1 and the Ritz value moved by at
+    # most tau2 of its previous value; nothing is localized without a previous value (l = 1)
+    res = np.array([0.05, 0.05, 0.2, 0.1])
+    E = np.array([1.0, 2.0, 3.0, -1.05])
+    E_prev = np.array([1.05, 2.5, 3.0, -1.0])
+    got = L.localized(res, E, E_prev, 0.1, 0.1)
+    # col 0: 0.05 <= 0.1 and |1 - 1.05| = 0.05 <= 0.105; col 1: moved 0.5 > 0.25;
+    # col 2: Res 0.2 > 0.1; col 3: Res at the bound, moved 0.05 <= 0.1 (|E_prev| taken)
+    assert got.tolist() == [True, False, False, True]
+    assert not L.localized(res, E, None, 0.1, 0.1).any()
+
+
 def test_default_m0():
     assert [L.default_m0(m) for m in (1, 16, 30, 31, 64, 256)] == [3, 3, 3, 4, 7, 26]
 
@@ -344,7 +370,6 @@ def test_planted_mistakes_are_caught(monkeypatch):
     # (d) refinement shift with the wrong sign: (H + eps_i S) instead of (H - eps_i S)
     monkeypatch.setattr(L, "refine", lambda Hs, S, e, r, p0, eta, mx: orig_ref(Hs, S, -e - 50.0, r, p0, eta, mx))
     r = L.labpsd(p, nev, 1e-9, seed=3, opts=L.Options(max_outer=200))
-    ref = L.labpsd.__wrapped__ if hasattr(L.labpsd, "__wrapped__") else None
     monkeypatch.setattr(L, "refine", orig_ref)
     good = L.labpsd(p, nev, 1e-9, seed=3)
     assert r.iters > good.iters
