@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"],
-                    help="mixed: FP32 LABPSD phase + FP64 refinement sweep to tol (default); fp64: FP64 throughout")
+                    help="mixed: step 6(a) in FP32 on the scaled pencil, Gram and update in double-float, "
+                         "the rest in FP64 (default); fp64: FP64 throughout")
     ap.add_argument("--local-solver", default="minres", choices=["minres", "onestep"],
                     help="step 6(b): MINRES (default) or the first-order one-step refinement (Sec. 6)")
     ap.add_argument("--workload", default="medium", choices=["medium", "medium-nonlocal"],

@@ -72,7 +72,8 @@ typedef struct {
 } hbsd_local_blocks;
 
 #define HBSD_PRECISION_FP64   0   /* every step in FP64                                  */
-#define HBSD_PRECISION_MIXED  1   /* FP32 sparse steps + FP64 Rayleigh-Ritz and final check */
+#define HBSD_PRECISION_MIXED  1   /* step 6(a) in FP32 on the scaled pencil, steps 8 and 10-11
+                                     in double-float, every other step in FP64             */
 
 #define HBSD_PRECOND_HYBRID   0   /* steps 6(a) + 6(b) (Sec. 3 hybrid scheme)           */
 #define HBSD_PRECOND_GLOBAL   1   /* step 6(a) only (Eq. globalprecond)                  */
@@ -106,7 +107,8 @@ typedef struct {
 /* Statistics of one solve (all counts cumulative over the solve). */
 typedef struct {
     int iters;               /* outer BPSD iterations (steps 4-11)                         */
-    int iters_fp64;          /* of which run in FP64 (the final refinement sweep, mixed)   */
+    int iters_fp64;          /* of which with FP64 residuals and Rayleigh-Ritz (all, in    */
+                             /* both forms)                                                */
     int64_t minres_steps;    /* total MINRES steps over all refined columns (M_s)          */
     int64_t precond_cols;    /* total columns through step 6(a)                            */
     int64_t local_cols;      /* total columns through step 6(b)                            */
@@ -212,7 +214,8 @@ int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k,
 int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e,
                       double* Y, int64_t ldy);
 
-/* FP32 forms used by the mixed precision (HBSD_PRECISION_MIXED) phase.  They act on the
+/* FP32 forms on the scaled pencil (hbsd_precond_apply_f32 is step 6(a) of HBSD_PRECISION_MIXED;
+ * hbsd_spmm_pair_f32 is a step-level product on the FP32 copy of the matrix).  They act on the
  * diagonally scaled pencil (D Hs D, D S D), D = diag(S)^{-1/2} (hbsd_dscale returns D, host,
  * n doubles): hbsd_spmm_pair_f32 gives (D Hs D) X and (D S D) X; hbsd_precond_apply_f32 gives
  * P = -(D (H - sigma_bar S) D)^{-1} R from the FP32 copy of the factor panels.  Blocks are

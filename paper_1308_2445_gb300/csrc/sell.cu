@@ -97,8 +97,9 @@ int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_id
     return sell_fill_fp32(m, hs.data(), cols.data(), slot_row.data());
 }
 
-// FP32 values of the diagonally scaled pencil (D Hs D, D S D), D = diag(S)^{-1/2}: the mixed
-// path's FP32 phase runs on it, because the unscaled basis spans ~30 orders of magnitude.
+// FP32 values of the diagonally scaled pencil (D Hs D, D S D), D = diag(S)^{-1/2}, for the FP32
+// step entry points: FP32 works only on this pencil, because the unscaled basis spans ~30 orders
+// of magnitude.
 int sell_fill_fp32(Sell& m, const double2* hs, const int32_t* cols, const int32_t* slot_row) {
     std::vector<float2> hs32(m.stored, make_float2(0.f, 0.f));
     for (int64_t sl = 0; sl < m.n_slices; ++sl) {

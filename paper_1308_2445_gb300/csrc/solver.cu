@@ -217,8 +217,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     int ti;
     int info[2];
     *converged = false;
-    // FP32 phase: Gram entries carry ~1e-7 relative noise, so a scaled-S_R pivot below 1e-6 is
-    // treated as a dependent direction and dropped; FP64 keeps the reading of the paper (R13).
+    // FP64 keeps the reading of the paper (R13).  An FP32 instantiation (which no solve form
+    // runs) would treat scaled-S_R pivots below 1e-6 as dependent directions: its Gram entries
+    // carry ~1e-7 relative noise.
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
     const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
     bool certified = false;   // Psi_H, Psi_S freshly recomputed in FP64 (mixed form)
@@ -478,7 +479,7 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     std::vector<double> E(w), Eprev;
     SolveBufs<double>& B64 = S->sb;
     HBSD_TRY(alloc_blocks(B64, n, ldw, ldp, m));
-    int it32 = 0, it64 = 0;
+    int it64 = 0;
     bool conv = false;
     if (mixed && S->has_factor) {
         HBSD_TRY(factor_make_fp32(S->F, S->A.dscale.p, st));
@@ -490,10 +491,11 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     }
     k_copy_block<double><<<grid_for(n * w), 256, 0, st>>>(X0, ldx0, w, n, B64.Psi.p, ldw);
     HBSD_LAUNCHED(S);
-    // FP64: the whole solve, or the final check and refinement sweep of the mixed form
-    PhaseRule r64{tol, std::max(0, o.max_outer - it32), false, 0};
+    // one FP64 outer loop in both forms; the mixed form differs inside it (FP32 directions of
+    // step 6(a), double-float Gram and update)
+    PhaseRule r64{tol, std::max(0, o.max_outer), false, 0};
     HBSD_TRY(labpsd_phase<double>(S, B64, C, m, w, ldw, ldp, r64, E, Eprev, &it64, &conv, tm));
-    const int iters = it32 + it64;
+    const int iters = it64;
     stt.iters = iters;
     stt.iters_fp64 = it64;
     tm.flush();

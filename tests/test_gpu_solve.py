@@ -220,7 +220,8 @@ def test_medium_solve_against_stored_oracle():
 
 # ------------------------------------------------------------------ mixed precision form
 def test_small_solve_mixed_precision():
-    """FP32 phase + FP64 refinement sweep: the same eigenpairs as the FP64 oracle at 1e-8."""
+    """Mixed form (FP32 step 6(a), double-float Gram and update): the same eigenpairs as the
+    FP64 oracle at 1e-8."""
     p = pi.small_case(1)
     nev = 16
     X0 = pi.seed_normal_block(1, p.n, 19)
