@@ -152,6 +152,23 @@ def _spmv_ld(A, x):
     return out
 
 
+def test_krylov_bogoliubov_bound_against_brute_force(small_problem):
+    # every computed pair (lam, x) has an exact eigenvalue within ||r||_{S^-1} / ||x||_S,
+    # r = H x - lam S x (the bound for the pencil (H, S)); the computed ones are the lowest
+    p = small_problem
+    nev = 16
+    r = L.labpsd(p, nev, 1e-8, seed=2)
+    H, S = p.scipy_pair()
+    Hd, Sd = H.toarray(), S.toarray()
+    w, _ = _brute(p)
+    Sinv_R = np.linalg.solve(Sd, Hd @ r.X - (Sd @ r.X) * r.lam[None, :])
+    R = Hd @ r.X - (Sd @ r.X) * r.lam[None, :]
+    bound = np.sqrt(np.einsum("ij,ij->j", R, Sinv_R)) / np.sqrt(np.einsum("ij,ij->j", r.X, Sd @ r.X))
+    for j in range(nev):
+        assert np.abs(w - r.lam[j]).min() <= bound[j] * (1 + 1e-6) + 1e-12 * np.abs(w).max()
+    assert np.abs(r.lam - w[:nev]).max() <= 1e-8 * np.abs(w[:nev]).max()
+
+
 def test_exact_invariant_subspace_zero_iterations(small_problem):
     p = small_problem
     w, V = _brute(p)
@@ -243,6 +260,17 @@ def test_minres_minimises_over_krylov_space():
         best = np.linalg.norm(r0 - A @ K @ c)
         x, _, hist = L.minres(lambda v: A @ v, b, x0, 0.0, k)
         assert abs(np.linalg.norm(b - A @ x) - best) <= 1e-9 * np.linalg.norm(r0)
+
+
+def test_minres_residual_history_never_grows():
+    # the iterates minimise the residual over nested Krylov spaces, so the recurrence estimate
+    # is non-increasing (here for an indefinite operator, as in step 6(b))
+    A = _indefinite(40, 11)
+    b = np.random.default_rng(12).standard_normal(40)
+    _, k, hist = L.minres(lambda v: A @ v, b, np.zeros(40), 0.0, 30)
+    assert k == 30
+    assert all(q <= p_ * (1 + 1e-12) for p_, q in zip(hist, hist[1:]))
+    assert hist[-1] < 0.05 * hist[0]
 
 
 def test_minres_zero_steps_when_start_meets_eta():
