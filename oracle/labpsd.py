@@ -39,6 +39,10 @@ solve) as the only library steps.  Readings of points the paper leaves open:
       local part H_loc^(1) - eps_bar S (Eq. ldl) and the nonlocal part enters through the
       Sherman-Morrison-Woodbury steps 1-6 of Sec. 4; every product with H (steps 3, 7 and the
       MINRES operator of 6(b)) applies the full H.
+
+Parity unpinned: the outer iteration count and the per-column MINRES step counts of labpsd are
+properties of the trajectory, pinned only in special cases (0 iterations from an exact invariant
+subspace, the textbook block steepest descent reduction); its eigenpairs are pinned.
 """
 from __future__ import annotations
 
