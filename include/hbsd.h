@@ -14,7 +14,8 @@
  *   - Block vectors on the device are ROW-MAJOR: entry (i, j) of an n x k block with leading
  *     dimension ld (ld >= k, in elements) sits at ptr[i * ld + j].  Every device pointer
  *     must be 16-byte aligned and every ld even, so that a row pair of doubles is one
- *     16-byte access.
+ *     16-byte access.  ld >= k is checked (HBSD_ERR_ARG); alignment and evenness are the
+ *     caller's contract.
  *   - Host arrays (hbsd_csr, X0, outputs of hbsd_solve) are plain C arrays; the caller owns
  *     them; the library copies what it keeps.  Device buffers passed to step-level entry
  *     points are owned by the caller; the library never frees them.

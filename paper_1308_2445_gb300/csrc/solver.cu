@@ -651,9 +651,10 @@ static int m0_of(const Session& S, int nev) { return S.opt.m0 >= 0 ? S.opt.m0 : 
 int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0, double* lambda_dev,
                       double* X_dev, int64_t ldx, int* iters, hbsd_stats* st) {
     return guarded([&]() -> int {
-        if (!h) return fail(HBSD_ERR_ARG, "NULL handle");
+        if (!h || !lambda_dev) return fail(HBSD_ERR_ARG, "NULL handle or lambda");
         Session* S = &h->s;
         if (nev < 1 || !(tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
+        if (X_dev && ldx < nev) return fail(HBSD_ERR_ARG, "ldx < nev");
         const int w = nev + m0_of(*S, nev);
         if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
         if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
@@ -731,6 +732,9 @@ int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out
 }
 
 // ---- step-level entry points ---------------------------------------------------------------
+// A row-major block of `width` columns needs ld >= width (kernels would read past a row).
+static bool ld_ok(int64_t ld, int64_t width) { return width <= 0 || ld >= width; }
+
 int hbsd_res_history(const hbsd_handle* h, double* out, int cap) {
     return guarded([&]() -> int {
         if (!h || cap < 0 || (cap > 0 && !out)) return fail(HBSD_ERR_ARG, "bad arguments");
@@ -752,6 +756,7 @@ int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k, double* 
                    int64_t ldsx) {
     return guarded([&]() -> int {
         if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldx, k) || !ld_ok(ldhx, k) || !ld_ok(ldsx, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return spmm_pair<double>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
     });
 }
@@ -760,6 +765,7 @@ int hbsd_spmm_pair_f32(hbsd_handle* h, const float* X, int64_t ldx, int k, float
                        int64_t ldsx) {
     return guarded([&]() -> int {
         if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldx, k) || !ld_ok(ldhx, k) || !ld_ok(ldsx, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return spmm_pair<float>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
     });
 }
@@ -767,6 +773,7 @@ int hbsd_spmm_pair_f32(hbsd_handle* h, const float* X, int64_t ldx, int k, float
 int hbsd_precond_apply_f32(hbsd_handle* h, const float* R, int64_t ldr, int k, float* P, int64_t ldp) {
     return guarded([&]() -> int {
         if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldr, k) || !ld_ok(ldp, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         HBSD_TRY(factor_make_fp32(h->s.F, h->s.A.dscale.p, h->s.stream));
         HBSD_TRY(factor_solve<float>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
         return nl_smw_correct<float>(&h->s, P, ldp, k, h->s.stream);
@@ -784,6 +791,7 @@ int hbsd_dscale(const hbsd_handle* h, double* d_host) {
 int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e, double* Y, int64_t ldy) {
     return guarded([&]() -> int {
         if (!h || !X || !e || !Y || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldx, k) || !ld_ok(ldy, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return spmm_shifted<double>(&h->s, h->s.A, X, ldx, k, e, Y, ldy, h->s.stream);
     });
 }
@@ -792,6 +800,7 @@ int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double*
                   int m, double* R, int64_t ldr, double* res) {
     return guarded([&]() -> int {
         if (!h || !PsiH || !PsiS || !E || !res || m <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldh, m) || !ld_ok(lds, m) || (R && !ld_ok(ldr, m))) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         Session* S = &h->s;
         HBSD_TRY(S->ws.alloc((size_t)304 * 2 * m + 64));
         return residual<double>(S, PsiH, ldh, PsiS, lds, E, m, R, ldr, S->n, res, nullptr, S->stream);
@@ -801,6 +810,7 @@ int hbsd_residual(hbsd_handle* h, const double* PsiH, int64_t ldh, const double*
 int hbsd_precond_apply(hbsd_handle* h, const double* R, int64_t ldr, int k, double* P, int64_t ldp) {
     return guarded([&]() -> int {
         if (!h || !R || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldr, k) || !ld_ok(ldp, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         HBSD_TRY(factor_solve<double>(&h->s, h->s.F, R, ldr, k, P, ldp, h->s.stream));
         return nl_smw_correct<double>(&h->s, P, ldp, k, h->s.stream);
     });
@@ -810,6 +820,7 @@ int hbsd_minres(hbsd_handle* h, const double* R, int64_t ldr, const double* e, i
                 double* P, int64_t ldp, int* steps) {
     return guarded([&]() -> int {
         if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldr, k) || !ld_ok(ldp, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         Session* S = &h->s;
         HBSD_TRY(S->ws.alloc((size_t)304 * 2 * std::max(k, 1) + 64));
         return minres_batch<double>(S, R, ldr, e, k, eta, max_minres, P, ldp, steps, nullptr, S->stream);
@@ -820,6 +831,7 @@ int hbsd_onestep(hbsd_handle* h, const double* R, int64_t ldr, const double* e, 
                  double* P, int64_t ldp, int* steps) {
     return guarded([&]() -> int {
         if (!h || !R || !e || !P || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldr, k) || !ld_ok(ldp, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         Session* S = &h->s;
         return minres_batch<double>(S, R, ldr, e, k, eta, max_steps, P, ldp, steps, nullptr, S->stream,
                                     HBSD_LOCAL_ONESTEP);
@@ -837,6 +849,7 @@ int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, cons
               int q, double* HR, double* SR, void* stream) {
     return guarded([&]() -> int {
         if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldz, q) || !ld_ok(ldzh, q) || !ld_ok(ldzs, q)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         Session* S = scratch_session();
         const int tiles = ceil_div(q, 32);
         HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + 1024));
@@ -849,6 +862,7 @@ int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ld
                       int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream) {
     return guarded([&]() -> int {
         if (!Z || !ZH || !ZS || !HR || !SR) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldz, q) || !ld_ok(ldzh, q) || !ld_ok(ldzs, q)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return gram_noalloc(Z, ldz, ZH, ldzh, ZS, ldzs, n, q, HR, SR, (cudaStream_t)stream);
     });
 }
@@ -872,6 +886,7 @@ int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double*
 int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
     return guarded([&]() -> int {
         if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldz, q)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return update2<double>(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream);
     });
 }
@@ -880,6 +895,7 @@ int hbsd_gram_df64(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh,
                    int64_t n, int q, double* HR, double* SR, void* stream) {
     return guarded([&]() -> int {
         if (!Z || !ZH || !ZS || !HR || !SR || n <= 0 || q <= 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldz, q) || !ld_ok(ldzh, q) || !ld_ok(ldzs, q)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return gram2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, ZH, ldzh, nullptr, 0, ZS, ldzs, nullptr, 0, n, HR,
                           SR, (cudaStream_t)stream);
     });
@@ -888,6 +904,7 @@ int hbsd_gram_df64(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh,
 int hbsd_update_df64(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k, void* stream) {
     return guarded([&]() -> int {
         if (!Z || !W || n <= 0 || q <= 0 || k <= 0 || k > q) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldz, q)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return update2_df64(scratch_session(), Z, ldz, q, nullptr, 0, 0, n, W, k, (cudaStream_t)stream, true);
     });
 }

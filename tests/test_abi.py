@@ -144,3 +144,22 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
         hbsd.lib()
     with pytest.raises(RuntimeError, match="missing"):
         hbsd.options_default()
+
+
+def test_step_entry_points_refuse_a_short_leading_dimension(lib):
+    # checked before any device work: a row-major block of q columns needs ld >= q
+    from paper_1308_2445_gb300 import hbsd
+    import ctypes as C
+    buf = (C.c_double * 64)()
+    p = C.cast(buf, C.POINTER(C.c_double))
+    n, q = 8, 4
+    assert lib.hbsd_update(p, 3, n, q, p, 2, None) == hbsd.HBSD_ERR_ARG
+    assert b"leading dimension" in lib.hbsd_last_error()
+    assert lib.hbsd_update_df64(p, 3, n, q, p, 2, None) == hbsd.HBSD_ERR_ARG
+    assert lib.hbsd_gram(p, q, p, 2, p, q, n, q, p, p, None) == hbsd.HBSD_ERR_ARG
+    assert b"leading dimension" in lib.hbsd_last_error()
+    assert lib.hbsd_gram_df64(p, q, p, q, p, 1, n, q, p, p, None) == hbsd.HBSD_ERR_ARG
+    assert lib.hbsd_gram_noalloc(p, 2, p, q, p, q, n, q, p, p, None) == hbsd.HBSD_ERR_ARG
+    # k > q is refused as before
+    assert lib.hbsd_update(p, q, n, q, p, q + 1, None) == hbsd.HBSD_ERR_ARG
+    assert b"bad arguments" in lib.hbsd_last_error()
