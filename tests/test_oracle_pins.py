@@ -79,6 +79,47 @@ def test_closed_form_bloch_complex():
     assert np.abs(r.lam - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
+def test_complex_oracle_agrees_with_the_real_equivalent_pencil():
+    # H = Hr + i Hi, S = Sr + i Si Hermitian is equivalent to the real symmetric pencil
+    # ([Hr, -Hi; Hi, Hr], [Sr, -Si; Si, Sr]) of size 2n, every eigenvalue twice (x and i x): the
+    # oracle's complex solve must agree with its real solve of that pencil (a missing conjugate
+    # anywhere in the complex path breaks it), and the complex span of V[:n] + i V[n:] over the
+    # 2 nev real vectors must have dimension nev and hold the complex eigenvectors
+    import dataclasses
+    import scipy.sparse as sp
+    k = (0.5 * np.pi, -0.5 * np.pi, 0.5 * np.pi)
+    q = pi.generate(8, 2, 2, 0.25, 1, kpt=k)
+    nev = 16
+    w = nev + L.default_m0(nev)
+    rc = L.labpsd(q, nev, 1e-8, X0=pi.seed_normal_block(4, q.n, w) + 1j * pi.seed_normal_block(5, q.n, w))
+    H, S = q.scipy_pair()
+
+    def blocks(A):
+        Ar = sp.csr_matrix((A.data.real.copy(), A.indices, A.indptr), shape=A.shape)
+        Ai = sp.csr_matrix((A.data.imag.copy(), A.indices, A.indptr), shape=A.shape)
+        B = sp.bmat([[Ar, -Ai], [Ai, Ar]], format="csr")
+        B.sort_indices()
+        return B
+    Hb, Sb = blocks(H.tocsr()), blocks(S.tocsr())
+    assert np.array_equal(Hb.indices, Sb.indices) and abs(Hb - Hb.T).max() == 0.0
+    qr = dataclasses.replace(q, n=2 * q.n, row_ptr=Hb.indptr.astype(np.int64), col_idx=Hb.indices.astype(np.int32),
+                             h_val=Hb.data, s_val=Sb.data, kpt=None,
+                             dof_node=np.concatenate([q.dof_node, q.dof_node]).astype(np.int32),
+                             dof_cluster=np.concatenate([q.dof_cluster, q.dof_cluster]).astype(np.int32))
+    w2 = 2 * nev + L.default_m0(2 * nev)
+    rr = L.labpsd(qr, 2 * nev, 1e-8, X0=pi.seed_normal_block(6, qr.n, w2))
+    assert rc.converged and rr.converged
+    scale = np.abs(rc.lam).max()
+    assert np.abs(rr.lam[0::2] - rc.lam).max() <= 1e-12 * scale
+    assert np.abs(rr.lam[1::2] - rc.lam).max() <= 1e-12 * scale
+    Z = rr.X[:q.n] + 1j * rr.X[q.n:]
+    g = np.sort(np.linalg.eigvalsh(Z.conj().T @ (S @ Z)))[::-1]
+    assert g[nev - 1] > 1.0 and g[nev] < 1e-10                        # complex rank nev
+    # each complex eigenvector of the native solve lies in that span (S-projection residual)
+    Q = Z @ np.linalg.pinv(Z.conj().T @ (S @ Z), rcond=1e-10) @ (Z.conj().T @ (S @ rc.X))
+    assert np.abs(Q - rc.X).max() <= 1e-6 * np.abs(rc.X).max()
+
+
 # ------------------------------------------------------------------ brute force
 def _brute(p):
     H, S = p.scipy_pair()
