@@ -210,6 +210,22 @@ def test_krylov_bogoliubov_bound_against_brute_force(small_problem):
     assert np.abs(r.lam - w[:nev]).max() <= 1e-8 * np.abs(w[:nev]).max()
 
 
+def test_locking_and_localisation_bookkeeping(small_problem):
+    # remarks 3-4: only unconverged columns among the first m get a direction (soft locking,
+    # R9); of those, the localized ones are refined, at most max_minres steps each; nothing is
+    # localized at the first iteration (R10, no previous Ritz value)
+    p = small_problem
+    m = 16
+    r = L.labpsd(p, m, 1e-8, seed=4)
+    assert r.converged and len(r.n_precond) == len(r.n_local) == len(r.minres_steps) == r.iters
+    assert r.n_local[0] == 0
+    for npc, nloc, st in zip(r.n_precond, r.n_local, r.minres_steps):
+        assert 0 < npc <= m and 0 <= nloc <= npc and st.size == nloc
+        assert np.all((st >= 0) & (st <= 20))
+    assert r.n_precond[-1] < m                      # converged columns left the block of directions
+    assert sum(r.n_local) > 0
+
+
 def test_exact_invariant_subspace_zero_iterations(small_problem):
     p = small_problem
     w, V = _brute(p)
