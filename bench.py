@@ -53,6 +53,9 @@ def parse():
                     help="step 6(b): MINRES (default) or the first-order one-step refinement (Sec. 6)")
     ap.add_argument("--workload", default="medium", choices=["medium", "medium-nonlocal"],
                     help="medium-nonlocal: the same problem with the nonlocal term H_nl = F G F^T (Sec. 4)")
+    ap.add_argument("--m0", type=int, default=-1,
+                    help="guard columns (remark 1; default max(3, ceil(nev/10))); the medium workload "
+                         "has a stored oracle run for m0 = 21")
     return ap.parse_args()
 
 
@@ -117,10 +120,20 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def golden(workload="medium"):
+def golden(workload="medium", m0=-1):
     name = "medium_nonlocal_seed1.json" if workload == "medium-nonlocal" else "medium_seed1.json"
-    with open(os.path.join(ROOT, "tests", "golden", name)) as f:
+    if m0 >= 0:
+        name = f"{workload.replace('-', '_')}_m0_{m0}_seed1.json"
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        raise SystemExit(f"no stored oracle run for workload {workload} with m0 = {m0} "
+                         f"(tests/golden/make_golden.py writes one)")
+    with open(path) as f:
         return json.load(f)
+
+
+def m0_of(nev, m0):
+    return m0 if m0 >= 0 else max(3, -(-nev // 10))
 
 
 def problem(workload):
@@ -128,13 +141,14 @@ def problem(workload):
     return pi.medium_nonlocal_case(1) if workload == "medium-nonlocal" else pi.medium_case(1)
 
 
-def cpu_baseline(nev, W_iters=2, workload="medium"):
+def cpu_baseline(nev, W_iters=2, workload="medium", m0=-1):
     """Time the CPU oracle, as it stands, on a bounded sample of the same workload."""
     import numpy as np
     from oracle import labpsd as L
     from paper_1308_2445_gb300 import pufe_inputs as pi
     p = problem(workload)
-    w = nev + L.default_m0(nev)
+    g = golden(workload, m0)
+    w = nev + m0_of(nev, m0)
     X0 = pi.seed_normal_block(1, p.n, w)
     t0 = time.perf_counter()
     Hs, S, s0 = L.make_shifted(p)
@@ -142,10 +156,9 @@ def cpu_baseline(nev, W_iters=2, workload="medium"):
     t_factor = time.perf_counter() - t0
     marks = []
     t1 = time.perf_counter()
-    L.labpsd(p, nev, TOL, X0=X0, precond=K, opts=L.Options(max_outer=W_iters),
+    L.labpsd(p, nev, TOL, X0=X0, precond=K, opts=L.Options(max_outer=W_iters, m0=m0_of(nev, m0)),
              on_iteration=lambda it, res: marks.append(time.perf_counter()))
     per_iter = (marks[-1] - marks[0]) / max(1, len(marks) - 1) if len(marks) > 1 else marks[0] - t1
-    g = golden(workload)
     t_solve = per_iter * g["iters"]
     return {"value": nev / t_solve, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"medium workload: library factorisation ({t_factor:.1f} s, excluded like value's) + initial "
@@ -163,23 +176,24 @@ def run_reference(args):
     from paper_1308_2445_gb300 import pufe_inputs as pi
     nev = pi.MEDIUM_NEV
     p = problem(args.workload)
-    X0 = pi.seed_normal_block(1, p.n, nev + L.default_m0(nev))
+    g = golden(args.workload, args.m0)
+    m0 = m0_of(nev, args.m0)
+    X0 = pi.seed_normal_block(1, p.n, nev + m0)
     Hs, S, s0 = L.make_shifted(p)
     K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
     marks = [time.perf_counter()]
-    L.labpsd(p, nev, TOL, X0=X0, precond=K, opts=L.Options(max_outer=args.warmup + args.steps),
+    L.labpsd(p, nev, TOL, X0=X0, precond=K, opts=L.Options(max_outer=args.warmup + args.steps, m0=m0),
              on_iteration=lambda it, res: marks.append(time.perf_counter()))
     d = [marks[i + 1] - marks[i] for i in range(len(marks) - 1)]
     timed = d[args.warmup:] or d
     per_iter = sum(timed) / len(timed)
-    g = golden(args.workload)
     value = nev / (per_iter * g["iters"])
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "eigenpairs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_iter * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NL if args.workload == "medium-nonlocal" else WORKLOAD, "n": p.n,
-                       "nnz": p.nnz, "nev": nev, "arithmetic": "fp64 (the CPU oracle)",
+                       "nnz": p.nnz, "nev": nev, "m0": m0, "arithmetic": "fp64 (the CPU oracle)",
                        "step": "one BPSD iteration of the CPU oracle; value scaled to the oracle's full solve"},
             "cpu_baseline": {"value": value, "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{len(timed)} timed BPSD iterations after {args.warmup} warm-up, "
@@ -208,12 +222,12 @@ def main():
     nev = pi.MEDIUM_NEV
     p = problem(args.workload)
     nl_nnz = int(np.count_nonzero(p.F)) if p.F is not None else 0
-    w = nev + max(3, -(-nev // 10))
+    w = nev + m0_of(nev, args.m0)
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     prec = hbsd.PRECISION_MIXED if args.precision == "mixed" else hbsd.PRECISION_FP64
     lsol = hbsd.LOCAL_ONESTEP if args.local_solver == "onestep" else hbsd.LOCAL_MINRES
-    sess = hbsd.Session.from_problem(p, stream=stream.cuda_stream, precision=prec, local_solver=lsol)
+    sess = hbsd.Session.from_problem(p, stream=stream.cuda_stream, precision=prec, local_solver=lsol, m0=args.m0)
     torch.cuda.synchronize()
     t_create = time.perf_counter() - t0
     X0h = torch.from_numpy(pi.seed_normal_block(1, p.n, w)).pin_memory()
@@ -259,7 +273,7 @@ def main():
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         ta = time.perf_counter()
-        s2 = hbsd.Session.from_problem(p, precision=prec, local_solver=lsol)
+        s2 = hbsd.Session.from_problem(p, precision=prec, local_solver=lsol, m0=args.m0)
         lam_h, X_h, it2, rc2, st2 = s2.solve(nev, TOL, X0=X0n)
         s2.close()
         torch.cuda.synchronize()
@@ -302,7 +316,8 @@ def main():
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_NL if args.workload == "medium-nonlocal" else WORKLOAD, "n": p.n,
-                       "nnz": p.nnz, "nev": nev, "precision": args.precision, "nonlocal_nnz": nl_nnz,
+                       "nnz": p.nnz, "nev": nev, "m0": m0_of(nev, args.m0), "precision": args.precision,
+                       "nonlocal_nnz": nl_nnz,
                        "local_solver": args.local_solver,
                        "iters": st["iters"], "iters_fp64": st["iters_fp64"], "t_factor_ms": st["t_factor_ms"],
                        "nnz_L": st["nnz_L"], "res_max": st["res_max"], "rr_fallbacks": st["rr_fallbacks"],
@@ -312,7 +327,7 @@ def main():
             "roofline": roof, "e2e": e2e, "gpu_launches": int(sum(s["gpu_launches"] for s in stats)),
             "clocks": ck}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(nev, workload=args.workload)
+        line["cpu_baseline"] = cpu_baseline(nev, workload=args.workload, m0=args.m0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -2,6 +2,8 @@
 
   python tests/golden/make_golden.py medium            -> tests/golden/medium_seed1.json
   python tests/golden/make_golden.py medium_nonlocal   -> tests/golden/medium_nonlocal_seed1.json
+  python tests/golden/make_golden.py medium_m0 21      -> tests/golden/medium_m0_21_seed1.json
+                                                          (the same solve with m0 = 21 guard columns)
 
 The medium workload (32^3 Q1 elements, 8 atoms, 4 enrichment dofs per node, nev = 64) takes the
 oracle a few minutes, too long to rerun inside the test suite; every value in the file comes
@@ -19,10 +21,10 @@ from oracle import labpsd as L  # noqa: E402
 from paper_1308_2445_gb300 import pufe_inputs as pi  # noqa: E402
 
 
-def medium(seed=1, nonlocal_term=False):
+def medium(seed=1, nonlocal_term=False, m0=-1):
     p = pi.medium_nonlocal_case(seed) if nonlocal_term else pi.medium_case(seed)
     t0 = time.time()
-    r = L.labpsd(p, pi.MEDIUM_NEV, 1e-8, seed=seed)
+    r = L.labpsd(p, pi.MEDIUM_NEV, 1e-8, seed=seed, opts=L.Options(m0=None if m0 < 0 else m0))
     name = "32^3 Q1, 8 atoms, 4 enrichment dofs/node, r_c 0.15"
     if nonlocal_term:
         name += ", s+p projectors per atom (k = 32)"
@@ -30,7 +32,8 @@ def medium(seed=1, nonlocal_term=False):
                 nev=pi.MEDIUM_NEV, tol=1e-8, eps_bar=p.eps_bar, lam=[float(x) for x in r.lam],
                 E_all=[float(x) for x in r.E_all], iters=r.iters, converged=bool(r.converged),
                 res_history=[float(x) for x in r.res_history], minres_total=int(sum(int(s.sum()) for s in r.minres_steps)),
-                rr_fallbacks=r.rr_fallbacks, oracle_seconds=time.time() - t0)
+                rr_fallbacks=r.rr_fallbacks, m0=m0 if m0 >= 0 else L.default_m0(pi.MEDIUM_NEV),
+                oracle_seconds=time.time() - t0)
 
 
 if __name__ == "__main__":
@@ -38,5 +41,11 @@ if __name__ == "__main__":
     if which in ("medium", "medium_nonlocal"):
         out = medium(1, nonlocal_term=which == "medium_nonlocal")
         with open(os.path.join(HERE, f"{which}_seed1.json"), "w") as f:
+            json.dump(out, f, indent=1)
+        print("iters", out["iters"], "seconds", out["oracle_seconds"])
+    elif which == "medium_m0":
+        m0 = int(sys.argv[2])
+        out = medium(1, m0=m0)
+        with open(os.path.join(HERE, f"medium_m0_{m0}_seed1.json"), "w") as f:
             json.dump(out, f, indent=1)
         print("iters", out["iters"], "seconds", out["oracle_seconds"])
