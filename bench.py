@@ -168,6 +168,54 @@ def cpu_baseline(nev, W_iters=2, workload="medium", m0=-1):
             "t_factor_s": t_factor, "t_iter_s": per_iter}
 
 
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s when the peaks file is present, else the
+    profiling recipe's fallback figure (said so in the result)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured HBM copy bandwidth (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback HBM figure (6.8 TB/s; no measured peaks file)"
+
+
+def roofline_object(st, nnz, nl_nnz, peak64, precision, workload):
+    """Roofline of the dominant step class, from the solve's CUDA-event step times and the
+    algorithmic work per unit.  FP64 classes are bound by the FP64 FMA rate (measured in the same
+    run, peak64 in FLOP/s); the FP32 sweeps of the mixed form by HBM (their panels, 4 bytes per
+    entry, read once per sweep: 8 nnz(L) bytes per call)."""
+    classes = {
+        "precond": (st["t_precond_ms"], 4.0 * st["nnz_L"] * st["precond_cols"], st["precond_calls"],
+                    "supernodal triangular solves of step 6(a): 2 FMA per factor entry per column"),
+        "matvec": (st["t_matvec_ms"], (4.0 * nnz + 4.0 * nl_nnz) * st["matvec_cols"], None,
+                   "fused SpMM of steps 3/7: 2 FMA (h and s) per nonzero per column"
+                   + (" + 2 FMA per F entry (F^T X and F Z)" if nl_nnz else "")),
+        "minres": (st["t_local_ms"], (4.0 * nnz + 4.0 * nl_nnz) * st["minres_spmm_cols"], None,
+                   "MINRES of step 6(b): shifted fused SpMM, 2 FMA per nonzero per column"
+                   + (" + 2 FMA per F entry" if nl_nnz else "")),
+    }
+    dom = max(classes, key=lambda k: classes[k][0])
+    t_ms, flops, _, what = classes[dom]
+    step_ms = {k: st[f"t_{k}_ms"] for k in ("matvec", "resid", "precond", "local", "gram", "rr", "update")}
+    if dom == "precond" and precision == "mixed":
+        peak, source = hbm_peak_gbs()
+        achieved = 8.0 * st["nnz_L"] * st["precond_calls"] / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": dom,
+                "what": "FP32 supernodal sweeps of step 6(a): the FP32 panels read once per sweep, 8 nnz(L) bytes per call",
+                "peak_source": source, "step_ms": step_ms}
+    achieved = flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+    traffic = None
+    if dom == "minres" and st["local_calls"] > 0 and workload == "medium":
+        traffic = MINRES_DRAM_BYTES_PER_COLUMN_PRODUCT * st["minres_spmm_cols"] / st["local_calls"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / (peak64 / 1e12) if peak64 > 0 else None, "traffic": traffic,
+            "traffic_note": "DRAM bytes per launch: ncu bytes per column product x the average launch's column products"
+            if traffic is not None else None,
+            "kernel": dom, "what": what, "peak_source": "FP64 FMA probe (hbsd_probe_peak) measured in this run",
+            "step_ms": step_ms}
+
+
 def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
@@ -288,28 +336,7 @@ def main():
 
     # ---- roofline of the dominant step class (device time from the solve's CUDA events) ----
     peak64 = hbsd.probe_peak(0, stream.cuda_stream)
-    classes = {
-        "precond": (st["t_precond_ms"], 4.0 * st["nnz_L"] * st["precond_cols"], st["precond_calls"],
-                    "supernodal triangular solves of step 6(a): 2 FMA per factor entry per column"),
-        "matvec": (st["t_matvec_ms"], (4.0 * p.nnz + 4.0 * nl_nnz) * st["matvec_cols"], None,
-                   "fused SpMM of steps 3/7: 2 FMA (h and s) per nonzero per column"
-                   + (" + 2 FMA per F entry (F^T X and F Z)" if nl_nnz else "")),
-        "minres": (st["t_local_ms"], (4.0 * p.nnz + 4.0 * nl_nnz) * st["minres_spmm_cols"], None,
-                   "MINRES of step 6(b): shifted fused SpMM, 2 FMA per nonzero per column"
-                   + (" + 2 FMA per F entry" if nl_nnz else "")),
-    }
-    dom = max(classes, key=lambda k: classes[k][0])
-    t_ms, flops, _, what = classes[dom]
-    achieved = flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
-    traffic = None
-    if dom == "minres" and st["local_calls"] > 0 and args.workload == "medium":
-        traffic = MINRES_DRAM_BYTES_PER_COLUMN_PRODUCT * st["minres_spmm_cols"] / st["local_calls"]
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / (peak64 / 1e12) if peak64 > 0 else None, "traffic": traffic,
-            "traffic_note": "DRAM bytes per launch: ncu bytes per column product x the average launch's column products"
-            if traffic is not None else None,
-            "kernel": dom, "what": what, "peak_source": "FP64 FMA probe (hbsd_probe_peak) measured in this run",
-            "step_ms": {k: st[f"t_{k}_ms"] for k in ("matvec", "resid", "precond", "local", "gram", "rr", "update")}}
+    roof = roofline_object(st, p.nnz, nl_nnz, peak64, args.precision, args.workload)
 
     line = {"metric": METRIC, "value": value,
             "unit": "eigenpairs/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
