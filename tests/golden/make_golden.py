@@ -4,6 +4,8 @@
   python tests/golden/make_golden.py medium_nonlocal   -> tests/golden/medium_nonlocal_seed1.json
   python tests/golden/make_golden.py medium_m0 21      -> tests/golden/medium_m0_21_seed1.json
                                                           (the same solve with m0 = 21 guard columns)
+  python tests/golden/make_golden.py medium_nonlocal_m0 21
+                                                       -> tests/golden/medium_nonlocal_m0_21_seed1.json
 
 The medium workload (32^3 Q1 elements, 8 atoms, 4 enrichment dofs per node, nev = 64) takes the
 oracle a few minutes, too long to rerun inside the test suite; every value in the file comes
@@ -43,9 +45,9 @@ if __name__ == "__main__":
         with open(os.path.join(HERE, f"{which}_seed1.json"), "w") as f:
             json.dump(out, f, indent=1)
         print("iters", out["iters"], "seconds", out["oracle_seconds"])
-    elif which == "medium_m0":
+    elif which in ("medium_m0", "medium_nonlocal_m0"):
         m0 = int(sys.argv[2])
-        out = medium(1, m0=m0)
-        with open(os.path.join(HERE, f"medium_m0_{m0}_seed1.json"), "w") as f:
+        out = medium(1, nonlocal_term=which == "medium_nonlocal_m0", m0=m0)
+        with open(os.path.join(HERE, f"{which}_{m0}_seed1.json"), "w") as f:
             json.dump(out, f, indent=1)
         print("iters", out["iters"], "seconds", out["oracle_seconds"])

@@ -1,11 +1,13 @@
-"""The stored oracle runs of the 32^3 workload agree with each other: the eigenvalues do not
-depend on the number of guard columns (remark 1), so the runs with m0 = 7 and m0 = 21 must give
+"""The stored oracle runs of the 32^3 workloads (with and without the nonlocal term) agree with
+each other: the eigenvalues do not depend on the number of guard columns (remark 1), so the runs
+with m0 = 7 and m0 = 21 must give
 the same lowest 64 eigenvalues to the accuracy a 1e-8 residual fixes.  Each file records what
 it is (workload, seed, nev, m0, iterations) as written by tests/golden/make_golden.py."""
 import json
 import os
 
 import numpy as np
+import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -15,8 +17,9 @@ def load(name):
         return json.load(f)
 
 
-def test_guard_columns_change_the_path_not_the_answer():
-    a, b = load("medium_seed1.json"), load("medium_m0_21_seed1.json")
+@pytest.mark.parametrize("base", ["medium", "medium_nonlocal"])
+def test_guard_columns_change_the_path_not_the_answer(base):
+    a, b = load(f"{base}_seed1.json"), load(f"{base}_m0_21_seed1.json")
     assert a["n"] == b["n"] and a["nev"] == b["nev"] == 64 and b["m0"] == 21
     assert a["converged"] and b["converged"]
     la, lb = np.array(a["lam"]), np.array(b["lam"])
