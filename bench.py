@@ -30,8 +30,8 @@ sys.path.insert(0, ROOT)
 
 TOL = 1e-8
 # DRAM bytes (read + write) per column product of the fused MINRES kernel, from one ncu capture of a
-# 57-column, 99-step launch on this workload (profiles/k_minres_medium.md); the roofline's traffic
-# scales it by the column products of the average launch of the timed solve
+# 57-column, 99-step launch on the 32^3 workload; the roofline's traffic scales it by the column
+# products of the average launch of the timed solve
 MINRES_DRAM_BYTES_PER_COLUMN_PRODUCT = (1212.506368e6 + 438.241536e6) / 156
 METRIC = "eigenpairs/s to 1e-8 residual (LABPSD, hybrid preconditioner)"
 WORKLOAD = "32^3 periodic Q1 elements, 8 atoms Z=4, 4 Gaussian enrichment dofs/node within r_c=0.15, nev=64, tol=1e-8"
@@ -264,7 +264,6 @@ def main():
     from paper_1308_2445_gb300 import build_lib
     if not os.path.exists(build_lib.LIB):
         build_lib.build()
-    from oracle import labpsd as L  # only for default_m0 (a formula), no oracle arithmetic here
     from paper_1308_2445_gb300 import hbsd, pufe_inputs as pi
 
     nev = pi.MEDIUM_NEV

@@ -258,12 +258,15 @@ int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, cons
 /* Allocation-free form of hbsd_gram, for callers that must not allocate device memory:
  * a serving loop whose per-request path may not call cudaMalloc / cudaFree (both can
  * synchronise the whole device and stall the requests already in flight), or a host whose
- * memory pool owns all device memory up front.  It computes exactly what hbsd_gram computes,
- * but its scratch is a file-scope device array of 2^21 doubles (16 MiB) that every device which
- * loads the library holds until the process exits; the paper has no counterpart.  Sizes:
- * q <= 1024 (2 q^2 scratch doubles per row chunk); a larger q returns HBSD_ERR_ARG.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current, so make that first call before any stream capture.  All calls share the one array:
+ * memory pool owns all device memory up front.  It computes what hbsd_gram computes, the same
+ * result up to rounding (for large q it sums fewer row chunks, so the order of the partial sums
+ * differs), but its scratch is a file-scope device array of 2^21 doubles (16 MiB) that every
+ * device which loads the library holds until the process exits; the paper has no counterpart.
+ * Sizes: q <= 1024 (2 q^2 scratch doubles per row chunk); a larger q returns HBSD_ERR_ARG
+ * before any other argument check.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current and keeps it, so make that first call
+ * before any stream capture, and do not use the library across a cudaDeviceReset (the array may
+ * then live at another address).  All calls share the one array:
  * calls that overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller; each call overwrites every scratch element it reads, so nothing
  * carries over from the previous call.  Asynchronous on stream; no allocation, no free. */

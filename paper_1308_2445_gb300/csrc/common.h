@@ -208,6 +208,8 @@ template <class T>
 int gram2(Session* s, const T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1, const T* H0,
           int64_t ldh0, const T* H1, int64_t ldh1, const T* S0, int64_t lds0, const T* S1, int64_t lds1,
           int64_t n, double* HR, double* SR, cudaStream_t st);
+// largest q the allocation-free Gram's static scratch holds (2 q^2 doubles per row chunk, 2^21 in all)
+constexpr int GRAM_NOALLOC_MAX_Q = 1024;
 int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
                  int64_t n, int q, double* HR, double* SR, cudaStream_t st);
 template <class T>

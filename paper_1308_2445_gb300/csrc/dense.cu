@@ -267,7 +267,8 @@ static __device__ __align__(256) double g_gram_static[GRAM_STATIC_DOUBLES];
 
 // Device address of g_gram_static on the current device, looked up once per device.  In host
 // code the symbol names a host-side stand-in, not device memory, so kernels must be given this
-// address instead.
+// address instead.  The cached address belongs to the device's primary context: after a
+// cudaDeviceReset the module may load elsewhere, so the library must not be used across a reset.
 static int gram_static_address(double** out) {
     static std::mutex mu;
     static double* addr[64] = {};
@@ -291,7 +292,7 @@ int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, c
                  int64_t n, int q, double* HR, double* SR, cudaStream_t st) {
     if (q <= 0 || n <= 0) return fail(HBSD_ERR_ARG, "gram_noalloc: need n > 0 and q > 0");
     const size_t per_chunk = (size_t)2 * q * q;
-    if (per_chunk > GRAM_STATIC_DOUBLES)
+    if (q > GRAM_NOALLOC_MAX_Q || per_chunk > GRAM_STATIC_DOUBLES)
         return fail(HBSD_ERR_ARG, "gram_noalloc: q = " + std::to_string(q) +
                                       " exceeds the static scratch (2 q^2 <= 2^21 doubles, q <= 1024)");
     double* scratch = nullptr;

@@ -862,6 +862,10 @@ int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ld
                       int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream) {
     return guarded([&]() -> int {
         if (!Z || !ZH || !ZS || !HR || !SR) return fail(HBSD_ERR_ARG, "bad arguments");
+        // the scratch limit is reported before any other size check, whatever the ld
+        if (q > GRAM_NOALLOC_MAX_Q)
+            return fail(HBSD_ERR_ARG, "gram_noalloc: q = " + std::to_string(q) +
+                                          " exceeds the static scratch (2 q^2 <= 2^21 doubles, q <= 1024)");
         if (!ld_ok(ldz, q) || !ld_ok(ldzh, q) || !ld_ok(ldzs, q)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return gram_noalloc(Z, ldz, ZH, ldzh, ZS, ldzs, n, q, HR, SR, (cudaStream_t)stream);
     });

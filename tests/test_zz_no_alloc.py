@@ -42,7 +42,10 @@ def _gram(fn, Z, ZH, ZS):
 def test_noalloc_gram_matches_gram_on_consecutive_calls():
     from paper_1308_2445_gb300 import hbsd, pufe_inputs as pi
     lib = hbsd.lib()
-    for call, (n, q) in enumerate([(47620, 135), (4000, 71), (47620, 135)]):
+    # q = 135 and 71 keep hbsd_gram's row chunks; q = 400 and 1024 make the static scratch cut
+    # the chunk count (1 chunk at q = 1024, the largest q it holds)
+    for call, (n, q) in enumerate([(47620, 135), (4000, 71), (47620, 135), (20000, 400), (4096, 1024),
+                                   (4096, 1024)]):
         Z = _block(pi.seed_normal_block(10 + call, n, q))
         ZH = _block(pi.seed_normal_block(20 + call, n, q))
         ZS = _block(pi.seed_normal_block(30 + call, n, q))
@@ -56,8 +59,14 @@ def test_noalloc_gram_matches_gram_on_consecutive_calls():
 def test_noalloc_gram_rejects_sizes_beyond_its_scratch():
     from paper_1308_2445_gb300 import hbsd
     lib = hbsd.lib()
-    t = torch.zeros(8, 2, dtype=torch.float64, device="cuda")
+    # leading dimensions that fit q = 1025, so only the scratch limit can refuse the call; it is
+    # refused on the host before any launch (nothing is read or written)
+    t = torch.zeros(4, 1026, dtype=torch.float64, device="cuda")
     p = t.data_ptr()
+    rc = lib.hbsd_gram_noalloc(p, 1026, p, 1026, p, 1026, 4, 1025, p, p, None)
+    assert rc == hbsd.HBSD_ERR_ARG
+    assert b"exceeds the static scratch" in lib.hbsd_last_error()
+    # the same refusal with a leading dimension below q: the scratch limit is reported first
     rc = lib.hbsd_gram_noalloc(p, 2, p, 2, p, 2, 4, 1025, p, p, None)
     assert rc == hbsd.HBSD_ERR_ARG
     assert b"exceeds the static scratch" in lib.hbsd_last_error()
