@@ -218,6 +218,49 @@ def test_medium_solve_against_stored_oracle():
     assert np.abs(hist[:10] / np.array(g["res_history"][:10]) - 1).max() <= 1e-3
 
 
+# ------------------------------------------------------------------ 32^3 against a live oracle run
+@pytest.fixture(scope="module")
+def medium_m0_21_oracle():
+    """The oracle's solve of the 32^3 workload with m0 = 21 guard columns (25 outer iterations,
+    about 1.5 min on 8-16 host cores), run here so that its eigenvectors can be compared; its
+    eigenvalues and iteration count must reproduce the stored run of the same solve."""
+    g = json.load(open(os.path.join(HERE, "golden", "medium_m0_21_seed1.json")))
+    p = pi.medium_case(1)
+    nev, m0 = g["nev"], g["m0"]
+    X0 = pi.seed_normal_block(1, p.n, nev + m0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0, opts=L.Options(m0=m0))
+    assert ro.converged and ro.iters == g["iters"]
+    assert np.abs(ro.lam - np.array(g["lam"])).max() <= 1e-12 * np.abs(ro.lam).max()
+    return p, nev, m0, X0, ro
+
+
+@pytest.mark.parametrize("form", ["fp64", "mixed"])
+def test_medium_m0_21_eigenpairs_and_iterations_against_the_oracle(medium_m0_21_oracle, form):
+    """32^3 workload, nev = 64, m0 = 21: eigenvalues to 1e-9 max|lambda|, the S-principal angle
+    between span X(:, :j) of GPU and oracle <= 1e-6 at every gap > 1e-2 max|lambda| (a cluster is
+    compared only as a whole), outer iterations within +-1 of the oracle's, X^T S X = I and
+    Res_max <= tol recomputed on the host."""
+    import scipy.sparse as sp
+    from subspace import gap_indices, s_angle
+    p, nev, m0, X0, ro = medium_m0_21_oracle
+    prec = hb().PRECISION_MIXED if form == "mixed" else hb().PRECISION_FP64
+    s = hb().Session.from_problem(p, precision=prec, m0=m0)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    assert rc == 0
+    scale = np.abs(ro.lam).max()
+    assert np.abs(lam - ro.lam).max() <= 1e-9 * scale
+    assert abs(it - ro.iters) <= 1, (form, it, ro.iters)
+    H, S = p.scipy_pair()
+    S = sp.csr_matrix(S)
+    assert np.abs(X.T @ (S @ X) - np.eye(nev)).max() <= 1e-10
+    assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+    js = gap_indices(ro.lam, nev)
+    assert len(js) >= 3
+    worst = max(s_angle(X[:, :j], ro.X[:, :j], S) for j in js)
+    assert worst <= 1e-6, (form, worst)
+    s.close()
+
+
 # ------------------------------------------------------------------ mixed precision form
 def test_small_solve_mixed_precision():
     """Mixed form (FP32 step 6(a), double-float Gram and update): the same eigenpairs as the
