@@ -152,13 +152,22 @@ void hbsd_options_default(hbsd_options* opt);
  * sigma_bar lies below the spectrum; otherwise (a non-positive pivot) the factorisation is
  * redone as LDL^T with 1 x 1 pivots in the same order (Eq. ldl without 2 x 2 blocks), whose
  * negative pivots (hbsd_stats.neg_pivots) count the eigenvalues below sigma_bar; sigma0 must then
- * be set below the spectrum.  Returns HBSD_ERR_NOT_SPD if a pivot is zero or not finite,
- * HBSD_ERR_UNSUPPORTED for complex input. */
+ * be set below the spectrum.  Returns HBSD_ERR_NOT_SPD if a pivot is zero or not finite.
+ *
+ * Complex Hermitian input (Sec. 2: H Hermitian, S Hermitian positive definite, complex at a
+ * Bloch vector k != 0): H and S both with is_complex = 1 (HBSD_ERR_ARG if only one is).  The
+ * session then holds the real symmetric pencil ([Hr, -Hi; Hi, Hr], [Sr, -Si; Si, Sr]) of size
+ * 2n, equivalent to the complex one (every eigenvalue twice: x and i x), with the real and
+ * imaginary part of each dof stored next to each other (real dof 2i is Re x_i, 2i+1 is Im x_i)
+ * and factorised as above (both halves of a dof share its mesh node).  hbsd_solve and
+ * hbsd_solve_device take and return complex blocks (see there); every step-level entry point
+ * acts on the real-equivalent pencil, with 2n rows in that order.  hbsd_n returns n. */
 int hbsd_create(const hbsd_csr* H, const hbsd_csr* S, const hbsd_local_blocks* lb,
                 const hbsd_options* opt, void* stream, hbsd_handle** out);
 
 /* Replace H's values (same pattern) for an SCF follow-up; the global factor keeps the
- * first H (Sec. 4: K built from H^(1) and reused through the SCF). */
+ * first H (Sec. 4: K built from H^(1) and reused through the SCF).  H_val: nnz doubles, or
+ * 2 nnz interleaved (re, im) doubles on a complex session. */
 int hbsd_update_H(hbsd_handle* h, const double* H_val);
 
 /* Nonlocal term of the Hamiltonian (Sec. 4, Eq. fgf): from now on the session's H is
@@ -173,19 +182,33 @@ int hbsd_update_H(hbsd_handle* h, const double* H_val);
  * H_loc^(1) - eps_bar S + F G F^T (Sec. 4, steps 1-6): Fhat = K F and M = (I + G F^T Fhat)^{-1} G
  * are formed on first use with the factor of the local part and kept until the next call.
  * HBSD_ERR_ARG there if I + G F^T Fhat is singular.  The factor itself is unchanged (it is
- * that of the local part).  Waits for the session's stream; not to be called during a solve. */
+ * that of the local part).  Waits for the session's stream; not to be called during a solve.
+ * HBSD_ERR_UNSUPPORTED for k > 0 on a complex session. */
 int hbsd_set_nonlocal(hbsd_handle* h, int k, const double* F, int64_t ldf, const double* G);
 
 /* LABPSD (Sec. 3 outline, steps 1-12): lowest nev eigenpairs to Res_max <= tol (remark 2).
  * X0: host, row-major n x (nev + m0) start block (remark 1), or NULL for seed-normal draws,
  * or the previous solve's block if warm != 0 (X0 must then be NULL).  lambda: host, nev
  * unshifted eigenvalues ascending.  X: host, row-major n x nev S-orthonormal eigenvectors, or
- * NULL.  iters, st: nullable.  Synchronous. */
+ * NULL.  iters, st: nullable.  Synchronous.
+ *
+ * Complex session: X0 is n x (nev + m0) complex (2 doubles per entry, re then im; NULL draws
+ * the real parts from the SplitMix64 normals of stream 2 and the imaginary parts from stream 6
+ * of opt.seed) and X is n x nev complex, S-orthonormal in x^H S y.  The solve runs LABPSD on the
+ * real-equivalent pencil for 2 nev pairs with 2 m0 guard columns from the start block whose
+ * columns are the realified x_c and J x_c (J: multiplication by i), whose span every step keeps
+ * invariant under J: it is the complex iteration of the outline in real arithmetic, and iters
+ * and hbsd_stats count its iterations.  From the 2 nev real eigenvectors, nev complex
+ * directions are then selected on the GPU in ascending eigenvalue order and S-orthonormalised
+ * (HBSD_ERR_RR_RANK if fewer than nev are independent).  nev <= 512.  The nonlocal term is not
+ * available on complex sessions. */
 int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm,
                double* lambda, double* X, int* iters, hbsd_stats* st);
 
 /* Same as hbsd_solve with device buffers: X0_dev row-major n x (nev+m0), ld = ldx0 (or NULL),
- * lambda_dev nev doubles, X_dev row-major n x nev with ld = ldx (or NULL). */
+ * lambda_dev nev doubles, X_dev row-major n x nev with ld = ldx (or NULL).  On a complex
+ * session X0_dev and X_dev are complex (re, im doubles per entry) and ldx0, ldx count complex
+ * entries. */
 int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0,
                       double* lambda_dev, double* X_dev, int64_t ldx, int* iters, hbsd_stats* st);
 
@@ -199,6 +222,7 @@ void hbsd_destroy(hbsd_handle* h);
 const char* hbsd_status_string(int status);
 const char* hbsd_last_error(void);
 int64_t hbsd_n(const hbsd_handle* h);
+int hbsd_is_complex(const hbsd_handle* h);   /* 1 for a session created from complex input */
 double hbsd_sigma0(const hbsd_handle* h);
 void hbsd_get_stats(const hbsd_handle* h, hbsd_stats* st);
 

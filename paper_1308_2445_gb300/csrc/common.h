@@ -208,6 +208,9 @@ template <class T>
 int gram2(Session* s, const T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1, const T* H0,
           int64_t ldh0, const T* H1, int64_t ldh1, const T* S0, int64_t lds0, const T* S1, int64_t lds1,
           int64_t n, double* HR, double* SR, cudaStream_t st);
+// A1 = antisymmetric part of Z^T V1, A2 = symmetric part of Z^T V2 (q x q, row-major)
+int gram_skew(Session* s, const double* Z, int64_t ldz, const double* V1, int64_t ldv1, const double* V2,
+              int64_t ldv2, int64_t n, int q, double* A1, double* A2, cudaStream_t st);
 // largest q the allocation-free Gram's static scratch holds (2 q^2 doubles per row chunk, 2^21 in all)
 constexpr int GRAM_NOALLOC_MAX_Q = 1024;
 int gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS, int64_t ldzs,
@@ -324,6 +327,15 @@ struct Session {
     int keep_w = 0;
     int64_t keep_ld = 0;
     Nonlocal nl;                // H_nl = F G F^T (k = 0: none)
+    // complex Hermitian input: the session holds the real-equivalent pencil of size n = 2 n_c
+    // with the dofs interleaved (row 2i: real part of complex dof i, row 2i+1: imaginary part)
+    bool cplx = false;
+    int64_t n_c = 0;
+    std::vector<int64_t> c_row_ptr;  // complex pattern, kept to realify new H values
+    std::vector<int32_t> c_col_idx;
+    DBuf<double> cx_gr, cx_gc, cx_w, cx_x0, cx_y0;   // recovery: Gram parts, coefficients; start blocks
+    DBuf<double2> cx_a, cx_l, cx_m;  // recovery: Gram (eliminated in place), Cholesky columns, inverse
+    DBuf<int> cx_piv;
     std::vector<double> res_hist;   // Res_max at each convergence test of the last solve
 };
 
@@ -335,6 +347,14 @@ template <class T>   // SMW step 6 on P = -K R (T = float: scaled P^ of the mixe
 int nl_smw_correct(Session* s, T* P, int64_t ldp, int p, cudaStream_t st);
 int nl_minres_index(Session* s, int grid, const std::vector<int64_t>& blk, int64_t kp);
 int barrier_timeout_probe(double limit_s, cudaStream_t st);
+
+// complex Hermitian input through the real-equivalent pencil (complex.cu)
+int complex_realify_csr(int64_t n, const int64_t* rp, const int32_t* ci, const double* hv, const double* sv,
+                        const int32_t* dof_node, std::vector<int64_t>& rp2, std::vector<int32_t>& ci2,
+                        std::vector<double>& hv2, std::vector<double>& sv2, std::vector<int32_t>& node2);
+void complex_realify_values(int64_t n, const int64_t* rp, const double* v, std::vector<double>& out);
+int complex_start_block(Session* s, const double* X0c, int64_t ldc, int wc, double* Y, int64_t ldy);
+int complex_recover(Session* s, int nev, double* lam_dev, double* Xc_dev, int64_t ldxc);
 
 // ---- small utilities -----------------------------------------------------------------
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }

@@ -259,6 +259,44 @@ template int gram2<float>(Session*, const float*, int64_t, int, const float*, in
                           const float*, int64_t, const float*, int64_t, const float*, int64_t, int64_t, double*,
                           double*, cudaStream_t);
 
+// ---- cross Gram of the complex recovery ----------------------------------------------------
+// Sum the chunks in order; A1 = (X - X^T) / 2 (the antisymmetric part of Z^T V1), A2 = (Y + Y^T) / 2.
+__global__ void k_gram_final_skew(const double* __restrict__ partial, int nchunks, int q,
+                                  double* __restrict__ A1, double* __restrict__ A2) {
+    const int64_t qq = (int64_t)q * q;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= qq) return;
+    const int a = (int)(idx / q), b = (int)(idx % q);
+    double x_ab = 0, x_ba = 0, y_ab = 0, y_ba = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const double* px = partial + (int64_t)c * 2 * qq;
+        x_ab += px[(int64_t)a * q + b];
+        x_ba += px[(int64_t)b * q + a];
+        y_ab += px[qq + (int64_t)a * q + b];
+        y_ba += px[qq + (int64_t)b * q + a];
+    }
+    A1[idx] = 0.5 * (x_ab - x_ba);
+    A2[idx] = 0.5 * (y_ab + y_ba);
+}
+
+int gram_skew(Session* s, const double* Z, int64_t ldz, const double* V1, int64_t ldv1, const double* V2,
+              int64_t ldv2, int64_t n, int q, double* A1, double* A2, cudaStream_t st) {
+    if (q <= 0) return 0;
+    const int tiles = ceil_div(q, 32);
+    int nch = (int)std::max<int64_t>(1, std::min<int64_t>((n + 127) / 128, ceil_div(1216, tiles * tiles)));
+    const int64_t rpc = (n + nch - 1) / nch;
+    nch = (int)((n + rpc - 1) / rpc);
+    HBSD_TRY(s->ws.alloc((size_t)nch * 2 * q * q + 64));
+    Seg2<double> A{Z, ldz, q, nullptr, 0}, B1{V1, ldv1, q, nullptr, 0}, B2{V2, ldv2, q, nullptr, 0};
+    dim3 grid(tiles * tiles, nch);
+    k_gram_partial<double><<<grid, 256, 0, st>>>(A, B1, B2, q, n, rpc, tiles, s->ws.p);
+    HBSD_LAUNCHED(s);
+    const int64_t qq = (int64_t)q * q;
+    k_gram_final_skew<<<ceil_div(qq, 256), 256, 0, st>>>(s->ws.p, nch, q, A1, A2);
+    HBSD_LAUNCHED(s);
+    return 0;
+}
+
 // ---- allocation-free Gram ---------------------------------------------------------------
 // Scratch for hbsd_gram_noalloc: a file-scope device array, so the call needs no cudaMalloc.
 // Every device that loads the library holds it (16 MiB) until the process exits.

@@ -448,11 +448,11 @@ __global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, 
 // subspace from them in FP32 diverges, and FP32 MINRES on them multiplies the outer iterations
 // (both measured on the 32^3 workload).
 static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t ldx0, double* lam_dev,
-                        double* X_dev, int64_t ldx, int* iters_out) {
+                        double* X_dev, int64_t ldx, int* iters_out, int m0_force = -1) {
     cudaStream_t st = S->stream;
     const hbsd_options& o = S->opt;
     const int64_t n = S->n;
-    const int m0 = o.m0 >= 0 ? o.m0 : std::max(3, (m + 9) / 10);
+    const int m0 = m0_force >= 0 ? m0_force : o.m0 >= 0 ? o.m0 : std::max(3, (m + 9) / 10);
     const int w = m + m0;
     if (m < 1 || w > n) return fail(HBSD_ERR_ARG, "nev + m0 must lie in [1, n]");
     const bool mixed = o.precision == HBSD_PRECISION_MIXED;
@@ -575,7 +575,7 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
         if (!out) return fail(HBSD_ERR_ARG, "out is NULL");
         *out = nullptr;
         if (!H || !Sm || !lb || !opt) return fail(HBSD_ERR_ARG, "H, S, local blocks and options are required");
-        if (H->is_complex || Sm->is_complex) return fail(HBSD_ERR_UNSUPPORTED, "complex Hermitian input is not built yet");
+        if (H->is_complex != Sm->is_complex) return fail(HBSD_ERR_ARG, "H and S must both be real or both complex");
         if (!H->row_ptr || !H->col_idx || !H->val || !Sm->val || !Sm->row_ptr || !Sm->col_idx)
             return fail(HBSD_ERR_ARG, "NULL CSR array");
         if (H->n <= 0 || H->n != Sm->n || H->nnz != Sm->nnz || H->nnz != H->row_ptr[H->n])
@@ -592,11 +592,38 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
             return fail(HBSD_ERR_ARG, "hbsd_create: local_solver must be HBSD_LOCAL_MINRES or HBSD_LOCAL_ONESTEP");
         if (!lb->dof_node || lb->grid[0] <= 0 || lb->grid[1] <= 0 || lb->grid[2] <= 0)
             return fail(HBSD_ERR_ARG, "local blocks need dof_node and a positive grid");
+        // complex Hermitian input: the real-equivalent pencil of size 2n (complex.cu)
+        std::vector<int64_t> rp2;
+        std::vector<int32_t> ci2, node2;
+        std::vector<double> hv2, sv2;
+        const int64_t* row_ptr = H->row_ptr;
+        const int32_t* col_idx = H->col_idx;
+        const double* hval = H->val;
+        const double* sval = Sm->val;
+        const int32_t* dof_node = lb->dof_node;
+        int64_t n_dofs = H->n, nnz = H->nnz;
+        if (H->is_complex) {
+            for (int64_t e = 0; e < 2 * H->nnz; ++e)
+                if (!std::isfinite(H->val[e]) || !std::isfinite(Sm->val[e])) return fail(HBSD_ERR_ARG, "non-finite value");
+            complex_realify_csr(H->n, H->row_ptr, H->col_idx, H->val, Sm->val, lb->dof_node, rp2, ci2, hv2, sv2, node2);
+            row_ptr = rp2.data();
+            col_idx = ci2.data();
+            hval = hv2.data();
+            sval = sv2.data();
+            dof_node = node2.data();
+            n_dofs = 2 * H->n;
+            nnz = 4 * H->nnz;
+        }
         hbsd_handle* h = new hbsd_handle();
         Session* S = &h->s;
-        S->n = H->n;
-        S->nnz = H->nnz;
+        S->n = n_dofs;
+        S->nnz = nnz;
         S->opt = *opt;
+        if (H->is_complex) {
+            S->cplx = true;
+            S->n_c = H->n;
+            S->c_row_ptr.assign(H->row_ptr, H->row_ptr + H->n + 1);
+        }
         {
             const char* e = std::getenv("HBSD_NO_DF64");
             S->opt_df64 = !(e && e[0] && e[0] != '0');
@@ -611,13 +638,13 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
             }
             S->own_stream = true;
         }
-        int rc = sell_build(S->A, S->n, H->row_ptr, H->col_idx, H->val, Sm->val, S->sigma0);
+        int rc = sell_build(S->A, S->n, row_ptr, col_idx, hval, sval, S->sigma0);
         if (rc < 0) { hbsd_destroy(h); return rc; }
-        S->h_sval.assign(Sm->val, Sm->val + S->nnz);
+        S->h_sval.assign(sval, sval + S->nnz);
         std::vector<double> aval(S->nnz);
-        for (int64_t e = 0; e < S->nnz; ++e) aval[e] = H->val[e] - opt->sigma_bar * Sm->val[e];
+        for (int64_t e = 0; e < S->nnz; ++e) aval[e] = hval[e] - opt->sigma_bar * sval[e];
         if (opt->precond != HBSD_PRECOND_LOCAL) {   // the local-only mode has no global step
-            rc = factor_build(S, S->F, S->n, H->row_ptr, H->col_idx, aval.data(), lb->dof_node, lb->grid, S->stream);
+            rc = factor_build(S, S->F, S->n, row_ptr, col_idx, aval.data(), dof_node, lb->grid, S->stream);
             if (rc < 0) { std::string keep = g_last_error; hbsd_destroy(h); g_last_error = keep; return rc; }
             S->has_factor = true;
         }
@@ -629,6 +656,11 @@ int hbsd_create(const hbsd_csr* H, const hbsd_csr* Sm, const hbsd_local_blocks* 
 int hbsd_update_H(hbsd_handle* h, const double* H_val) {
     return guarded([&]() -> int {
         if (!h || !H_val) return fail(HBSD_ERR_ARG, "NULL argument");
+        if (h->s.cplx) {   // 2 nnz interleaved (re, im) values of the complex pattern
+            std::vector<double> v2;
+            complex_realify_values(h->s.n_c, h->s.c_row_ptr.data(), H_val, v2);
+            return sell_update_h(h->s.A, v2.data(), h->s.h_sval.data(), h->s.sigma0);
+        }
         return sell_update_h(h->s.A, H_val, h->s.h_sval.data(), h->s.sigma0);
     });
 }
@@ -640,7 +672,8 @@ void hbsd_destroy(hbsd_handle* h) {
     delete h;
 }
 
-int64_t hbsd_n(const hbsd_handle* h) { return h ? h->s.n : -1; }
+int64_t hbsd_n(const hbsd_handle* h) { return h ? (h->s.cplx ? h->s.n_c : h->s.n) : -1; }
+int hbsd_is_complex(const hbsd_handle* h) { return h && h->s.cplx ? 1 : 0; }
 double hbsd_sigma0(const hbsd_handle* h) { return h ? h->s.sigma0 : 0.0; }
 void hbsd_get_stats(const hbsd_handle* h, hbsd_stats* st) {
     if (h && st) *st = h->s.stats;
@@ -648,12 +681,64 @@ void hbsd_get_stats(const hbsd_handle* h, hbsd_stats* st) {
 
 static int m0_of(const Session& S, int nev) { return S.opt.m0 >= 0 ? S.opt.m0 : std::max(3, (nev + 9) / 10); }
 
+// Complex session: LABPSD on the real-equivalent pencil for 2 nev pairs from the realified start
+// block Yb (2 n_c x 2 (nev + m0), ld ldy; columns J-paired), then the complex recovery.
+static int complex_solve_block(Session* S, int nev, double tol, const double* Yb, int64_t ldy, double* lambda_dev,
+                               double* X_dev, int64_t ldx, int* iters) {
+    const int m0c = m0_of(*S, nev);
+    S->launches = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = labpsd_solve(S, 2 * nev, tol, Yb, ldy, nullptr, nullptr, 0, iters, 2 * m0c);
+    if (rc >= 0) {
+        const int rr = complex_recover(S, nev, lambda_dev, X_dev, ldx);
+        if (rr < 0) rc = rr;
+        else if (cudaStreamSynchronize(S->stream) != cudaSuccess) rc = fail(HBSD_ERR_CUDA, "complex recovery");
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    S->stats.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    S->stats.gpu_launches = S->launches;
+    return rc;
+}
+
+static int complex_solve_device(Session* S, int nev, double tol, const double* X0_dev, int64_t ldx0,
+                                double* lambda_dev, double* X_dev, int64_t ldx, int* iters) {
+    const int wc = nev + m0_of(*S, nev);
+    if (wc > S->n_c) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
+    if (X_dev && ldx < nev) return fail(HBSD_ERR_ARG, "ldx < nev");
+    if (2 * nev > 1024) return fail(HBSD_ERR_ARG, "complex input: nev <= 512");
+    if (!X0_dev) {   // seed-normal complex block: real part from stream 2, imaginary part from stream 6
+        const int64_t cnt = S->n_c * wc;
+        std::vector<double> re(cnt), im(cnt), hx(2 * cnt);
+        seed_normals(S->opt.seed, 2, cnt, re.data());
+        seed_normals(S->opt.seed, 6, cnt, im.data());
+        for (int64_t t = 0; t < cnt; ++t) { hx[2 * t] = re[t]; hx[2 * t + 1] = im[t]; }
+        HBSD_TRY(S->cx_x0.alloc(hx.size()));
+        HBSD_CUDA(cudaMemcpyAsync(S->cx_x0.p, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice, S->stream));
+        HBSD_CUDA(cudaStreamSynchronize(S->stream));
+        X0_dev = S->cx_x0.p;
+        ldx0 = wc;
+    } else if (ldx0 < wc) {
+        return fail(HBSD_ERR_ARG, "ldx0 < nev + m0");
+    }
+    const int64_t w = 2 * (int64_t)wc;
+    HBSD_TRY(S->cx_y0.alloc((size_t)S->n * w));
+    HBSD_TRY(complex_start_block(S, X0_dev, ldx0, wc, S->cx_y0.p, w));
+    return complex_solve_block(S, nev, tol, S->cx_y0.p, w, lambda_dev, X_dev, ldx, iters);
+}
+
 int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev, int64_t ldx0, double* lambda_dev,
                       double* X_dev, int64_t ldx, int* iters, hbsd_stats* st) {
     return guarded([&]() -> int {
         if (!h || !lambda_dev) return fail(HBSD_ERR_ARG, "NULL handle or lambda");
         Session* S = &h->s;
         if (nev < 1 || !(tol > 0)) return fail(HBSD_ERR_ARG, "nev >= 1 and tol > 0 required");
+        if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
+            return fail(HBSD_ERR_ARG, "unknown precision mode");
+        if (S->cplx) {
+            const int rc = complex_solve_device(S, nev, tol, X0_dev, ldx0, lambda_dev, X_dev, ldx, iters);
+            if (st) *st = S->stats;
+            return rc;
+        }
         if (X_dev && ldx < nev) return fail(HBSD_ERR_ARG, "ldx < nev");
         const int w = nev + m0_of(*S, nev);
         if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
@@ -681,12 +766,50 @@ int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev,
     });
 }
 
+// hbsd_solve on a complex session: X0 host n_c x (nev + m0) complex (interleaved re, im), X host
+// n_c x nev complex; warm: the session's last real-equivalent block.
+static int complex_solve_host(Session* S, int nev, double tol, const double* X0, int warm, double* lambda, double* X,
+                              int* iters, hbsd_stats* st) {
+    if (!(tol > 0)) return fail(HBSD_ERR_ARG, "tol > 0 required");
+    if (S->opt.precision != HBSD_PRECISION_FP64 && S->opt.precision != HBSD_PRECISION_MIXED)
+        return fail(HBSD_ERR_ARG, "unknown precision mode");
+    const int wc = nev + m0_of(*S, nev);
+    if (wc > S->n_c) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
+    if (2 * nev > 1024) return fail(HBSD_ERR_ARG, "complex input: nev <= 512");
+    HBSD_TRY(S->io_lam.alloc(nev));
+    if (X) HBSD_TRY(S->io_x.alloc((size_t)S->n_c * nev * 2));
+    int rc;
+    if (warm) {
+        if (X0) return fail(HBSD_ERR_ARG, "warm start takes X0 = NULL");
+        if (!S->psi_keep.p || S->keep_w != 2 * wc)
+            return fail(HBSD_ERR_ARG, "no previous block of this width to warm-start from");
+        HBSD_TRY(S->cx_y0.alloc(S->psi_keep.n));
+        HBSD_CUDA(cudaMemcpyAsync(S->cx_y0.p, S->psi_keep.p, S->psi_keep.n * 8, cudaMemcpyDeviceToDevice, S->stream));
+        rc = complex_solve_block(S, nev, tol, S->cx_y0.p, S->keep_ld, S->io_lam.p, X ? S->io_x.p : nullptr, nev, iters);
+    } else {
+        const double* x0p = nullptr;
+        if (X0) {
+            HBSD_TRY(S->io_x0.alloc((size_t)S->n_c * wc * 2));
+            HBSD_CUDA(cudaMemcpyAsync(S->io_x0.p, X0, (size_t)S->n_c * wc * 16, cudaMemcpyHostToDevice, S->stream));
+            x0p = S->io_x0.p;
+        }
+        rc = complex_solve_device(S, nev, tol, x0p, wc, S->io_lam.p, X ? S->io_x.p : nullptr, nev, iters);
+    }
+    if (st) *st = S->stats;
+    if (rc < 0) return rc;
+    HBSD_CUDA(cudaMemcpyAsync(lambda, S->io_lam.p, nev * 8, cudaMemcpyDeviceToHost, S->stream));
+    if (X) HBSD_CUDA(cudaMemcpyAsync(X, S->io_x.p, (size_t)S->n_c * nev * 16, cudaMemcpyDeviceToHost, S->stream));
+    HBSD_CUDA(cudaStreamSynchronize(S->stream));
+    return rc;
+}
+
 int hbsd_solve(hbsd_handle* h, int nev, double tol, const double* X0, int warm, double* lambda, double* X, int* iters,
                hbsd_stats* st) {
     return guarded([&]() -> int {
         if (!h || !lambda) return fail(HBSD_ERR_ARG, "NULL handle or lambda");
         Session* S = &h->s;
         if (nev < 1) return fail(HBSD_ERR_ARG, "nev >= 1 required");
+        if (S->cplx) return complex_solve_host(S, nev, tol, X0, warm, lambda, X, iters, st);
         const int w = nev + m0_of(*S, nev);
         if (w > S->n) return fail(HBSD_ERR_ARG, "nev + m0 exceeds n");
         // host <-> device traffic goes through session-resident buffers on the session's stream
@@ -747,6 +870,7 @@ int hbsd_res_history(const hbsd_handle* h, double* out, int cap) {
 int hbsd_set_nonlocal(hbsd_handle* h, int k, const double* F, int64_t ldf, const double* G) {
     return guarded([&]() -> int {
         if (!h) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (h->s.cplx && k > 0) return fail(HBSD_ERR_UNSUPPORTED, "nonlocal term on a complex session");
         HBSD_CUDA(cudaStreamSynchronize(h->s.stream));   // no work of this session reads the old term any more
         return nl_set(&h->s, k, F, ldf, G);
     });

@@ -104,6 +104,7 @@ _SIGS = {
     "hbsd_status_string": (C.c_char_p, [C.c_int]),
     "hbsd_last_error": (C.c_char_p, []),
     "hbsd_n": (C.c_int64, [_P]),
+    "hbsd_is_complex": (C.c_int, [_P]),
     "hbsd_sigma0": (C.c_double, [_P]),
     "hbsd_get_stats": (None, [_P, C.POINTER(hbsd_stats)]),
     "hbsd_spmm_pair": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
@@ -197,15 +198,19 @@ class Session:
         self._keep = []
         rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
         ci = np.ascontiguousarray(col_idx, dtype=np.int32)
-        hv = np.ascontiguousarray(h_val, dtype=np.float64)
-        sv = np.ascontiguousarray(s_val, dtype=np.float64)
+        # complex Hermitian values go in as interleaved (re, im) doubles
+        self.is_complex = bool(np.iscomplexobj(h_val) or np.iscomplexobj(s_val))
+        vdt = np.complex128 if self.is_complex else np.float64
+        hv = np.ascontiguousarray(h_val, dtype=vdt).view(np.float64)
+        sv = np.ascontiguousarray(s_val, dtype=vdt).view(np.float64)
         dn = np.ascontiguousarray(dof_node, dtype=np.int32)
         self._keep += [rp, ci, hv, sv, dn]
         self.n = int(n)
+        cflag = int(self.is_complex)
         H = hbsd_csr(self.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
-                     ci.ctypes.data_as(C.POINTER(C.c_int32)), hv.ctypes.data_as(_D), 0)
+                     ci.ctypes.data_as(C.POINTER(C.c_int32)), hv.ctypes.data_as(_D), cflag)
         S = hbsd_csr(self.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
-                     ci.ctypes.data_as(C.POINTER(C.c_int32)), sv.ctypes.data_as(_D), 0)
+                     ci.ctypes.data_as(C.POINTER(C.c_int32)), sv.ctypes.data_as(_D), cflag)
         lb = hbsd_local_blocks(dn.ctypes.data_as(C.POINTER(C.c_int32)), None, (C.c_int32 * 3)(*grid))
         self.opts = options_default(sigma_bar=float(sigma_bar), **opts)
         h = C.c_void_p()
@@ -265,24 +270,26 @@ class Session:
         return self.opts.m0 if self.opts.m0 >= 0 else max(3, -(-nev // 10))
 
     def update_H(self, h_val):
-        hv = np.ascontiguousarray(h_val, dtype=np.float64)
+        hv = np.ascontiguousarray(h_val, dtype=np.complex128 if self.is_complex else np.float64).view(np.float64)
         check(lib().hbsd_update_H(self.h, hv.ctypes.data_as(_D)), "hbsd_update_H")
 
     def solve(self, nev, tol, X0=None, warm=False, want_vectors=True):
         """hbsd_solve with host arrays: returns (lambda, X, iters, status, stats)."""
         w = nev + self.m0(nev)
         x0p = None
+        vdt = np.complex128 if self.is_complex else np.float64
         if X0 is not None:
-            X0 = np.ascontiguousarray(X0, dtype=np.float64)
+            X0 = np.ascontiguousarray(X0, dtype=vdt)
             if X0.shape != (self.n, w):
                 raise ValueError(f"X0 must be {self.n} x {w}")
-            x0p = X0.ctypes.data_as(_D)
+            x0p = X0.view(np.float64).ctypes.data_as(_D)
         lam = np.empty(nev)
-        X = np.empty((self.n, nev)) if want_vectors else None
+        X = np.empty((self.n, nev), dtype=vdt) if want_vectors else None
         it = C.c_int(0)
         st = hbsd_stats()
         rc = check(lib().hbsd_solve(self.h, nev, tol, x0p, int(bool(warm)), lam.ctypes.data_as(_D),
-                                    X.ctypes.data_as(_D) if X is not None else None, C.byref(it), C.byref(st)),
+                                    X.view(np.float64).ctypes.data_as(_D) if X is not None else None, C.byref(it),
+                                    C.byref(st)),
                    "hbsd_solve")
         return lam, X, it.value, rc, st.as_dict()
 

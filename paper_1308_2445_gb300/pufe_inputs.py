@@ -58,6 +58,7 @@ STREAM_X0 = 2
 STREAM_NOISE = 3
 STREAM_BATCH = 4
 STREAM_REQUESTS = 5
+STREAM_X0_IM = 6      # imaginary part of a complex start block
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -96,6 +97,12 @@ def normal(seed: int, stream: int, count: int) -> np.ndarray:
 def seed_normal_block(seed: int, n: int, w: int, stream: int = STREAM_X0) -> np.ndarray:
     """Seed-normal n x w starting block X0 (row-major, entry (i, j) = draw i*w + j)."""
     return normal(seed, stream, n * w).reshape(n, w)
+
+
+def seed_normal_block_complex(seed: int, n: int, w: int) -> np.ndarray:
+    """Complex start block for Hermitian (Bloch) problems: real part from the X0 stream, imaginary
+    part from its own stream, both seed-normal (what the library draws for X0 = NULL)."""
+    return seed_normal_block(seed, n, w) + 1j * seed_normal_block(seed, n, w, stream=STREAM_X0_IM)
 
 
 @dataclasses.dataclass
