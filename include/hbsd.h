@@ -370,7 +370,10 @@ void hbsd_server_opts_default(hbsd_server_opts* opts);
 int hbsd_server_create(const hbsd_server_opts* opts, hbsd_server** out);
 /* Queues a request and returns at once with its ticket.  lambda_out (nev doubles) and X_out
  * (n x nev, row-major, or NULL) are host buffers the caller keeps valid until the result has
- * been polled.  HBSD_ERR_OOM if the problem alone exceeds the memory budget, HBSD_ERR_ARG for
+ * been polled.  A complex problem (H and S with is_complex = 1, Bloch phases) runs as in
+ * hbsd_solve on a complex session: X0, X_out and the H_val of its follow-ups are complex
+ * (re, im doubles per entry), and it is admitted by the footprint of its real pencil of size
+ * 2n; the nonlocal term is not available for it (HBSD_ERR_UNSUPPORTED).  HBSD_ERR_OOM if the problem alone exceeds the memory budget, HBSD_ERR_ARG for
  * an unknown session or malformed input. */
 int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, double* X_out, uint64_t* ticket);
 /* HBSD_BUSY while the request is queued or running; HBSD_OK once, with the result (the ticket

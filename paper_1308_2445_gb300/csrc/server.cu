@@ -31,6 +31,7 @@ struct Request {
     bool is_new = false;
     // new problem (copied at submission)
     int64_t n = 0, nnz = 0;
+    int is_complex = 0;              // values are (re, im) pairs; the session solves the 2n real pencil
     std::vector<int64_t> row_ptr;
     std::vector<int32_t> col_idx, dof_node, dof_cluster;
     std::vector<double> hval, sval;
@@ -164,8 +165,8 @@ void run_request(hbsd_server* sv, Request& rq) {
         if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess) {
             rc = fail(HBSD_ERR_CUDA, "server: cudaStreamCreateWithFlags failed");
         } else {
-            hbsd_csr H{rq.n, rq.nnz, rq.row_ptr.data(), rq.col_idx.data(), rq.hval.data(), 0};
-            hbsd_csr S{rq.n, rq.nnz, rq.row_ptr.data(), rq.col_idx.data(), rq.sval.data(), 0};
+            hbsd_csr H{rq.n, rq.nnz, rq.row_ptr.data(), rq.col_idx.data(), rq.hval.data(), rq.is_complex};
+            hbsd_csr S{rq.n, rq.nnz, rq.row_ptr.data(), rq.col_idx.data(), rq.sval.data(), rq.is_complex};
             hbsd_local_blocks lb{};
             lb.dof_node = rq.dof_node.data();
             lb.dof_cluster = rq.dof_cluster.empty() ? nullptr : rq.dof_cluster.data();
@@ -328,8 +329,9 @@ int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, dou
         int64_t n = 0;
         if (rq->session_id < 0) {   // new problem: H, S, local blocks and options copied here
             if (!rq->H || !rq->S || !rq->lb || !rq->opt) return fail(HBSD_ERR_ARG, "a new problem needs H, S, lb, opt");
-            if (rq->H->n <= 0 || rq->H->n != rq->S->n || rq->H->nnz != rq->S->nnz || rq->H->is_complex || rq->S->is_complex)
-                return fail(HBSD_ERR_ARG, "H and S must be real with the same n and nnz");
+            if (rq->H->n <= 0 || rq->H->n != rq->S->n || rq->H->nnz != rq->S->nnz || rq->H->is_complex != rq->S->is_complex)
+                return fail(HBSD_ERR_ARG, "H and S must have the same n, nnz and value type");
+            if (rq->H->is_complex && rq->nl_k > 0) return fail(HBSD_ERR_UNSUPPORTED, "nonlocal term on complex input");
             if (!rq->lb->dof_node || !rq->H->row_ptr || !rq->H->col_idx || !rq->H->val || !rq->S->val)
                 return fail(HBSD_ERR_ARG, "NULL array in the problem");
             if (rq->warm) return fail(HBSD_ERR_ARG, "a new problem cannot warm-start");
@@ -339,8 +341,10 @@ int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, dou
             r->nnz = rq->H->nnz;
             r->row_ptr.assign(rq->H->row_ptr, rq->H->row_ptr + n + 1);
             r->col_idx.assign(rq->H->col_idx, rq->H->col_idx + r->nnz);
-            r->hval.assign(rq->H->val, rq->H->val + r->nnz);
-            r->sval.assign(rq->S->val, rq->S->val + r->nnz);
+            r->is_complex = rq->H->is_complex ? 1 : 0;
+            const int64_t vals = r->nnz * (r->is_complex ? 2 : 1);
+            r->hval.assign(rq->H->val, rq->H->val + vals);
+            r->sval.assign(rq->S->val, rq->S->val + vals);
             r->dof_node.assign(rq->lb->dof_node, rq->lb->dof_node + n);
             if (rq->lb->dof_cluster) r->dof_cluster.assign(rq->lb->dof_cluster, rq->lb->dof_cluster + n);
             std::memcpy(r->grid, rq->lb->grid, sizeof(r->grid));
@@ -354,24 +358,28 @@ int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, dou
                     std::memcpy(r->nl_F.data() + i * rq->nl_k, rq->nl_F + i * rq->nl_ldf, rq->nl_k * sizeof(double));
                 r->nl_G.assign(rq->nl_G, rq->nl_G + (size_t)rq->nl_k * rq->nl_k);
             }
-            r->est_bytes = estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
+            // a complex problem runs as the real pencil of size 2n (4 nnz entries, 2 nev columns)
+            r->est_bytes = r->is_complex ? estimate_bytes(2 * n, 4 * r->nnz, 2 * rq->nev, 0)
+                                         : estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
             if (r->est_bytes > sv->opts.hbm_budget_bytes) return fail(HBSD_ERR_OOM, "request exceeds the server's memory budget");
         } else {   // follow-up of a resident session: new H values (optional), warm start or X0
             std::lock_guard<std::mutex> lk(sv->mu);
             auto s = sv->sessions.find(rq->session_id);
             if (s == sv->sessions.end()) return fail(HBSD_ERR_ARG, "unknown or evicted session");
             const Session& ses = s->second.h->s;
-            n = ses.n;
+            const int cw = ses.cplx ? 2 : 1;                    // doubles per value
+            n = ses.cplx ? ses.n_c : ses.n;
+            r->is_complex = ses.cplx ? 1 : 0;
             r->session_id = rq->session_id;
-            if (rq->H_val) r->hval_new.assign(rq->H_val, rq->H_val + ses.nnz);
+            if (rq->H_val) r->hval_new.assign(rq->H_val, rq->H_val + (ses.cplx ? 2 * (int64_t)ses.c_row_ptr.back() : ses.nnz));
             if (rq->X0) {
                 const int64_t w = rq->nev + (ses.opt.m0 >= 0 ? ses.opt.m0 : std::max(3, (rq->nev + 9) / 10));
-                r->X0.assign(rq->X0, rq->X0 + (size_t)n * w);
+                r->X0.assign(rq->X0, rq->X0 + (size_t)n * w * cw);
             }
         }
         if (rq->X0 && r->is_new) {
             const int64_t w = rq->nev + (rq->opt->m0 >= 0 ? rq->opt->m0 : std::max(3, (rq->nev + 9) / 10));
-            r->X0.assign(rq->X0, rq->X0 + (size_t)n * w);
+            r->X0.assign(rq->X0, rq->X0 + (size_t)n * w * (r->is_complex ? 2 : 1));
         }
         r->t_submit = Clock::now();
         {

@@ -395,25 +395,33 @@ class Server:
         self._out = {}   # ticket -> (lambda, X) host buffers, kept alive until polled
 
     def submit(self, nev, tol, problem=None, session_id=-1, H_val=None, X0=None, warm=False, want_vectors=True,
-               **opts):
+               n=None, is_complex=None, **opts):
+        """Queue a request.  A complex (Bloch) problem, or a follow-up of one, takes complex H_val
+        and X0 and returns a complex X; for a follow-up without X0, pass n and is_complex to get
+        the eigenvectors back."""
         keep = []
         rq = hbsd_request()
         rq.session_id = int(session_id)
         rq.nev = int(nev)
         rq.tol = float(tol)
         rq.warm = int(bool(warm))
-        n = None
+        cplx = bool(is_complex) if is_complex is not None else False
+        if problem is not None:
+            cplx = bool(np.iscomplexobj(problem.h_val) or np.iscomplexobj(problem.s_val))
+        elif is_complex is None:
+            cplx = bool((H_val is not None and np.iscomplexobj(H_val)) or (X0 is not None and np.iscomplexobj(X0)))
+        vdt = np.complex128 if cplx else np.float64
         if problem is not None:
             p = problem
             rp = np.ascontiguousarray(p.row_ptr, dtype=np.int64)
             ci = np.ascontiguousarray(p.col_idx, dtype=np.int32)
-            hv = np.ascontiguousarray(p.h_val, dtype=np.float64)
-            sv = np.ascontiguousarray(p.s_val, dtype=np.float64)
+            hv = np.ascontiguousarray(p.h_val, dtype=vdt).view(np.float64)
+            sv = np.ascontiguousarray(p.s_val, dtype=vdt).view(np.float64)
             dn = np.ascontiguousarray(p.dof_node, dtype=np.int32)
             H = hbsd_csr(p.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
-                         ci.ctypes.data_as(C.POINTER(C.c_int32)), hv.ctypes.data_as(_D), 0)
+                         ci.ctypes.data_as(C.POINTER(C.c_int32)), hv.ctypes.data_as(_D), int(cplx))
             S = hbsd_csr(p.n, int(ci.size), rp.ctypes.data_as(C.POINTER(C.c_int64)),
-                         ci.ctypes.data_as(C.POINTER(C.c_int32)), sv.ctypes.data_as(_D), 0)
+                         ci.ctypes.data_as(C.POINTER(C.c_int32)), sv.ctypes.data_as(_D), int(cplx))
             lb = hbsd_local_blocks(dn.ctypes.data_as(C.POINTER(C.c_int32)), None, (C.c_int32 * 3)(*p.grid))
             op = options_default(sigma_bar=float(p.eps_bar), **opts)
             keep += [rp, ci, hv, sv, dn, H, S, lb, op]
@@ -427,21 +435,22 @@ class Server:
             rq.session_id = -1
             n = p.n
         if H_val is not None:
-            hvn = np.ascontiguousarray(H_val, dtype=np.float64)
+            hvn = np.ascontiguousarray(H_val, dtype=vdt).view(np.float64)
             keep.append(hvn)
             rq.H_val = hvn.ctypes.data_as(_D)
         if X0 is not None:
-            x0 = np.ascontiguousarray(X0, dtype=np.float64)
+            x0 = np.ascontiguousarray(X0, dtype=vdt)
             keep.append(x0)
-            rq.X0 = x0.ctypes.data_as(_D)
+            rq.X0 = x0.view(np.float64).ctypes.data_as(_D)
             n = x0.shape[0]
         if n is None and want_vectors:
-            raise ValueError("want_vectors for a follow-up needs X0 or n; pass n through X0 or problem")
+            raise ValueError("want_vectors for a follow-up needs X0 or n; pass n through X0, problem or n=")
         lam = np.empty(nev)
-        X = np.empty((n, nev)) if want_vectors else None
+        X = np.empty((n, nev), dtype=vdt) if want_vectors else None
         t = C.c_uint64(0)
         check(lib().hbsd_submit(self.h, C.byref(rq), lam.ctypes.data_as(_D),
-                                X.ctypes.data_as(_D) if X is not None else None, C.byref(t)), "hbsd_submit")
+                                X.view(np.float64).ctypes.data_as(_D) if X is not None else None, C.byref(t)),
+              "hbsd_submit")
         self._out[t.value] = (lam, X)
         return t.value
 

@@ -1,11 +1,15 @@
 """Served-form benchmark: a stream of solve requests through hbsd_server_* on one GPU.
 
   python -m paper_1308_2445_gb300.serve_bench [--requests R] [--slots S] [--load 0.8] [--seed 11]
+                                              [--problems P] [--meshes 16,24,32,40]
 
-Request mix (synthetic, seeded): problems on 16^3 and 24^3 meshes with 4-8 atoms and 2-4
-enrichment dofs per node (r_c = 0.15), nev from {32, 64}; about half of the requests are
-SCF-style follow-ups of a session seen before (V perturbed by 1% Gaussian noise at the
-quadrature points, H re-assembled, warm start from the session's last block).
+Request mix (synthetic, seeded): a pool of P problems, each drawn like an instance of the batched
+workload -- mesh from {16^3, 24^3, 32^3, 40^3}, 4-16 atoms, 2-4 enrichment dofs per node within
+r_c = 0.15 -- and carrying one of the 8 Bloch phases of the 2 x 2 x 2 k-grid
+k = 2 pi (+-1/4, +-1/4, +-1/4) (complex Hermitian H and S); nev from {32, 64, 128}.  About half
+of the requests are SCF-style follow-ups of a session seen before (V perturbed by 1% Gaussian
+noise at the quadrature points, H re-assembled, warm start from the session's last block, first
+factor kept).  Every request runs in the mixed form to Res_max <= 1e-8.
 
 1. Capacity: a closed loop keeps `slots` requests in flight; capacity = requests / wall time.
 2. Served run: Poisson arrivals at `load` x capacity; each request's latency runs from its
@@ -28,17 +32,30 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def build_pool(seed):
+KGRID = [(a * 0.5 * np.pi, b * 0.5 * np.pi, c * 0.5 * np.pi) for a in (1, -1) for b in (1, -1) for c in (1, -1)]
+
+
+def build_pool(seed, problems=8, meshes=(16, 24, 32, 40)):
     from paper_1308_2445_gb300 import pufe_inputs as pi
     rng = np.random.default_rng(seed)
     pool = []
-    for k, mesh in enumerate([16, 16, 24, 24]):
-        atoms = int(rng.integers(4, 9))
+    for k in range(problems):
+        mesh = int(meshes[k % len(meshes)])
         enr = int(rng.integers(2, 5))
+        kpt = KGRID[int(rng.integers(len(KGRID)))]
         s = int(rng.integers(1, 1 << 30))
-        base = pi.generate(mesh, atoms, enr, 0.15, s)
-        follow = [pi.generate(mesh, atoms, enr, 0.15, s, v_noise=0.01, noise_seed=s + j + 1).h_val for j in range(2)]
-        pool.append((f"{mesh}^3/{atoms}at/{enr}enr/n={base.n}", base, follow))
+        # 4-16 atoms, as many as fit with non-overlapping r_c spheres
+        atoms = int(rng.integers(4, 17))
+        while True:
+            try:
+                base = pi.generate(mesh, atoms, enr, 0.15, s, kpt=kpt)
+                break
+            except (ValueError, RuntimeError):
+                atoms -= 1
+        follow = [pi.generate(mesh, atoms, enr, 0.15, s, kpt=kpt, v_noise=0.01, noise_seed=s + j + 1).h_val
+                  for j in range(2)]
+        pool.append((f"{mesh}^3/{atoms}at/{enr}enr/k={tuple(round(x / np.pi, 2) for x in kpt)}pi/n={base.n}",
+                     base, follow))
     return pool
 
 
@@ -49,7 +66,7 @@ def make_requests(pool, count, seed):
     out = []
     for _ in range(count):
         i = int(rng.integers(len(pool)))
-        nev = int(rng.choice([32, 64]))
+        nev = int(rng.choice([32, 64, 128]))
         if i in seen and rng.random() < 0.5:
             out.append((i, nev, int(rng.integers(2))))
         else:
@@ -71,7 +88,8 @@ def run(hbsd, pool, reqs, slots, arrivals=None):
         i, nev, fol = reqs[k]
         name, p, follow = pool[i]
         if fol >= 0 and i in sessions and sessions[i][1] == nev:
-            t = sv.submit(nev, 1e-8, session_id=sessions[i][0], H_val=follow[fol], warm=True, want_vectors=False)
+            t = sv.submit(nev, 1e-8, session_id=sessions[i][0], H_val=follow[fol], warm=True, want_vectors=False,
+                          is_complex=bool(np.iscomplexobj(p.h_val)))
         else:
             t = sv.submit(nev, 1e-8, problem=p, want_vectors=False, precision=hbsd.PRECISION_MIXED)
         pending[t] = (k, time.perf_counter())
@@ -121,15 +139,18 @@ def run(hbsd, pool, reqs, slots, arrivals=None):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--requests", type=int, default=60)
+    ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--seed", type=int, default=11)
+    ap.add_argument("--problems", type=int, default=8)
+    ap.add_argument("--meshes", default="16,24,32,40")
+    ap.add_argument("--skip-one-slot", action="store_true", help="leave out the one-slot comparison run")
     a = ap.parse_args()
     from paper_1308_2445_gb300 import build_lib, hbsd
     if not os.path.exists(build_lib.LIB):
         build_lib.build()
-    pool = build_pool(a.seed)
+    pool = build_pool(a.seed, a.problems, [int(x) for x in a.meshes.split(",")])
     reqs = make_requests(pool, a.requests, a.seed)
     # warm the library (module loading, first launches) on one request
     run(hbsd, pool, reqs[:1], 1)
@@ -139,7 +160,7 @@ def main():
     gaps = rng.exponential(1.0 / (a.load * capacity), size=len(reqs))
     arrivals = np.cumsum(gaps) - gaps[0]
     served, t_served = run(hbsd, pool, reqs, a.slots, arrivals=arrivals)
-    single, t_single = run(hbsd, pool, reqs, 1)
+    single, t_single = run(hbsd, pool, reqs, 1) if not a.skip_one_slot else ([], float("nan"))
     lat = np.array([r["latency_ms"] for _, r in served])
     conv = sum(reqs[k][1] for k, r in served if r["status"] == 0 and r["res_max"] <= 1e-8)
     conv_closed = sum(reqs[k][1] for k, r in closed if r["status"] == 0 and r["res_max"] <= 1e-8)

@@ -115,3 +115,40 @@ def test_admission_and_errors(problems):
     with pytest.raises(hb().HbsdError):
         sv.submit(NEV, 1e-8, session_id=12345, want_vectors=False)
     sv.close()
+
+
+def test_bloch_requests_in_the_mix():
+    """Complex (Bloch) requests at several k-points of the 2 x 2 x 2 grid, in flight together
+    with a real one: each result equals, bit for bit, its solve alone on a complex session, and
+    a complex SCF follow-up (new H values, warm start) equals the same sequence on a session."""
+    kgrid = [(a * 0.5 * np.pi, b * 0.5 * np.pi, c * 0.5 * np.pi) for a in (1, -1) for b in (1, -1) for c in (1, -1)]
+    probs = [pi.generate(8, 2, 2, 0.25, 1, kpt=kgrid[0]), pi.generate(8, 2, 2, 0.25, 2, kpt=kgrid[3]),
+             pi.generate(8, 2, 2, 0.25, 1), pi.generate(10, 3, 2, 0.2, 3, kpt=kgrid[6])]
+    w = NEV + max(3, -(-NEV // 10))
+    starts, ref = [], []
+    for i, p in enumerate(probs):
+        X0 = (pi.seed_normal_block_complex(20 + i, p.n, w) if np.iscomplexobj(p.h_val)
+              else pi.seed_normal_block(20 + i, p.n, w))
+        starts.append(X0)
+        ref.append(alone(p, NEV, X0=X0))
+    sv = hb().Server(max_slots=4)
+    tickets = [sv.submit(NEV, 1e-8, problem=p, X0=X0) for p, X0 in zip(probs, starts)]
+    outs = [sv.wait(t) for t in tickets]
+    for k, (res, lam, X) in enumerate(outs):
+        lam0, X0v, it0, rc0 = ref[k]
+        assert res["status"] == 0 and rc0 == 0 and res["iters"] == it0
+        assert np.iscomplexobj(X) == np.iscomplexobj(probs[k].h_val)
+        assert np.array_equal(lam, lam0) and np.array_equal(X, X0v)
+    # complex follow-up of request 0
+    q1 = pi.generate(8, 2, 2, 0.25, 1, kpt=kgrid[0], v_noise=0.01, noise_seed=5)
+    sid = outs[0][0]["session_id"]
+    t = sv.submit(NEV, 1e-8, session_id=sid, H_val=q1.h_val, warm=True, n=probs[0].n, is_complex=True)
+    res, lam_f, X_f = sv.wait(t)
+    sv.close()
+    s = hb().Session.from_problem(probs[0])
+    s.solve(NEV, 1e-8, X0=starts[0])
+    s.update_H(q1.h_val)
+    lam_s, X_s, it_s, rc_s, _ = s.solve(NEV, 1e-8, warm=True)
+    s.close()
+    assert res["status"] == 0 and rc_s == 0 and res["iters"] == it_s
+    assert np.array_equal(lam_f, lam_s) and np.array_equal(X_f, X_s)
