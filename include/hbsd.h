@@ -137,6 +137,9 @@ typedef struct {
     int64_t neg_pivots;      /* negative pivots of the LDL^T factor of H_loc - eps_bar S: the
                                 number of eigenvalues of the local pencil below eps_bar
                                 (Sylvester's inertia; 0 when eps_bar lies below the spectrum) */
+    double gram_fma;         /* algorithmic multiply-adds of step 8 over the solve: n q (q+1)
+                                per call (both reduced matrices, one triangle each)            */
+    double update_fma;       /* algorithmic multiply-adds of steps 10-11: 3 n q w per call     */
 } hbsd_stats;
 
 typedef struct hbsd_handle hbsd_handle;

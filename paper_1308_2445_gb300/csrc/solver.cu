@@ -232,6 +232,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     HBSD_TRY(gram_step<T>(S, dfp, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, B.PsiH.p, ldw, (const T*)nullptr, 0, B.PsiS.p,
                       ldw, (const T*)nullptr, 0, n, C.HR.p, C.SR.p, st));
     tm.end(ti, st);
+    stt.gram_fma += (double)n * w * (w + 1);
     if (trace_on())
         std::fprintf(stderr, "[hbsd] %s start: Rayleigh-Ritz on the start block, nonfinite HR %d SR %d\n",
                      sizeof(T) == 4 ? "fp32" : "fp64", count_nonfinite(C.HR.p, (int64_t)w * w, st),
@@ -245,6 +246,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     HBSD_TRY(update_step<T>(S, dfp, B.PsiH.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
     HBSD_TRY(update_step<T>(S, dfp, B.PsiS.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
     tm.end(ti, st);
+    stt.update_fma += 3.0 * n * w * w;
     HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
     HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
     std::vector<double> res(m);
@@ -376,6 +378,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         HBSD_TRY(gram_step<T>(S, dfp, B.Psi.p, ldw, w, B.P.p, ldp, p, B.PsiH.p, ldw, B.PH.p, ldp, B.PsiS.p, ldw, B.PS.p, ldp,
                           n, C.HR.p, C.SR.p, st));
         tm.end(ti, st);
+        stt.gram_fma += (double)n * q * (q + 1);
         // step 9
         if (trace_on())
             std::fprintf(stderr, "[hbsd] %s it %d res_max %.3e p %d a %d nonfinite HR %d SR %d\n",
@@ -396,6 +399,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         HBSD_TRY(update_step<T>(S, dfp, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st, false));
         HBSD_TRY(update_step<T>(S, dfp, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st, false));
         tm.end(ti, st);
+        stt.update_fma += 3.0 * n * q * w;
         Eprev = E;
         HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
         HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
@@ -475,6 +479,7 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     stt.matvec_cols = stt.minres_spmm_cols = 0;
     stt.local_calls = 0;
     stt.precond_calls = 0;
+    stt.gram_fma = stt.update_fma = 0.0;
     StepTimer tm;
     std::vector<double> E(w), Eprev;
     SolveBufs<double>& B64 = S->sb;

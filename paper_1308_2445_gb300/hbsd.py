@@ -79,7 +79,8 @@ class hbsd_stats(C.Structure):
                 ("t_matvec_ms", C.c_double), ("t_resid_ms", C.c_double), ("t_precond_ms", C.c_double),
                 ("t_local_ms", C.c_double), ("t_gram_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_update_ms", C.c_double), ("matvec_cols", C.c_int64), ("minres_spmm_cols", C.c_int64),
-                ("precond_calls", C.c_int), ("local_calls", C.c_int64), ("neg_pivots", C.c_int64)]
+                ("precond_calls", C.c_int), ("local_calls", C.c_int64), ("neg_pivots", C.c_int64),
+                ("gram_fma", C.c_double), ("update_fma", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -48,3 +48,39 @@ def test_hbm_peak_falls_back_without_the_peaks_file(monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peak, source = bench.hbm_peak_gbs()
     assert peak == 6800.0 and "fallback" in source
+
+
+def test_double_float_update_dominant_is_an_fp32_issue_roofline():
+    st = stats(t_update_ms=2500.0, update_fma=3.0 * 334_272 * 538 * 282 * 46)
+    r = bench.roofline_object(st, 17_220_448, 0, 1.25e12, "mixed", "large", peak32=80e12)
+    assert r["kernel"] == "update" and r["bound"] == "alu"
+    instr = bench.DF_FP32_OPS * st["update_fma"]
+    assert r["achieved"] == pytest.approx(instr / 2.5 / 1e12)
+    assert r["peak"] == pytest.approx(40.0) and r["frac"] == pytest.approx(r["achieved"] / 40.0)
+    # the same step in the FP64 form is bound by the FP64 FMA rate
+    r64 = bench.roofline_object(st, 17_220_448, 0, 1.25e12, "fp64", "large", peak32=80e12)
+    assert r64["unit"] == "TFLOP/s" and r64["achieved"] == pytest.approx(2.0 * st["update_fma"] / 2.5 / 1e12)
+
+
+def test_oracle_sample_of_the_large_workload_scales_by_the_stored_runs(monkeypatch):
+    runs = {("medium", -1): {"nev": 64, "iters": 114, "oracle_seconds": 228.0},
+            ("large", -1): {"nev": 256, "iters": 46, "oracle_seconds": 4600.0}}
+    monkeypatch.setattr(bench, "golden", lambda w="medium", m0=-1, required=True: runs.get((w, m0)))
+    swl, snev, scale, its, how = bench.oracle_sample_plan("large", -1)
+    assert swl == "medium" and snev == 64 and its == 46
+    assert scale == pytest.approx((4600.0 / 46) / (228.0 / 114))
+    del runs[("large", -1)]
+    swl, snev, scale, its, how = bench.oracle_sample_plan("large", -1)
+    assert scale is None and "unscaled" in how
+
+
+def test_angles_at_gaps_sees_a_small_rotation():
+    import numpy as np
+    rng = np.random.default_rng(0)
+    Q, _ = np.linalg.qr(rng.standard_normal((200, 12)))
+    Xa = Q[:, :6]
+    Xb = Xa.copy()
+    Xb[:, 2] = np.cos(1e-7) * Xa[:, 2] + np.sin(1e-7) * Q[:, 8]
+    lam = np.array([1.0, 2.0, 3.0, 3.0000001, 5.0, 6.0])
+    got = bench.angles_at_gaps(Xa.T @ Xa, Xb.T @ Xb, Xa.T @ Xb, lam, 6)
+    assert abs(got - 1e-7) <= 2e-8
