@@ -18,7 +18,9 @@
 #include <algorithm>
 #include <array>
 #include <chrono>
+#include <mutex>
 #include <numeric>
+#include <type_traits>
 
 #include "common.h"
 
@@ -511,6 +513,150 @@ __global__ void __launch_bounds__(256) k_solve_gemm(const SnDev* __restrict__ sn
 #pragma unroll
         for (int v = 0; v < CPT; ++v) {
             const int j = tc + 16 * v;
+            if (j >= kc) continue;
+            if (it.nsplit > 1) {
+                part[(it.part_row + (int64_t)it.split * nout + o) * ldf + j0 + j] = acc[u][v];
+            } else if (BWD) {
+                X[(s.first + o) * ldx + j0 + j] = acc[u][v];
+            } else if (o < s.ns) {
+                Y[(s.first + o) * ldx + j0 + j] = acc[u][v];
+            } else {
+                fv[(s.fv_off + o) * ldf + j0 + j] += acc[u][v];
+            }
+        }
+    }
+}
+
+// ---- FP32 sweep products (the mixed form's step 6(a)) --------------------------------------------
+// The same work items as k_solve_gemm, for T = float, shaped for the FP32 pipes and for HBM:
+//  - a CTA computes a 64-row output tile for up to 32 TN columns of the right-hand sides, so for
+//    k <= 256 columns every panel entry is read from HBM once per sweep;
+//  - each thread holds an 8 x TN register tile (8 TN FMAs per 2 + TN/4 shared-memory vector loads);
+//  - panel and right-hand-side tiles are staged by cp.async, two stages in flight;
+//  - the forward sweep reads the column-major panels, the backward sweep a row-major copy, so both
+//    stream contiguous rows of the panel for consecutive output indices.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(pred ? 4 : 0));
+}
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, int src_bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+constexpr int SW_KT = 32;   // reduction rows per stage
+
+template <int TN>
+constexpr size_t sweep32_smem() { return (size_t)2 * SW_KT * (64 + 32 * TN) * sizeof(float); }
+
+// column of the thread's v-th accumulator: groups of 4 interleaved across the warp for TN >= 4
+// (each 16-byte shared load of a warp then covers 512 contiguous bytes), contiguous otherwise
+template <int TN>
+__device__ __forceinline__ int sweep_col(int cg, int v) {
+    return TN >= 4 ? (v >> 2) * 128 + cg * 4 + (v & 3) : cg * TN + v;
+}
+
+template <int TN, bool BWD>
+__global__ void __launch_bounds__(256) k_sweep32(const SnDev* __restrict__ sn, const SolveItem* __restrict__ items,
+                                                 const float* __restrict__ Gc, const float* __restrict__ Gr,
+                                                 const int64_t* __restrict__ srows, int p, float* __restrict__ fv,
+                                                 int64_t ldf, float* __restrict__ Y, float* __restrict__ X,
+                                                 int64_t ldx, float* __restrict__ part) {
+    constexpr int COLS = 32 * TN;
+    extern __shared__ __align__(16) float sw_smem[];
+    float* Gt = sw_smem;                      // [2][SW_KT][64]
+    float* Zt = sw_smem + 2 * SW_KT * 64;     // [2][SW_KT][COLS]
+    const SolveItem it = items[blockIdx.x];
+    const SnDev s = sn[it.sn];
+    const int nf = s.ns + s.nu;
+    const int j0 = blockIdx.y * COLS;
+    const int kc = min(COLS, p - j0);
+    const int nout = BWD ? s.ns : nf;
+    const int r8 = threadIdx.x >> 5;          // output rows r8*8 .. r8*8+7 of the tile
+    const int cg = threadIdx.x & 31;
+    // panel entry (reduction index k, output index o): forward G(o, k) column-major, backward
+    // G(k, o) from the row-major copy
+    const float* Gb = (BWD ? Gr : Gc) + s.L_off;
+    const int64_t gld = BWD ? s.ns : nf;
+
+    auto load_stage = [&](int buf, int kk) {
+        float* gt = Gt + buf * SW_KT * 64;
+        float* zt = Zt + buf * SW_KT * COLS;
+        for (int e = threadIdx.x; e < SW_KT * 64; e += 256) {
+            const int q = e >> 6, i = e & 63;
+            const int k = kk + q, o = it.t0 + i;
+            const bool ok = k < it.k1 && o < nout;
+            cp_async4(gt + e, ok ? Gb + (int64_t)k * gld + o : Gb, ok);
+        }
+        constexpr int V = COLS / 4;
+        for (int e = threadIdx.x; e < SW_KT * V; e += 256) {
+            const int q = e / V, j = (e % V) * 4;
+            const int k = kk + q;
+            int nb = 0;
+            const float* src = fv;   // 16-byte aligned; nothing is read when nb = 0
+            if (k < it.k1 && j < kc) {
+                nb = 4 * min(4, kc - j);
+                if (!BWD) src = fv + (s.fv_off + k) * ldf + j0 + j;
+                else src = (k < s.ns) ? Y + (s.first + k) * ldx + j0 + j
+                                      : X + srows[s.struct_off + k - s.ns] * ldx + j0 + j;
+            }
+            cp_async16(zt + q * COLS + j, src, nb);
+        }
+        cp_async_commit();
+    };
+
+    float acc[8][TN];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < TN; ++v) acc[u][v] = 0.f;
+    const int nk = (it.k1 - it.k0 + SW_KT - 1) / SW_KT;
+    load_stage(0, it.k0);
+    for (int t = 0; t < nk; ++t) {
+        if (t + 1 < nk) {
+            load_stage((t + 1) & 1, it.k0 + (t + 1) * SW_KT);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+        const float* gt = Gt + (t & 1) * SW_KT * 64 + r8 * 8;
+        const float* zt = Zt + (t & 1) * SW_KT * COLS;
+#pragma unroll 4
+        for (int q = 0; q < SW_KT; ++q) {
+            const float4 a0 = *reinterpret_cast<const float4*>(gt + q * 64);
+            const float4 a1 = *reinterpret_cast<const float4*>(gt + q * 64 + 4);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float b[TN];
+            if constexpr (TN >= 4) {
+#pragma unroll
+                for (int g = 0; g < TN / 4; ++g) {
+                    const float4 bv = *reinterpret_cast<const float4*>(zt + q * COLS + g * 128 + cg * 4);
+                    b[4 * g] = bv.x; b[4 * g + 1] = bv.y; b[4 * g + 2] = bv.z; b[4 * g + 3] = bv.w;
+                }
+            } else if constexpr (TN == 2) {
+                const float2 bv = *reinterpret_cast<const float2*>(zt + q * COLS + cg * 2);
+                b[0] = bv.x; b[1] = bv.y;
+            } else {
+                b[0] = zt[q * COLS + cg];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < TN; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int o = it.t0 + r8 * 8 + u;
+        if (o >= nout) continue;
+#pragma unroll
+        for (int v = 0; v < TN; ++v) {
+            const int j = sweep_col<TN>(cg, v);
             if (j >= kc) continue;
             if (it.nsplit > 1) {
                 part[(it.part_row + (int64_t)it.split * nout + o) * ldf + j0 + j] = acc[u][v];
@@ -1050,9 +1196,22 @@ __global__ void k_g_to_float_scaled(const SnDev* __restrict__ sn, const double* 
     }
 }
 
+// The same FP32 panel values row-major: entry (r, c) of a supernode's panel at L_off + r ns + c.
+__global__ void k_panel_transpose32(const SnDev* __restrict__ sn, const float* __restrict__ Gc,
+                                    float* __restrict__ Gr) {
+    const SnDev s = sn[blockIdx.y];
+    const int nf = s.ns + s.nu;
+    const int64_t total = (int64_t)nf * s.ns;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / s.ns), c = (int)(idx % s.ns);
+        Gr[s.L_off + idx] = Gc[s.L_off + (int64_t)c * nf + r];
+    }
+}
+
 int factor_make_fp32(Factor& f, const double* dscale, cudaStream_t st) {
     if (f.G32.p) return 0;
     HBSD_TRY(f.G32.alloc(f.G.n));
+    HBSD_TRY(f.G32T.alloc(f.G.n));
     const int nsn = (int)f.sn.size();
     int64_t maxp = 1;
     for (int q = 0; q < nsn; ++q) maxp = std::max<int64_t>(maxp, ((int64_t)f.sn[q].ns + f.sn[q].nu) * f.sn[q].ns);
@@ -1060,6 +1219,26 @@ int factor_make_fp32(Factor& f, const double* dscale, cudaStream_t st) {
     k_g_to_float_scaled<<<g, 256, 0, st>>>(reinterpret_cast<const SnDev*>(f.d_sn.p), f.G.p, f.perm.p, f.d_struct.p,
                                            dscale, f.G32.p);
     HBSD_CUDA(cudaPeekAtLastError());
+    k_panel_transpose32<<<g, 256, 0, st>>>(reinterpret_cast<const SnDev*>(f.d_sn.p), f.G32.p, f.G32T.p);
+    HBSD_CUDA(cudaPeekAtLastError());
+    return 0;
+}
+
+template <int TN, bool BWD>
+static int launch_sweep32(Session* s, Factor& f, dim3 g, const SolveItem* it, int k, float* fv, int64_t ld, float* Y,
+                          float* X, float* part, cudaStream_t st) {
+    constexpr size_t smem = sweep32_smem<TN>();
+    if (smem > 48 * 1024) {   // the cap, once: concurrent sessions never lower it under each other
+        static std::once_flag once;
+        static cudaError_t e = cudaSuccess;
+        std::call_once(once, [] {
+            e = cudaFuncSetAttribute(k_sweep32<TN, BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        HBSD_CUDA(e);
+    }
+    k_sweep32<TN, BWD><<<g, 256, smem, st>>>(reinterpret_cast<const SnDev*>(f.d_sn.p), it, f.G32.p, f.G32T.p,
+                                             f.d_struct.p, k, fv, ld, Y, X, ld, part);
+    HBSD_LAUNCHED(s);
     return 0;
 }
 
@@ -1097,9 +1276,31 @@ int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, in
     const bool narrow = k <= 16;
     const int rc = narrow ? 16 : 64;
     const int rchunks = ceil_div(k, rc);
+    // FP32: TN = columns per thread / 8 (32 TN columns per CTA)
+    const int tn = k <= 32 ? 1 : k <= 64 ? 2 : k <= 128 ? 4 : 8;
     auto gemm = [&](int h, bool bwd) -> int {
         const Factor::Sweep& sw = f.sweep[2 * h + (bwd ? 1 : 0)];
-        if (sw.n_items > 0) {
+        if (sw.n_items > 0 && std::is_same<T, float>::value && f.G32T.p) {
+            float* fv32 = reinterpret_cast<float*>(fv);
+            float* Y32 = reinterpret_cast<float*>(Y);
+            float* X32 = reinterpret_cast<float*>(X);
+            float* part32 = reinterpret_cast<float*>(part);
+            dim3 g(sw.n_items, ceil_div(k, 32 * tn));
+            const SolveItem* it = items + sw.item_off;
+            int rc = 0;
+            if (bwd) {
+                if (tn == 1) rc = launch_sweep32<1, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+                else if (tn == 2) rc = launch_sweep32<2, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+                else if (tn == 4) rc = launch_sweep32<4, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+                else rc = launch_sweep32<8, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+            } else {
+                if (tn == 1) rc = launch_sweep32<1, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+                else if (tn == 2) rc = launch_sweep32<2, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+                else if (tn == 4) rc = launch_sweep32<4, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+                else rc = launch_sweep32<8, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
+            }
+            HBSD_TRY(rc);
+        } else if (sw.n_items > 0) {
             dim3 g(sw.n_items, rchunks);
             const SolveItem* it = items + sw.item_off;
             if (bwd) {

@@ -178,6 +178,7 @@ struct Factor {
     // explicit panels G = [L11^{-1}; -L21 L11^{-1}] used by the solves (layout of L)
     DBuf<double> G;
     DBuf<float> G32;
+    DBuf<float> G32T;                            // the FP32 panels row-major (backward sweep)
     DBuf<int2> src;                              // extend-add sources of each front row (child 0, child 1)
     struct Sweep { int item_off, n_items, red_off, n_red; };
     std::vector<Sweep> sweep;                    // [2*level + (0 forward, 1 backward)]

@@ -356,7 +356,7 @@ def test_spmm_pair_f32_scaled(mid, k):
     assert np.allclose(1.0 / d ** 2, S.diagonal(), rtol=1e-12)
 
 
-@pytest.mark.parametrize("k", [1, 13, 64])
+@pytest.mark.parametrize("k", [1, 13, 64, 100, 200, 300])
 def test_precond_f32_scaled(mid, k):
     """FP32 preconditioner on the scaled pencil: P = -(D A D)^{-1} R, A = H - eps_bar S.
     Compared with the FP64 library solve in the energy norm of D A D (errors along its
@@ -399,3 +399,18 @@ def test_rayleigh_ritz_fallback_large(q, k, ndep):
     inf = host(info)
     assert fb and inf[0] == 1 and inf[1] == q - ndep
     assert np.abs(host(th) - g).max() <= 1e-8 * np.abs(g).max()
+
+
+def test_precond_f32_columns_independent_of_the_block_width(mid):
+    """Each column of the FP32 sweeps is reduced in the same order whatever the block width (the
+    CTA column tiles of 32, 64, 128 and 256 columns differ only in which columns share a tile), so a
+    column solved in a block of 300, 130, 37 or alone must come out bit for bit the same."""
+    p, s = mid
+    R = pi.seed_normal_block(77, p.n, 300)
+    P = fbuf(p.n, 300)
+    s.precond_apply_f32(fdev(R), P)
+    full = host(P)
+    for cols in ([5], [299], list(range(0, 37)), list(range(100, 230))):
+        Pk = fbuf(p.n, len(cols))
+        s.precond_apply_f32(fdev(R[:, cols]), Pk)
+        assert np.array_equal(host(Pk), full[:, cols]), cols[:3]
