@@ -282,6 +282,17 @@ int hbsd_onestep(hbsd_handle* h, const double* R, int64_t ldr, const double* e, 
 int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
               int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream);
 
+/* Tensor-core building block of the split-slice products: D = A B^T with A (M x K) and B (N x K)
+ * row-major bf16 (uint16 bit patterns), D (M x N) row-major FP32, all device pointers; one CTA per
+ * 128 rows of D issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory) on shared-memory
+ * tiles of 16 K-columns.  M a multiple of 128, N a multiple of 16 in [16, 256], K a multiple of 16
+ * (HBSD_ERR_ARG otherwise).  variant 0 is the operand layout the products use; variant 1 describes
+ * the same tiles with the descriptor's two core-matrix offsets exchanged (a layout check).
+ * HBSD_ERR_TIMEOUT if an MMA completion wait gives up (2 s).  Synchronous.  The paper has no
+ * counterpart: its products run on CPU BLAS. */
+int hbsd_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K, int variant,
+                      void* stream);
+
 /* Allocation-free form of hbsd_gram, for callers that must not allocate device memory:
  * a serving loop whose per-request path may not call cudaMalloc / cudaFree (both can
  * synchronise the whole device and stall the requests already in flight), or a host whose

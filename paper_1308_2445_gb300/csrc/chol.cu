@@ -552,11 +552,11 @@ constexpr int SW_KT = 32;   // reduction rows per stage
 template <int TN>
 constexpr size_t sweep32_smem() { return (size_t)2 * SW_KT * (64 + 32 * TN) * sizeof(float); }
 
-// column of the thread's v-th accumulator: groups of 4 interleaved across the warp for TN >= 4
+// column of the thread's v-th accumulator: for TN = 4 and 8 groups of 4 interleaved across the warp
 // (each 16-byte shared load of a warp then covers 512 contiguous bytes), contiguous otherwise
 template <int TN>
 __device__ __forceinline__ int sweep_col(int cg, int v) {
-    return TN >= 4 ? (v >> 2) * 128 + cg * 4 + (v & 3) : cg * TN + v;
+    return (TN % 4 == 0) ? (v >> 2) * 128 + cg * 4 + (v & 3) : cg * TN + v;
 }
 
 template <int TN, bool BWD>
@@ -631,17 +631,21 @@ __global__ void __launch_bounds__(256) k_sweep32(const SnDev* __restrict__ sn, c
             const float4 a1 = *reinterpret_cast<const float4*>(gt + q * 64 + 4);
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             float b[TN];
-            if constexpr (TN >= 4) {
+            if constexpr (TN % 4 == 0) {
 #pragma unroll
                 for (int g = 0; g < TN / 4; ++g) {
                     const float4 bv = *reinterpret_cast<const float4*>(zt + q * COLS + g * 128 + cg * 4);
                     b[4 * g] = bv.x; b[4 * g + 1] = bv.y; b[4 * g + 2] = bv.z; b[4 * g + 3] = bv.w;
                 }
-            } else if constexpr (TN == 2) {
-                const float2 bv = *reinterpret_cast<const float2*>(zt + q * COLS + cg * 2);
-                b[0] = bv.x; b[1] = bv.y;
-            } else {
-                b[0] = zt[q * COLS + cg];
+            } else if constexpr (TN % 2 == 0) {
+#pragma unroll
+                for (int g = 0; g < TN / 2; ++g) {
+                    const float2 bv = *reinterpret_cast<const float2*>(zt + q * COLS + cg * TN + 2 * g);
+                    b[2 * g] = bv.x; b[2 * g + 1] = bv.y;
+                }
+            } else {   // odd TN: scalar loads at an odd word stride, conflict-free
+#pragma unroll
+                for (int v = 0; v < TN; ++v) b[v] = zt[q * COLS + cg * TN + v];
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -1276,8 +1280,8 @@ int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, in
     const bool narrow = k <= 16;
     const int rc = narrow ? 16 : 64;
     const int rchunks = ceil_div(k, rc);
-    // FP32: TN = columns per thread / 8 (32 TN columns per CTA)
-    const int tn = k <= 32 ? 1 : k <= 64 ? 2 : k <= 128 ? 4 : 8;
+    // FP32: TN columns per thread, 32 TN per CTA, the smallest TN whose tile holds all k columns
+    const int tn = std::min(8, ceil_div(k, 32));
     auto gemm = [&](int h, bool bwd) -> int {
         const Factor::Sweep& sw = f.sweep[2 * h + (bwd ? 1 : 0)];
         if (sw.n_items > 0 && std::is_same<T, float>::value && f.G32T.p) {
@@ -1288,17 +1292,23 @@ int factor_solve(Session* s, Factor& f, const T* R, int64_t ldr, int k, T* P, in
             dim3 g(sw.n_items, ceil_div(k, 32 * tn));
             const SolveItem* it = items + sw.item_off;
             int rc = 0;
-            if (bwd) {
-                if (tn == 1) rc = launch_sweep32<1, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-                else if (tn == 2) rc = launch_sweep32<2, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-                else if (tn == 4) rc = launch_sweep32<4, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-                else rc = launch_sweep32<8, true>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-            } else {
-                if (tn == 1) rc = launch_sweep32<1, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-                else if (tn == 2) rc = launch_sweep32<2, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-                else if (tn == 4) rc = launch_sweep32<4, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-                else rc = launch_sweep32<8, false>(s, f, g, it, k, fv32, ld, Y32, X32, part32, st);
-            }
+            auto go = [&](auto tn_c, auto bwd_c) {
+                return launch_sweep32<decltype(tn_c)::value, decltype(bwd_c)::value>(s, f, g, it, k, fv32, ld, Y32,
+                                                                                      X32, part32, st);
+            };
+            auto pick = [&](auto bwd_c) {
+                switch (tn) {
+                    case 1: return go(std::integral_constant<int, 1>{}, bwd_c);
+                    case 2: return go(std::integral_constant<int, 2>{}, bwd_c);
+                    case 3: return go(std::integral_constant<int, 3>{}, bwd_c);
+                    case 4: return go(std::integral_constant<int, 4>{}, bwd_c);
+                    case 5: return go(std::integral_constant<int, 5>{}, bwd_c);
+                    case 6: return go(std::integral_constant<int, 6>{}, bwd_c);
+                    case 7: return go(std::integral_constant<int, 7>{}, bwd_c);
+                    default: return go(std::integral_constant<int, 8>{}, bwd_c);
+                }
+            };
+            rc = bwd ? pick(std::true_type{}) : pick(std::false_type{});
             HBSD_TRY(rc);
         } else if (sw.n_items > 0) {
             dim3 g(sw.n_items, rchunks);

@@ -356,7 +356,7 @@ def test_spmm_pair_f32_scaled(mid, k):
     assert np.allclose(1.0 / d ** 2, S.diagonal(), rtol=1e-12)
 
 
-@pytest.mark.parametrize("k", [1, 13, 64, 100, 200, 300])
+@pytest.mark.parametrize("k", [1, 13, 64, 90, 100, 150, 180, 200, 300])
 def test_precond_f32_scaled(mid, k):
     """FP32 preconditioner on the scaled pencil: P = -(D A D)^{-1} R, A = H - eps_bar S.
     Compared with the FP64 library solve in the energy norm of D A D (errors along its
