@@ -282,6 +282,18 @@ int hbsd_onestep(hbsd_handle* h, const double* R, int64_t ldr, const double* e, 
 int hbsd_gram(const double* Z, int64_t ldz, const double* ZH, int64_t ldzh, const double* ZS,
               int64_t ldzs, int64_t n, int q, double* HR, double* SR, void* stream);
 
+/* Steps 10-11 on the tensor cores: Y = [Z0 Z1] W with FP64 operands and result, computed from
+ * exact bf16 slices (8 six-bit digits per entry, against the largest entry of each row of Z0, of
+ * each row of Z1 and of each column of W's two row blocks) whose products of equal weight are
+ * summed exactly in FP32 tensor-memory accumulators (tcgen05.mma); products of weight below 2^-48
+ * are dropped.  Error per entry about 2^-46 (max|Z_g(i,:)| sum_k |W_g(k,j)| + sum_k |Z_g(i,k)|
+ * max|W_g(:,j)|) summed over the two blocks g: the accuracy of FP64 relative to each row's and
+ * column's largest entry (fixed point), where FP64 itself is relative per product.  Z0 n x q0 (ld0), Z1 n x q1 (ld1; q1 may be 0), W
+ * (q0 + q1) x k row-major (ld k), Y n x k (ldy), all device; Y must not overlap Z0 or Z1.
+ * 1 <= q0 <= 640, 0 <= q1 <= 640 (HBSD_ERR_ARG otherwise).  Synchronous. */
+int hbsd_update_oz(const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1,
+                   int64_t n, const double* W, int k, double* Y, int64_t ldy, void* stream);
+
 /* Tensor-core building block of the split-slice products: D = A B^T with A (M x K) and B (N x K)
  * row-major bf16 (uint16 bit patterns), D (M x N) row-major FP32, all device pointers; one CTA per
  * 128 rows of D issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory) on shared-memory

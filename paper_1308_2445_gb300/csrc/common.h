@@ -227,6 +227,9 @@ int gram2_df64(Session* s, const double* Z0, int64_t ld0, int q0, const double* 
                const double* S1, int64_t lds1, int64_t n, double* HR, double* SR, cudaStream_t st);
 int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
                  const double* W, int k, cudaStream_t st, bool split_w);
+// Y = [Z0 Z1] W on the tensor cores by exact bf16 slices (oz.cu); Y must not alias Z0 or Z1
+int update_oz(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
+              const double* W, int k, double* Y, int64_t ldy, cudaStream_t st);
 int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
                           double* W, int* info_host, cudaStream_t st, double drop_tol = 0.0);
 template <class T>
@@ -313,6 +316,7 @@ struct Session {
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel
     DBuf<float2> df_w;          // double-float copy of the Rayleigh-Ritz coefficients W
+    DBuf<double> oz_ws;         // split-slice update: exponents and bf16 slices of W (oz.cu)
     SolveBufs<double> sb;       // per-solve blocks, resident (grow only)
     SolveCommon sc;
     DBuf<double> io_x0, io_lam, io_x;   // host API staging of X0, lambda, X

@@ -1000,6 +1000,16 @@ int hbsd_gram_noalloc(const double* Z, int64_t ldz, const double* ZH, int64_t ld
     });
 }
 
+int hbsd_update_oz(const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
+                   const double* W, int k, double* Y, int64_t ldy, void* stream) {
+    return guarded([&]() -> int {
+        if (!Z0 || !W || !Y || (q1 > 0 && !Z1)) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ld0, q0) || (q1 > 0 && !ld_ok(ld1, q1)) || !ld_ok(ldy, k))
+            return fail(HBSD_ERR_ARG, "leading dimension below the block width");
+        return update_oz(scratch_session(), Z0, ld0, q0, Z1, ld1, q1, n, W, k, Y, ldy, (cudaStream_t)stream);
+    });
+}
+
 int hbsd_rayleigh_ritz(const double* HR, const double* SR, int q, int k, double* theta, double* W, int* info,
                        void* stream) {
     return guarded([&]() -> int {

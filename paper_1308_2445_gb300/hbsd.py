@@ -117,6 +117,8 @@ _SIGS = {
     "hbsd_precond_apply": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64]),
     "hbsd_minres": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int, C.c_double, C.c_int, _P, C.c_int64, _P]),
     "hbsd_gram": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int, _P, _P, _P]),
+    "hbsd_update_oz": (C.c_int, [_P, C.c_int64, C.c_int, _P, C.c_int64, C.c_int, C.c_int64, _P, C.c_int, _P,
+                                 C.c_int64, _P]),
     "hbsd_tc_gemm_bf16": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P]),
     "hbsd_gram_noalloc": (C.c_int, [_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, C.c_int64, C.c_int, _P, _P, _P]),
     "hbsd_rayleigh_ritz": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
