@@ -90,7 +90,7 @@ typedef struct {
 
 /* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
  * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,
- * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar). */
+ * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar), tc_update = 1. */
 typedef struct {
     double sigma_bar;   /* global shift eps_bar of K = (H - eps_bar S)^{-1}; must lie below the spectrum */
     double sigma0;      /* shift making H - sigma0 S positive definite (Sec. 5); NaN -> sigma_bar        */
@@ -103,6 +103,9 @@ typedef struct {
     int precond;        /* HBSD_PRECOND_*                                                               */
     uint64_t seed;      /* seed of the SplitMix64 normals used when X0 is NULL                           */
     int local_solver;   /* HBSD_LOCAL_* (default MINRES)                                                */
+    int tc_update;      /* mixed form: 1 (default) runs steps 10-11 on the tensor cores from exact bf16
+                           slices (as hbsd_update_oz) while q <= 640, 0 in double-float on the FP32
+                           pipes; the FP64 form ignores it                                              */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */

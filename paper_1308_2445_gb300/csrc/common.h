@@ -228,8 +228,11 @@ int gram2_df64(Session* s, const double* Z0, int64_t ld0, int q0, const double* 
 int update2_df64(Session* s, double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
                  const double* W, int k, cudaStream_t st, bool split_w);
 // Y = [Z0 Z1] W on the tensor cores by exact bf16 slices (oz.cu); Y must not alias Z0 or Z1
+// status: device int that a timed-out MMA wait sets to 1 (the call is then asynchronous), or NULL
+// (the call checks its own flag and synchronises)
 int update_oz(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
-              const double* W, int k, double* Y, int64_t ldy, cudaStream_t st);
+              const double* W, int k, double* Y, int64_t ldy, cudaStream_t st, int* status = nullptr);
+constexpr int OZ_MAX_Q_SEG = 640;   // largest block width update_oz takes
 int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q, int k, double* theta,
                           double* W, int* info_host, cudaStream_t st, double drop_tol = 0.0);
 template <class T>
@@ -285,6 +288,7 @@ struct Nonlocal {
 template <class T>
 struct SolveBufs {
     DBuf<T> Psi, PsiH, PsiS, P, PH, PS, RU, Xa, Ra, shifts;
+    DBuf<T> upd;                // out-of-place target of the tensor-core update, swapped in
 };
 
 struct SolveCommon {
@@ -317,6 +321,7 @@ struct Session {
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel
     DBuf<float2> df_w;          // double-float copy of the Rayleigh-Ritz coefficients W
     DBuf<double> oz_ws;         // split-slice update: exponents and bf16 slices of W (oz.cu)
+    DBuf<int> oz_status;        // set by a timed-out MMA wait of the solve's tensor-core updates
     SolveBufs<double> sb;       // per-solve blocks, resident (grow only)
     SolveCommon sc;
     DBuf<double> io_x0, io_lam, io_x;   // host API staging of X0, lambda, X

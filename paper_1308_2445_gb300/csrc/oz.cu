@@ -14,9 +14,8 @@
 // operands' truncation).  The segments run one after the other on the same accumulators with
 // their own row scales, so a row whose P entries are far larger than its Psi entries (directions
 // K r carry large components along the near-null space of S) loses nothing on its Psi part.  After
-// each segment the epilogue adds its levels in integer arithmetic (levels 0-5 are exact multiples
-// of 2^-30 of the leading unit; the shared accumulator is rounded there) and applies the scales in
-// FP64.
+// each segment the epilogue adds its levels 0-5 in integer arithmetic (exact multiples of 2^-30
+// of the leading unit), then the shared accumulator of levels 6-8 and the scales in FP64.
 #include <algorithm>
 #include <mutex>
 #include <string>
@@ -27,17 +26,20 @@
 namespace hbsd {
 namespace {
 
-constexpr int OZ_N = 48;                        // output columns per CTA (N of every MMA)
+constexpr int OZ_N = 64;                        // output columns per CTA (N of every MMA)
 constexpr int OZ_DIG = 8;                       // 6-bit digits per operand
 constexpr int OZ_ACC = 7;                       // accumulators: levels 0..5 exact, 6..8 shared
 constexpr int OZ_LMAX = 8;                      // highest level kept (pairs of digits a + b <= 8)
-constexpr int OZ_THREADS = 256;
+constexpr int OZ_SLICERS = 256;                 // warps 0-7: slicing and epilogue
+constexpr int OZ_THREADS = OZ_SLICERS + 32;     // warp 8: MMA issue
+constexpr int OZ_NS = 3;                        // stage buffers
 constexpr int OZ_A_SLICE = 128 * 16 * 2;        // bytes of one 128 x 16 bf16 slice tile
 constexpr int OZ_B_SLICE = OZ_N * 16 * 2;       // bytes of one OZ_N x 16 bf16 slice tile
 constexpr int OZ_STAGE = OZ_DIG * (OZ_A_SLICE + OZ_B_SLICE);
-constexpr uint32_t OZ_TMEM_COLS = 512;          // 7 accumulators x 48 columns = 336 (power of 2 above)
+constexpr uint32_t OZ_TMEM_COLS = 512;          // 7 accumulators, one per 64 columns
+constexpr int OZ_ACC_STRIDE = 64;               // TMEM column stride between accumulators
 constexpr uint64_t OZ_WAIT_NS = 2000000000ull;
-constexpr int OZ_MAX_Q = 640;                   // per segment: keeps the level-5 sums below 2^24
+constexpr int OZ_MAX_Q = OZ_MAX_Q_SEG;          // per segment: keeps the level-5 sums below 2^24
 
 struct OzSeg {
     const double* Z;        // n x q, ld
@@ -70,6 +72,21 @@ __device__ __forceinline__ uint32_t digit_bf16(unsigned long long F, int s, bool
     const uint32_t d = (uint32_t)(F >> (42 - 6 * s)) & 63u;
     const float v = (float)d * __uint_as_float((uint32_t)(127 - 6 * s) << 23);
     return (__float_as_uint(v) >> 16) | (neg && d ? 0x8000u : 0u);
+}
+
+// bf16 bits of the 8 digits of x (without integer-to-float conversions: d | 0x4B000000 read as a
+// float is 2^23 + d exactly)
+__device__ __forceinline__ void digits8(double x, int emax, uint32_t (&bits)[OZ_DIG]) {
+    bool neg;
+    const unsigned long long F = fixed48(x, emax, &neg);
+    const uint32_t hi = (uint32_t)(F >> 24), lo = (uint32_t)F & 0xFFFFFFu;
+    const uint32_t sgn = neg ? 0x8000u : 0u;
+#pragma unroll
+    for (int s = 0; s < OZ_DIG; ++s) {
+        const uint32_t d = (s < 4 ? (hi >> (18 - 6 * s)) : (lo >> (18 - 6 * (s - 4)))) & 63u;
+        const float f = (__uint_as_float(0x4B000000u | d) - 8388608.0f) * __uint_as_float((uint32_t)(127 - 6 * s) << 23);
+        bits[s] = (__float_as_uint(f) >> 16) | (d ? sgn : 0u);
+    }
 }
 
 // rowexp[i] = exponent field of max_k |Z(i, k)|
@@ -112,11 +129,20 @@ __global__ void k_oz_wslices(const double* __restrict__ W, int k, int r0, int q,
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(tc::smem_u32(mbar)) : "memory");
+}
+
+// Warp roles: warps 0-7 (OZ_SLICERS threads) slice Z into the stage buffers, load the W slices and
+// run the epilogue; warp 8 issues the MMAs (lane 0).  Stages cycle through OZ_NS buffers: full[s]
+// completes when the slicers have filled stage s, empty[s] when the MMAs that read it are done.
+// segdone completes when a segment's MMAs are done; accfree when the slicers have read its
+// accumulators, before the next segment overwrites them.
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_update_oz(OzSeg s0, OzSeg s1, int64_t n, int k, int kpad,
                                                               double* __restrict__ Y, int64_t ldy,
                                                               int* __restrict__ status) {
     extern __shared__ __align__(1024) uint8_t oz_smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[OZ_NS], empty[OZ_NS], segdone, accfree;
     __shared__ uint32_t tslot;
     __shared__ int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -124,8 +150,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_update_oz(OzSeg s0, OzSeg s1,
     const int j0 = blockIdx.y * OZ_N;
     uint8_t* base = oz_smem + ((1024 - (tc::smem_u32(oz_smem) & 1023)) & 1023);   // 1 KB aligned
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int i = 0; i < OZ_NS; ++i) {
+            tc::mbar_init(&full[i], OZ_SLICERS);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(&segdone, 1);
+        tc::mbar_init(&accfree, OZ_SLICERS);
         s_fail = 0;
     }
     if (warp == 0) tc::tmem_alloc(&tslot, OZ_TMEM_COLS);
@@ -133,62 +163,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_update_oz(OzSeg s0, OzSeg s1,
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tslot;
-    const uint32_t idesc = tc::idesc_bf16_f32(128, OZ_N);
-    // A slicing: thread -> (row, half of the 16 columns); epilogue: warp w -> TMEM lanes
-    // (w % 4) * 32 .. +31 (rows), column half w / 4 (24 columns)
-    const int arow = tid >> 1, ahalf = tid & 1;
-    const int64_t agrow = row0 + arow;
-    const int er = (warp & 3) * 32 + lane, ch = warp >> 2;
-    const int64_t egrow = row0 + er;
-    const uint32_t lane_addr = tbase + ((uint32_t)((warp & 3) * 32) << 16);
-    double y[24];
-#pragma unroll
-    for (int v = 0; v < 24; ++v) y[v] = 0.0;
-    int t = 0;   // stage counter over both segments (buffer t & 1, its mbarrier phase t >> 1)
-    for (int g = 0; g < 2; ++g) {
-        const OzSeg& sg = g ? s1 : s0;
-        const int nk = (sg.q + 15) / 16;
-        if (nk == 0) continue;
-        const int emax_a = agrow < n ? sg.rowexp[agrow] : 0;
-        uint32_t init_mask = 0;   // thread 0: accumulators written in this segment
-        for (int step = 0; step < nk; ++step, ++t) {
-            const int buf = t & 1;
-            const int kk = step * 16;
-            uint8_t* stA = base + buf * OZ_STAGE;
-            uint8_t* stB = stA + OZ_DIG * OZ_A_SLICE;
-            // the MMAs that read this buffer two stages ago are done
-            if (t >= 2 && !tc::mbar_wait(&mbar[buf], (uint32_t)(((t - 2) >> 1) & 1), OZ_WAIT_NS)) s_fail = 1;
-            {   // A slices: the 8 digits of 8 consecutive entries of one row
-                uint32_t packed[OZ_DIG][4];
-#pragma unroll
-                for (int c = 0; c < 8; c += 2) {
-                    const int col0 = kk + ahalf * 8 + c;
-                    const double x0 = (agrow < n && col0 < sg.q) ? sg.Z[agrow * sg.ld + col0] : 0.0;
-                    const double x1 = (agrow < n && col0 + 1 < sg.q) ? sg.Z[agrow * sg.ld + col0 + 1] : 0.0;
-                    bool ng0, ng1;
-                    const unsigned long long F0 = fixed48(x0, emax_a, &ng0), F1 = fixed48(x1, emax_a, &ng1);
-#pragma unroll
-                    for (int d = 0; d < OZ_DIG; ++d)
-                        packed[d][c >> 1] = digit_bf16(F0, d, ng0) | (digit_bf16(F1, d, ng1) << 16);
+    const int n0 = (s0.q + 15) / 16, n1 = (s1.q + 15) / 16, total = n0 + n1;
+
+    if (warp == OZ_SLICERS / 32) {   // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(128, OZ_N);
+            uint32_t init_mask = 0;
+            for (int t = 0; t < total; ++t) {
+                const int st = t % OZ_NS;
+                if (t == n0) {   // the slicers have read segment 0's accumulators
+                    if (!tc::mbar_wait(&accfree, 0u, OZ_WAIT_NS)) { s_fail = 1; break; }
+                    init_mask = 0;
                 }
-                const uint32_t off = (uint32_t)(ahalf * 128 + (arow >> 3) * 256 + (arow & 7) * 16);
-#pragma unroll
-                for (int d = 0; d < OZ_DIG; ++d)
-                    *reinterpret_cast<uint4*>(stA + d * OZ_A_SLICE + off) =
-                        make_uint4(packed[d][0], packed[d][1], packed[d][2], packed[d][3]);
-            }
-            // B slices: rows j0 .. j0 + OZ_N of every digit plane, 16 columns, as 16-byte halves
-            for (int e = tid; e < OZ_DIG * OZ_N * 2; e += OZ_THREADS) {
-                const int d = e / (OZ_N * 2), rem = e % (OZ_N * 2), jr = rem >> 1, hf = rem & 1;
-                const uint4 v =
-                    *reinterpret_cast<const uint4*>(sg.B + ((int64_t)d * kpad + j0 + jr) * sg.qpad + kk + hf * 8);
-                *reinterpret_cast<uint4*>(stB + d * OZ_B_SLICE + hf * 128 + (jr >> 3) * 256 + (jr & 7) * 16) = v;
-            }
-            tc::fence_proxy_async();
-            __syncthreads();
-            if (s_fail) break;
-            if (tid == 0) {
+                if (!tc::mbar_wait(&full[st], (uint32_t)((t / OZ_NS) & 1), OZ_WAIT_NS)) { s_fail = 1; break; }
                 tc::fence_after_sync();
+                uint8_t* stA = base + st * OZ_STAGE;
+                uint8_t* stB = stA + OZ_DIG * OZ_A_SLICE;
 #pragma unroll 1
                 for (int a = 0; a < OZ_DIG; ++a) {
                     const uint64_t ad = tc::smem_desc(tc::smem_u32(stA + a * OZ_A_SLICE), 128, 256);
@@ -196,69 +186,137 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_update_oz(OzSeg s0, OzSeg s1,
                     for (int b = 0; b < OZ_DIG && a + b <= OZ_LMAX; ++b) {
                         const int acc = min(a + b, OZ_ACC - 1);
                         const uint64_t bd = tc::smem_desc(tc::smem_u32(stB + b * OZ_B_SLICE), 128, 256);
-                        tc::mma_bf16(tbase + (uint32_t)(acc * OZ_N), ad, bd, idesc, (init_mask >> acc) & 1u);
+                        tc::mma_bf16(tbase + (uint32_t)(acc * OZ_ACC_STRIDE), ad, bd, idesc, (init_mask >> acc) & 1u);
                         init_mask |= 1u << acc;
                     }
                 }
-                tc::mma_commit(&mbar[buf]);
+                tc::mma_commit(&empty[st]);
+                if (t == n0 - 1 || t == total - 1) tc::mma_commit(&segdone);
             }
         }
-        if (s_fail) break;
-        // the segment's last commit covers all its MMAs
-        if (!tc::mbar_wait(&mbar[(t - 1) & 1], (uint32_t)(((t - 1) >> 1) & 1), OZ_WAIT_NS)) s_fail = 1;
-        __syncthreads();
-        if (s_fail) break;
-        tc::fence_after_sync();
-        // fold the segment in: levels 0-5 are exact multiples of 2^-30, the shared 6-8 accumulator
-        // is rounded there; z w = 2^(E_r + E_c - 12) sum_L D_L with E = exponent field - 1022
-        const int e_row = egrow < n ? sg.rowexp[egrow] : 0;
+    } else {   // ---- slicers and epilogue
+        const int arow = tid >> 1, ahalf = tid & 1;
+        const int64_t agrow = row0 + arow;
+        const int er = (warp & 3) * 32 + lane, ch = warp >> 2;   // epilogue: row, column half (32 columns)
+        const int64_t egrow = row0 + er;
+        const uint32_t lane_addr = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+        double y[32];
 #pragma unroll
-        for (int c0 = 0; c0 < 24; c0 += 8) {
-            long long I[8];
+        for (int v = 0; v < 32; ++v) y[v] = 0.0;
+        int segs = 0;
+        for (int t = 0; t < total; ++t) {
+            const int st = t % OZ_NS;
+            const int g = t < n0 ? 0 : 1;
+            const OzSeg& sg = g ? s1 : s0;
+            const int kk = (g ? t - n0 : t) * 16;
+            uint8_t* stA = base + st * OZ_STAGE;
+            uint8_t* stB = stA + OZ_DIG * OZ_A_SLICE;
+            if (t >= OZ_NS && !tc::mbar_wait(&empty[st], (uint32_t)((t / OZ_NS - 1) & 1), OZ_WAIT_NS)) {
+                s_fail = 1;
+                break;
+            }
+            {   // A slices: the 8 digits of the thread's 8 entries of its row
+                const int emax_a = agrow < n ? sg.rowexp[agrow] : 0;
+                double x[8];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) I[v] = 0;
+                for (int c = 0; c < 8; ++c) {
+                    const int col = kk + ahalf * 8 + c;
+                    x[c] = (agrow < n && col < sg.q) ? sg.Z[agrow * sg.ld + col] : 0.0;
+                }
+                uint32_t packed[OZ_DIG][4];
 #pragma unroll
-            for (int a = 0; a < OZ_ACC; ++a) {
-                uint32_t rr[8];
-                const uint32_t ta = lane_addr + (uint32_t)(a * OZ_N + ch * 24 + c0);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-                             : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
-                               "=r"(rr[6]), "=r"(rr[7])
-                             : "r"(ta));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                for (int c = 0; c < 8; c += 2) {
+                    uint32_t b0[OZ_DIG], b1[OZ_DIG];
+                    digits8(x[c], emax_a, b0);
+                    digits8(x[c + 1], emax_a, b1);
 #pragma unroll
-                for (int v = 0; v < 8; ++v) I[v] += __float2ll_rn(__uint_as_float(rr[v]) * 1073741824.0f);
+                    for (int d = 0; d < OZ_DIG; ++d) packed[d][c >> 1] = b0[d] | (b1[d] << 16);
+                }
+                const uint32_t off = (uint32_t)(ahalf * 128 + (arow >> 3) * 256 + (arow & 7) * 16);
+#pragma unroll
+                for (int d = 0; d < OZ_DIG; ++d)
+                    *reinterpret_cast<uint4*>(stA + d * OZ_A_SLICE + off) =
+                        make_uint4(packed[d][0], packed[d][1], packed[d][2], packed[d][3]);
             }
 #pragma unroll
-            for (int v = 0; v < 8; ++v) {
-                const int j = j0 + ch * 24 + c0 + v;
-                if (j < k) y[c0 + v] += ldexp((double)I[v], e_row + sg.colexp[j] - 2044 - 12 - 30);
+            for (int i = 0; i < OZ_DIG * OZ_N * 2 / OZ_SLICERS; ++i) {   // B slices: 16-byte halves of rows
+                const int e = tid + OZ_SLICERS * i;
+                const int d = e / (OZ_N * 2), rem = e % (OZ_N * 2), jr = rem >> 1, hf = rem & 1;
+                *reinterpret_cast<uint4*>(stB + d * OZ_B_SLICE + hf * 128 + (jr >> 3) * 256 + (jr & 7) * 16) =
+                    *reinterpret_cast<const uint4*>(sg.B + ((int64_t)d * kpad + j0 + jr) * sg.qpad + kk + hf * 8);
+            }
+            tc::fence_proxy_async();
+            mbar_arrive(&full[st]);
+            if (t == n0 - 1 || t == total - 1) {
+                // fold the segment in: levels 0-5 are exact multiples of 2^-30 (summed as integers),
+                // the shared 6-8 accumulator is added in FP64; z w = 2^(E_r + E_c - 12) sum_L D_L,
+                // E = exponent field - 1022
+                if (!tc::mbar_wait(&segdone, (uint32_t)(segs & 1), OZ_WAIT_NS)) {
+                    s_fail = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const int e_row = egrow < n ? sg.rowexp[egrow] : 0;
+#pragma unroll
+                for (int c0 = 0; c0 < 32; c0 += 8) {
+                    long long I[8];
+                    float lowlev[8];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) I[v] = 0;
+#pragma unroll
+                    for (int a = 0; a < OZ_ACC; ++a) {
+                        uint32_t rr[8];
+                        const uint32_t ta = lane_addr + (uint32_t)(a * OZ_ACC_STRIDE + ch * 32 + c0);
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                                     : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
+                                       "=r"(rr[6]), "=r"(rr[7])
+                                     : "r"(ta));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                        if (a < OZ_ACC - 1) {
+#pragma unroll
+                            for (int v = 0; v < 8; ++v)
+                                I[v] += __float2ll_rn(__uint_as_float(rr[v]) * 1073741824.0f);
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < 8; ++v) lowlev[v] = __uint_as_float(rr[v]);
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const int j = j0 + ch * 32 + c0 + v;
+                        if (j < k) {
+                            const int sc = e_row + sg.colexp[j] - 2044 - 12;
+                            y[c0 + v] += ldexp((double)I[v], sc - 30) + ldexp((double)lowlev[v], sc);
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                mbar_arrive(&accfree);
+                ++segs;
             }
         }
-        // every thread has read the accumulators before the next segment overwrites them
-        tc::fence_before_sync();
-        __syncthreads();
-    }
-    if (!s_fail && egrow < n) {
+        if (!s_fail && egrow < n) {
 #pragma unroll
-        for (int v = 0; v < 24; ++v) {
-            const int j = j0 + ch * 24 + v;
-            if (j < k) Y[egrow * ldy + j] = y[v];
+            for (int v = 0; v < 32; ++v) {
+                const int j = j0 + ch * 32 + v;
+                if (j < k) Y[egrow * ldy + j] = y[v];
+            }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tbase, OZ_TMEM_COLS);
     if (tid == 0 && s_fail) atomicExch(status, 1);
 }
 
 }  // namespace
 
-size_t oz_smem_bytes() { return (size_t)2 * OZ_STAGE + 1024; }
+size_t oz_smem_bytes() { return (size_t)OZ_NS * OZ_STAGE + 1024; }
 
 // Y (n x k, ld ldy; may not alias Z0, Z1) = [Z0 Z1] W, W (q0 + q1) x k row-major (ld k), device.
 int update_oz(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z1, int64_t ld1, int q1, int64_t n,
-              const double* W, int k, double* Y, int64_t ldy, cudaStream_t st) {
+              const double* W, int k, double* Y, int64_t ldy, cudaStream_t st, int* status_out) {
     if (q0 < 1 || q1 < 0 || q0 > OZ_MAX_Q || q1 > OZ_MAX_Q || k < 1 || n < 1)
         return fail(HBSD_ERR_ARG, "update_oz: need 1 <= q0 <= 640, 0 <= q1 <= 640, k >= 1, n >= 1");
     const int kpad = (int)round_up(k, OZ_N);
@@ -275,7 +333,8 @@ int update_oz(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z
     int* status = ce1 + kpad;
     uint16_t* B0 = reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(s->oz_ws.p) + ((ints * 4 + 63) / 64) * 64);
     uint16_t* B1 = B0 + bsl0;
-    HBSD_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    if (status_out) status = status_out;
+    else HBSD_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
     const int rows_per_block = 8;
     k_oz_rowexp<<<ceil_div(n, rows_per_block), 32 * rows_per_block, 0, st>>>(Z0, ld0, q0, n, re0);
     HBSD_LAUNCHED(s);
@@ -300,6 +359,7 @@ int update_oz(Session* s, const double* Z0, int64_t ld0, int q0, const double* Z
     dim3 grid(ceil_div(n, 128), kpad / OZ_N);
     k_update_oz<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(a, b, n, k, kpad, Y, ldy, status);
     HBSD_LAUNCHED(s);
+    if (status_out) return 0;
     int h = 0;
     HBSD_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     HBSD_CUDA(cudaStreamSynchronize(st));

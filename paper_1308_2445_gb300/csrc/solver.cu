@@ -176,6 +176,12 @@ static int gram_step(Session* S, bool df, const T* Z0, int64_t ld0, int q0, cons
     }
     return gram2<T>(S, Z0, ld0, q0, Z1, ld1, q1, H0, ldh0, H1, ldh1, S0, lds0, S1, lds1, n, HR, SR, st);
 }
+// Steps 10-11 for one block: Zb(:, 0:k) := [Zb Z1] W.  With tc, on the tensor cores from exact bf16
+// slices into the spare block, which then takes Zb's place (k = q0: every column is replaced).
+template <class T>
+static int update_block(Session* S, bool df, bool tc, SolveBufs<T>& B, DBuf<T>& Zb, int64_t ld0, int q0,
+                        const T* Z1, int64_t ld1, int q1, int64_t n, const double* W, int k, cudaStream_t st,
+                        bool first);
 template <class T>
 static int update_step(Session* S, bool df, T* Z0, int64_t ld0, int q0, const T* Z1, int64_t ld1, int q1, int64_t n,
                        const double* W, int k, cudaStream_t st, bool first) {
@@ -184,6 +190,22 @@ static int update_step(Session* S, bool df, T* Z0, int64_t ld0, int q0, const T*
     }
     (void)first;
     return update2<T>(S, Z0, ld0, q0, Z1, ld1, q1, n, W, k, st);
+}
+
+template <class T>
+static int update_block(Session* S, bool df, bool tc, SolveBufs<T>& B, DBuf<T>& Zb, int64_t ld0, int q0,
+                        const T* Z1, int64_t ld1, int q1, int64_t n, const double* W, int k, cudaStream_t st,
+                        bool first) {
+    if constexpr (std::is_same<T, double>::value) {
+        if (tc && k == q0 && q0 <= OZ_MAX_Q_SEG && q1 <= OZ_MAX_Q_SEG) {
+            HBSD_TRY(B.upd.alloc((size_t)n * ld0));
+            HBSD_TRY(update_oz(S, Zb.p, ld0, q0, Z1, ld1, q1, n, W, k, B.upd.p, ld0, st, S->oz_status.p));
+            std::swap(Zb.p, B.upd.p);
+            std::swap(Zb.n, B.upd.n);
+            return 0;
+        }
+    }
+    return update_step<T>(S, df, Zb.p, ld0, q0, Z1, ld1, q1, n, W, k, st, first);
 }
 
 // ---- per-solve buffers -----------------------------------------------------------------------
@@ -222,6 +244,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     // carry ~1e-7 relative noise.
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
     const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
+    const bool tcu = o.precision == HBSD_PRECISION_MIXED && o.tc_update != 0;   // tensor-core update
     bool certified = false;   // Psi_H, Psi_S freshly recomputed in FP64 (mixed form)
     // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
     ti = tm.begin(StepTimer::MATVEC, st);
@@ -242,9 +265,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     tm.end(ti, st);
     stt.rr_fallbacks += info[0];
     ti = tm.begin(StepTimer::UPDATE, st);
-    HBSD_TRY(update_step<T>(S, dfp, B.Psi.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, true));
-    HBSD_TRY(update_step<T>(S, dfp, B.PsiH.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
-    HBSD_TRY(update_step<T>(S, dfp, B.PsiS.p, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
+    HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, true));
+    HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiH, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
+    HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiS, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
     tm.end(ti, st);
     stt.update_fma += 3.0 * n * w * w;
     HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
@@ -395,9 +418,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                          count_nonfinite(C.theta.p, w, st), count_nonfinite(C.W.p, (int64_t)q * w, st));
         // steps 10-11
         ti = tm.begin(StepTimer::UPDATE, st);
-        HBSD_TRY(update_step<T>(S, dfp, B.Psi.p, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st, true));
-        HBSD_TRY(update_step<T>(S, dfp, B.PsiH.p, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st, false));
-        HBSD_TRY(update_step<T>(S, dfp, B.PsiS.p, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st, false));
+        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st, true));
+        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiH, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st, false));
+        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiS, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st, false));
         tm.end(ti, st);
         stt.update_fma += 3.0 * n * q * w;
         Eprev = E;
@@ -472,6 +495,8 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
         HBSD_TRY(S->ws.alloc((size_t)2 * 1024 * (1216 + tiles * tiles) + (size_t)304 * 2 * qmax + 1024));
         HBSD_TRY(S->rr_info.alloc(4));
     }
+    HBSD_TRY(S->oz_status.alloc(1));
+    HBSD_CUDA(cudaMemsetAsync(S->oz_status.p, 0, sizeof(int), st));
     hbsd_stats& stt = S->stats;
     stt.iters = stt.iters_fp64 = 0;
     stt.minres_steps = stt.precond_cols = stt.local_cols = 0;
@@ -527,7 +552,10 @@ static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t
     HBSD_CUDA(cudaMemcpyAsync(S->psi_keep.p, B64.Psi.p, n * ldw * 8, cudaMemcpyDeviceToDevice, st));
     S->keep_w = w;
     S->keep_ld = ldw;
+    int oz_fail = 0;
+    HBSD_CUDA(cudaMemcpyAsync(&oz_fail, S->oz_status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     HBSD_CUDA(cudaStreamSynchronize(st));
+    if (oz_fail) return fail(HBSD_ERR_TIMEOUT, "tensor-core update: an MMA completion wait gave up");
     if (iters_out) *iters_out = iters;
     return conv ? HBSD_OK : HBSD_NOT_CONVERGED;
 }
@@ -554,6 +582,7 @@ void hbsd_options_default(hbsd_options* opt) {
     opt->precond = HBSD_PRECOND_HYBRID;
     opt->seed = 1;
     opt->local_solver = HBSD_LOCAL_MINRES;
+    opt->tc_update = 1;
 }
 
 const char* hbsd_status_string(int status) {
