@@ -90,7 +90,8 @@ typedef struct {
 
 /* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
  * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,
- * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar), tc_update = 1. */
+ * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar), tc_update = 0,
+ * update_hs = 0. */
 typedef struct {
     double sigma_bar;   /* global shift eps_bar of K = (H - eps_bar S)^{-1}; must lie below the spectrum */
     double sigma0;      /* shift making H - sigma0 S positive definite (Sec. 5); NaN -> sigma_bar        */
@@ -103,9 +104,16 @@ typedef struct {
     int precond;        /* HBSD_PRECOND_*                                                               */
     uint64_t seed;      /* seed of the SplitMix64 normals used when X0 is NULL                           */
     int local_solver;   /* HBSD_LOCAL_* (default MINRES)                                                */
-    int tc_update;      /* mixed form: 1 (default) runs steps 10-11 on the tensor cores from exact bf16
-                           slices (as hbsd_update_oz) while q <= 640, 0 in double-float on the FP32
-                           pipes; the FP64 form ignores it                                              */
+    int tc_update;      /* mixed form, experimental: 1 runs steps 10-11 on the tensor cores from exact
+                           bf16 slices (as hbsd_update_oz) while q <= 640; 0 (default) in double-float
+                           on the FP32 pipes.  The slices are fixed point against each row's largest
+                           entry, and the rows of the search blocks span many orders of magnitude
+                           across their columns: with 1 the solves of the synthetic workloads stall
+                           above 1e-8.  The FP64 form ignores it.                                       */
+    int update_hs;      /* 1: Psi_H and Psi_S are updated with W like Psi (steps 10-11 as printed);
+                           0 (default): they are recomputed from the updated Psi by the fused SpMM of
+                           steps 3/7 (the same blocks up to rounding; one SpMM costs less than two
+                           block updates on these workloads)                                           */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */

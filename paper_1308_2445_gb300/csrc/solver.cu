@@ -245,6 +245,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
     const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
     const bool tcu = o.precision == HBSD_PRECISION_MIXED && o.tc_update != 0;   // tensor-core update
+    // Psi_H, Psi_S updated with W (steps 10-11 as printed) or recomputed from the new Psi by the
+    // fused SpMM: the same blocks up to rounding, the SpMM costing less than two block updates here
+    const bool upd_hs = o.update_hs != 0;
     bool certified = false;   // Psi_H, Psi_S freshly recomputed in FP64 (mixed form)
     // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
     ti = tm.begin(StepTimer::MATVEC, st);
@@ -266,10 +269,18 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     stt.rr_fallbacks += info[0];
     ti = tm.begin(StepTimer::UPDATE, st);
     HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, true));
-    HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiH, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
-    HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiS, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
+    if (upd_hs) {
+        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiH, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
+        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiS, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, false));
+    }
     tm.end(ti, st);
-    stt.update_fma += 3.0 * n * w * w;
+    stt.update_fma += (upd_hs ? 3.0 : 1.0) * n * w * w;
+    if (!upd_hs) {   // Psi_H = Hs Psi, Psi_S = S Psi by the fused SpMM of steps 3/7
+        ti = tm.begin(StepTimer::MATVEC, st);
+        HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+        tm.end(ti, st);
+        stt.matvec_cols += w;
+    }
     HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
     HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
     std::vector<double> res(m);
@@ -297,7 +308,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             // the mixed form carries Psi_H, Psi_S through double-float updates: before accepting,
             // recompute them from Psi in FP64 and test the residual again (a failing test just
             // continues the iteration from the recomputed blocks)
-            if (dfp && !certified) {
+            if (dfp && upd_hs && !certified) {
                 certified = true;
                 ti = tm.begin(StepTimer::MATVEC, st);
                 HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
@@ -419,10 +430,18 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         // steps 10-11
         ti = tm.begin(StepTimer::UPDATE, st);
         HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st, true));
-        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiH, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st, false));
-        HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiS, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st, false));
+        if (upd_hs) {
+            HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiH, ldw, w, B.PH.p, ldp, p, n, C.W.p, w, st, false));
+            HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.PsiS, ldw, w, B.PS.p, ldp, p, n, C.W.p, w, st, false));
+        }
         tm.end(ti, st);
-        stt.update_fma += 3.0 * n * q * w;
+        stt.update_fma += (upd_hs ? 3.0 : 1.0) * n * q * w;
+        if (!upd_hs) {   // Psi_H = Hs Psi, Psi_S = S Psi by the fused SpMM of steps 3/7
+            ti = tm.begin(StepTimer::MATVEC, st);
+            HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+            tm.end(ti, st);
+            stt.matvec_cols += w;
+        }
         Eprev = E;
         HBSD_CUDA(cudaMemcpyAsync(C.E.p, C.theta.p, w * 8, cudaMemcpyDeviceToDevice, st));
         HBSD_CUDA(cudaMemcpyAsync(E.data(), C.theta.p, w * 8, cudaMemcpyDeviceToHost, st));
@@ -582,7 +601,8 @@ void hbsd_options_default(hbsd_options* opt) {
     opt->precond = HBSD_PRECOND_HYBRID;
     opt->seed = 1;
     opt->local_solver = HBSD_LOCAL_MINRES;
-    opt->tc_update = 1;
+    opt->tc_update = 0;
+    opt->update_hs = 0;
 }
 
 const char* hbsd_status_string(int status) {

@@ -77,6 +77,23 @@ def test_small_solve_hybrid(seed):
     assert st["local_cols"] > 0 and st["minres_steps"] >= 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_small_solve_with_psi_h_psi_s_updated_as_printed(precision):
+    """update_hs = 1: Psi_H and Psi_S carried through the update of steps 10-11 as the outline
+    prints it, instead of recomputed by the SpMM (the default): the same eigenpairs and, in FP64,
+    the oracle's iteration count within +-1."""
+    p = pi.small_case(2)
+    nev = pi.SMALL_NEV
+    X0 = pi.seed_normal_block(2, p.n, nev + L.default_m0(nev))
+    prec = hb().PRECISION_MIXED if precision == "mixed" else hb().PRECISION_FP64
+    s = hb().Session.from_problem(p, precision=prec, update_hs=1)
+    lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
+    ro = L.labpsd(p, nev, 1e-8, X0=X0)
+    assert rc == 0
+    compare(p, nev, lam, X, it, ro, iter_slack=1 if precision == "fp64" else 10**6)
+    assert host_res(p, lam, X, s.sigma0).max() <= 1e-8 * 1.001
+
+
 def test_small_solve_global_only():
     p = pi.small_case(1)
     nev = 16
