@@ -91,7 +91,7 @@ typedef struct {
 /* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
  * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,
  * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar), tc_update = 0,
- * update_hs = 0. */
+ * update_hs = -1, minres_f32 = 1. */
 typedef struct {
     double sigma_bar;   /* global shift eps_bar of K = (H - eps_bar S)^{-1}; must lie below the spectrum */
     double sigma0;      /* shift making H - sigma0 S positive definite (Sec. 5); NaN -> sigma_bar        */
@@ -111,9 +111,16 @@ typedef struct {
                            across their columns: with 1 the solves of the synthetic workloads stall
                            above 1e-8.  The FP64 form ignores it.                                       */
     int update_hs;      /* 1: Psi_H and Psi_S are updated with W like Psi (steps 10-11 as printed);
-                           0 (default): they are recomputed from the updated Psi by the fused SpMM of
-                           steps 3/7 (the same blocks up to rounding; one SpMM costs less than two
-                           block updates on these workloads)                                           */
+                           0: they are recomputed from the updated Psi by the fused SpMM of steps 3/7
+                           (the same blocks up to rounding; one SpMM costs less than two block updates
+                           when q is large); -1 (default): 1 in the FP64 form, which follows the
+                           printed outline step for step; in the mixed form 0 for an update of width
+                           q with q n > 3.5 nnz (the SpMM's 2 nnz FP64 FMA per column against the two
+                           double-float updates' 2 n q, at ~3.5 times the FP64 rate), else 1       */
+    int minres_f32;     /* mixed form: 1 (default) computes the operator products of the MINRES steps
+                           of 6(b) from the FP32 scaled pencil, (Hs - e S) v = D^-1 [(D Hs D) - e (D S
+                           D)] (D^-1 v) with v, the Lanczos and Givens recurrences and the solution in
+                           FP64; 0 in FP64 throughout.  The FP64 form ignores it.                      */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */

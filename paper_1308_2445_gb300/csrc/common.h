@@ -110,6 +110,7 @@ struct Sell {
     DBuf<double2> hs;           // (h - sigma0 s, s) per stored entry
     DBuf<float2> hs32;          // FP32 values of the scaled pencil (D Hs D, D S D) for the mixed path
     DBuf<double> dscale;        // D = diag(S)^{-1/2}
+    DBuf<double> dinv;          // D^-1
     std::vector<double> h_dscale;
     std::vector<int64_t> h_slice_ptr;
     std::vector<int32_t> h_slot_row, h_cols;
@@ -316,6 +317,7 @@ struct Session {
     // MINRES workspace (minres.cu)
     DBuf<double> mr_d;
     DBuf<double> mr_red;        // per-block partial sums of the fused MINRES kernel
+    DBuf<float> mr_v32;         // D^-1 v in FP32 for the FP32 operator products of MINRES
     DBuf<int> mr_any, mr_steps; // grid barrier + error flag; per-column step counts
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel

@@ -146,6 +146,12 @@ struct MrArgs {
     double* nl_part;              // [chunk slot][kp] partials of F^T U
     double* nl_zv;                // [block slot][kp] F^T v
     double* nl_zg;                // [block slot][kp] G F^T v
+    // operator products of the Lanczos steps from the FP32 scaled pencil (f32 = 1):
+    // (Hs - e S) v = D^-1 [(D Hs D) - e (D S D)] (D^-1 v), v^ = D^-1 v kept in FP32 beside V
+    int f32;
+    const float2* hs32;           // (D Hs D, D S D) per stored entry
+    const double* dinv;           // D^-1 (n)
+    float* V32;                   // v^ = D^-1 v, layout of V
 };
 
 template <class T> struct Pair;
@@ -385,6 +391,39 @@ __device__ __forceinline__ void spmm_pass(const MrArgs& a, const P* hs, const T*
     }
 }
 
+// The same product from the FP32 scaled pencil on v^ = D^-1 v (FP32 multiply-adds), scaled back by
+// D^-1 per row in FP64: f(row, j, y) receives ((Hs - e_j S) v)(row, j) to FP32 accuracy.
+template <class J, class F>
+__device__ __forceinline__ void spmm_pass_f32(const MrArgs& a, const double* E, int64_t ld, const Pass& p, J&& jcol,
+                                              F&& f) {
+    if (p.r >= p.rb) return;
+    const int j = jcol(p.c0 + p.c);
+    const float ej = (float)E[j];
+    const int64_t s1 = a.blk[blockIdx.x + 1];
+    for (int64_t slot = a.blk[blockIdx.x] + p.r; slot < s1; slot += p.rb) {
+        const int64_t sl = slot / a.C;
+        const int t = (int)(slot - sl * a.C);
+        const int64_t base = a.slice_ptr[sl] + t;
+        const int len = a.slice_len[sl];
+        float ah = 0.f, as = 0.f;
+#pragma unroll 4
+        for (int jj = 0; jj < len; ++jj) {
+            const int64_t ee = base + (int64_t)jj * a.C;
+            const int cj = __ldg(a.cols + ee);
+            const float2 hv = __ldg(a.hs32 + ee);
+            const float x = a.V32[(int64_t)cj * ld + j];
+            ah = fmaf(hv.x, x, ah);
+            as = fmaf(hv.y, x, as);
+        }
+        const int row = a.slot_row[slot];
+        if (row >= 0) {
+            double y = (double)fmaf(-ej, as, ah) * a.dinv[row];
+            if (a.nl_k) y += nl_slot(a, slot, j);
+            f((int64_t)row, j, y);
+        }
+    }
+}
+
 // Row-wise visit of one pass over this block's slot range: f(row, j).
 template <class J, class F>
 __device__ __forceinline__ void rows_pass(const MrArgs& a, const Pass& p, J&& jcol, F&& f) {
@@ -480,6 +519,7 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
         rows_pass(a, p, identity, [&](int64_t i, int j) {
             const int64_t o = i * ld + j;
             U[o] = S.g(I_ACTIVE)[j] ? (T)((double)V[o] * S.f(F_BINV)[j]) : V[o];
+            if (a.f32) a.V32[o] = (float)((double)U[o] * a.dinv[i]);
             Vp[o] = T(0);
             Wp[o] = T(0);
             Wpp[o] = T(0);
@@ -514,10 +554,12 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
         for (int c0 = 0; c0 < na; c0 += MR_PASS) {
             const Pass p = make_pass(c0, na);
             double acc = 0.0;
-            spmm_pass<T>(a, hs, E, V, ld, p, active_col, [&](int64_t row, int j, T u) {
+            auto take = [&](int64_t row, int j, T u) {
                 U[row * ld + j] = u;
                 acc += (double)V[row * ld + j] * (double)u;
-            });
+            };
+            if (a.f32) spmm_pass_f32(a, reinterpret_cast<const double*>(E), ld, p, active_col, take);
+            else spmm_pass<T>(a, hs, E, V, ld, p, active_col, take);
             block_partials(acc, p, S.red, rowA);
         }
         if (a.stamps && threadIdx.x == 0) a.stamps[8 + blockIdx.x] += gtimer() - ta;   // per-block phase A (tracing)
@@ -597,6 +639,7 @@ __global__ void __launch_bounds__(MR_THREADS, 2) k_minres(MrArgs a) {
                 if (S.g(I_CONT)[j]) {
                     Vp[o] = V[o];
                     V[o] = (T)((double)U[o] * S.f(F_BINV)[j]);
+                    if (a.f32) a.V32[o] = (float)((double)V[o] * a.dinv[i]);
                 }
             });
         }
@@ -924,6 +967,18 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         a.stamps = s->mr_stamps.p;
     }
     a.nl_k = nl ? s->nl.k : 0;
+    a.f32 = 0;
+    a.hs32 = nullptr;
+    a.dinv = nullptr;
+    a.V32 = nullptr;
+    if (sizeof(T) == 8 && solver == HBSD_LOCAL_MINRES && s->opt.precision == HBSD_PRECISION_MIXED &&
+        s->opt.minres_f32 && s->A.dinv.p) {
+        HBSD_TRY(s->mr_v32.alloc((size_t)n * ld));
+        a.f32 = 1;
+        a.hs32 = s->A.hs32.p;
+        a.dinv = s->A.dinv.p;
+        a.V32 = s->mr_v32.p;
+    }
     {
         Nonlocal& q = s->nl;
         a.nl_rptr = q.rptr.p; a.nl_rcol = q.rcol.p; a.nl_rval = q.rval.p; a.nl_frows = q.ch_rows.p;

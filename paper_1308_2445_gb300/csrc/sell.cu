@@ -93,6 +93,12 @@ int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_id
     m.h_cols = cols;
     HBSD_TRY(m.dscale.alloc(n));
     HBSD_CUDA(cudaMemcpy(m.dscale.p, m.h_dscale.data(), n * 8, cudaMemcpyHostToDevice));
+    {
+        std::vector<double> dinv(n);
+        for (int64_t i = 0; i < n; ++i) dinv[i] = 1.0 / m.h_dscale[i];
+        HBSD_TRY(m.dinv.alloc(n));
+        HBSD_CUDA(cudaMemcpy(m.dinv.p, dinv.data(), n * 8, cudaMemcpyHostToDevice));
+    }
     HBSD_TRY(m.hs32.alloc(m.stored));
     return sell_fill_fp32(m, hs.data(), cols.data(), slot_row.data());
 }

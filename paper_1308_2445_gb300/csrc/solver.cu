@@ -247,7 +247,15 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     const bool tcu = o.precision == HBSD_PRECISION_MIXED && o.tc_update != 0;   // tensor-core update
     // Psi_H, Psi_S updated with W (steps 10-11 as printed) or recomputed from the new Psi by the
     // fused SpMM: the same blocks up to rounding, the SpMM costing less than two block updates here
-    const bool upd_hs = o.update_hs != 0;
+    // per update of width q: update_hs = 1 updates, 0 recomputes; -1 (auto) updates in the FP64
+    // form and, in the mixed form, recomputes when the SpMM's FP64 work (2 nnz per column) is below
+    // that of two double-float block updates (2 n q per column at ~3.5x the FP64 rate)
+    auto upd_hs_for = [&](int qq) -> bool {
+        if (o.update_hs >= 0) return o.update_hs > 0;
+        if (o.precision == HBSD_PRECISION_FP64) return true;
+        return !((double)qq * (double)n > 3.5 * (double)S->nnz);
+    };
+    bool hs_fresh = false;   // Psi_H, Psi_S recomputed in FP64 by the last update step
     bool certified = false;   // Psi_H, Psi_S freshly recomputed in FP64 (mixed form)
     // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
     ti = tm.begin(StepTimer::MATVEC, st);
@@ -267,6 +275,8 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     HBSD_TRY(rayleigh_ritz_cluster(S, C.HR.p, C.SR.p, w, w, C.theta.p, C.W.p, info, st, drop_tol));
     tm.end(ti, st);
     stt.rr_fallbacks += info[0];
+    bool upd_hs = upd_hs_for(w);
+    hs_fresh = !upd_hs;
     ti = tm.begin(StepTimer::UPDATE, st);
     HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, true));
     if (upd_hs) {
@@ -308,8 +318,9 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             // the mixed form carries Psi_H, Psi_S through double-float updates: before accepting,
             // recompute them from Psi in FP64 and test the residual again (a failing test just
             // continues the iteration from the recomputed blocks)
-            if (dfp && upd_hs && !certified) {
+            if (dfp && !hs_fresh && !certified) {
                 certified = true;
+                hs_fresh = true;
                 ti = tm.begin(StepTimer::MATVEC, st);
                 HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
                 tm.end(ti, st);
@@ -428,6 +439,8 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             std::fprintf(stderr, "[hbsd]   RR q %d rank %d branch %d nonfinite theta %d W %d\n", q, info[1], info[0],
                          count_nonfinite(C.theta.p, w, st), count_nonfinite(C.W.p, (int64_t)q * w, st));
         // steps 10-11
+        upd_hs = upd_hs_for(q);
+        hs_fresh = !upd_hs;
         ti = tm.begin(StepTimer::UPDATE, st);
         HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st, true));
         if (upd_hs) {
@@ -602,7 +615,8 @@ void hbsd_options_default(hbsd_options* opt) {
     opt->seed = 1;
     opt->local_solver = HBSD_LOCAL_MINRES;
     opt->tc_update = 0;
-    opt->update_hs = 0;
+    opt->update_hs = -1;
+    opt->minres_f32 = 1;
 }
 
 const char* hbsd_status_string(int status) {

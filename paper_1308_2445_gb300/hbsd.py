@@ -48,7 +48,7 @@ class hbsd_options(C.Structure):
     _fields_ = [("sigma_bar", C.c_double), ("sigma0", C.c_double), ("m0", C.c_int), ("tau1", C.c_double),
                 ("tau2", C.c_double), ("eta", C.c_double), ("max_minres", C.c_int), ("max_outer", C.c_int),
                 ("precision", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64), ("local_solver", C.c_int),
-                ("tc_update", C.c_int), ("update_hs", C.c_int)]
+                ("tc_update", C.c_int), ("update_hs", C.c_int), ("minres_f32", C.c_int)]
 
 
 class hbsd_server_opts(C.Structure):

@@ -126,7 +126,6 @@ def step_only(workload, k_sweep, k_spmm):
     s = hbsd.Session.from_problem(p, precision=hbsd.PRECISION_MIXED)
     out = {"workload": workload, "n": p.n, "nnz": p.nnz}
     if k_sweep:
-        s.solve(1, 1e-2, want_vectors=False)          # makes the FP32 panels of the mixed form
         R = torch.randn(p.n, (k_sweep + 3) // 4 * 4, dtype=torch.float32, device="cuda")[:, :k_sweep]
         P = torch.zeros(p.n, (k_sweep + 3) // 4 * 4, dtype=torch.float32, device="cuda")[:, :k_sweep]
         out["sweep32_k"] = k_sweep

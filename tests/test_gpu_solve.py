@@ -77,16 +77,16 @@ def test_small_solve_hybrid(seed):
     assert st["local_cols"] > 0 and st["minres_steps"] >= 0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_small_solve_with_psi_h_psi_s_updated_as_printed(precision):
-    """update_hs = 1: Psi_H and Psi_S carried through the update of steps 10-11 as the outline
-    prints it, instead of recomputed by the SpMM (the default): the same eigenpairs and, in FP64,
-    the oracle's iteration count within +-1."""
+@pytest.mark.parametrize("precision,update_hs", [("fp64", 0), ("mixed", 1)])
+def test_small_solve_with_the_other_psi_h_psi_s_form(precision, update_hs):
+    """The form of Psi_H, Psi_S each precision does not use by default: recomputed by the SpMM in
+    the FP64 form (update_hs = 0), updated with W as the outline prints it in the mixed form
+    (update_hs = 1): the same eigenpairs and, in FP64, the oracle's iteration count within +-1."""
     p = pi.small_case(2)
     nev = pi.SMALL_NEV
     X0 = pi.seed_normal_block(2, p.n, nev + L.default_m0(nev))
     prec = hb().PRECISION_MIXED if precision == "mixed" else hb().PRECISION_FP64
-    s = hb().Session.from_problem(p, precision=prec, update_hs=1)
+    s = hb().Session.from_problem(p, precision=prec, update_hs=update_hs)
     lam, X, it, rc, st = s.solve(nev, 1e-8, X0=X0)
     ro = L.labpsd(p, nev, 1e-8, X0=X0)
     assert rc == 0
