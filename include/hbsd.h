@@ -91,7 +91,7 @@ typedef struct {
 /* Solver options.  hbsd_options_default() fills the paper's defaults (Sec. 5):
  * tau1 = tau2 = 0.1 (remark 4), eta = 0.25, max_minres = 20, max_outer = 1000,
  * m0 = -1 (= max(3, ceil(nev/10)), remark 1), sigma0 = NaN (= sigma_bar), tc_update = 0,
- * update_hs = -1, minres_f32 = 1. */
+ * update_hs = -1, minres_f32 = 1, spmm_df64 = 1. */
 typedef struct {
     double sigma_bar;   /* global shift eps_bar of K = (H - eps_bar S)^{-1}; must lie below the spectrum */
     double sigma0;      /* shift making H - sigma0 S positive definite (Sec. 5); NaN -> sigma_bar        */
@@ -115,12 +115,16 @@ typedef struct {
                            (the same blocks up to rounding; one SpMM costs less than two block updates
                            when q is large); -1 (default): 1 in the FP64 form, which follows the
                            printed outline step for step; in the mixed form 0 for an update of width
-                           q with q n > 3.5 nnz (the SpMM's 2 nnz FP64 FMA per column against the two
-                           double-float updates' 2 n q, at ~3.5 times the FP64 rate), else 1       */
+                           q with q n > 1.5 nnz when the products are double-float (spmm_df64: 2 nnz
+                           double-float multiply-adds per column against the two block updates' 2 n q),
+                           q n > 3.5 nnz when they are FP64, else 1                                    */
     int minres_f32;     /* mixed form: 1 (default) computes the operator products of the MINRES steps
                            of 6(b) from the FP32 scaled pencil, (Hs - e S) v = D^-1 [(D Hs D) - e (D S
                            D)] (D^-1 v) with v, the Lanczos and Givens recurrences and the solution in
                            FP64; 0 in FP64 throughout.  The FP64 form ignores it.                      */
+    int spmm_df64;      /* mixed form: 1 (default) computes the products of steps 3 and 7 and the
+                           recomputation of Psi_H, Psi_S as hbsd_spmm_pair_df64 does, and checks
+                           convergence on FP64 products; 0 in FP64.  The FP64 form ignores it.        */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */
@@ -259,6 +263,15 @@ int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k,
  * shifts relative to sigma0. */
 int hbsd_spmm_shifted(hbsd_handle* h, const double* X, int64_t ldx, int k, const double* e,
                       double* Y, int64_t ldy);
+
+/* Steps 3 and 7 in double-float arithmetic (the mixed form's products): HX = Hs X and SX = S X
+ * computed as D^-1 [(D Hs D)(D^-1 X)] and D^-1 [(D S D)(D^-1 X)], D = diag(S)^{-1/2}, with the
+ * scaled values and D^-1 X split into float pairs and every product and sum in double-float
+ * (about 2^-44 relative to |Hs||X| per entry; on the scaled pencil, whose entries are O(1), no
+ * value falls below the float range).  FP64 device blocks as in hbsd_spmm_pair; the nonlocal term
+ * is added in FP64. */
+int hbsd_spmm_pair_df64(hbsd_handle* h, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx,
+                        double* SX, int64_t ldsx);
 
 /* FP32 forms on the scaled pencil (hbsd_precond_apply_f32 is step 6(a) of HBSD_PRECISION_MIXED;
  * hbsd_spmm_pair_f32 is a step-level product on the FP32 copy of the matrix).  They act on the

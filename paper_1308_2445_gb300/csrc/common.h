@@ -109,6 +109,7 @@ struct Sell {
     DBuf<int32_t> cols;         // stored column indices, slice-major, then entry-major, then row
     DBuf<double2> hs;           // (h - sigma0 s, s) per stored entry
     DBuf<float2> hs32;          // FP32 values of the scaled pencil (D Hs D, D S D) for the mixed path
+    DBuf<float4> hsdf;          // the scaled pencil in double-float: (hi, lo) of D Hs D, then of D S D
     DBuf<double> dscale;        // D = diag(S)^{-1/2}
     DBuf<double> dinv;          // D^-1
     std::vector<double> h_dscale;
@@ -127,6 +128,10 @@ int sell_fill_fp32(Sell& m, const double2* hs, const int32_t* cols, const int32_
 template <class T>
 int spmm_pair(Session* s, const Sell& m, const T* X, int64_t ldx, int k, T* HX, int64_t ldhx,
               T* SX, int64_t ldsx, cudaStream_t st);
+// Y_h = Hs X, Y_s = S X in double-float arithmetic on the scaled pencil (mixed form): about 48 bits
+// per product, the FP64 inputs and outputs scaled by D^-1 on the way in and out
+int spmm_pair_df64(Session* s, const Sell& m, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx,
+                   double* SX, int64_t ldsx, cudaStream_t st);
 // Y(:, j) = (Hs - e_j S) X(:, j)
 template <class T>
 int spmm_shifted(Session* s, const Sell& m, const T* X, int64_t ldx, int k, const T* e, T* Y,
@@ -318,6 +323,7 @@ struct Session {
     DBuf<double> mr_d;
     DBuf<double> mr_red;        // per-block partial sums of the fused MINRES kernel
     DBuf<float> mr_v32;         // D^-1 v in FP32 for the FP32 operator products of MINRES
+    DBuf<float2> x2;            // D^-1 X in double-float for spmm_pair_df64
     DBuf<int> mr_any, mr_steps; // grid barrier + error flag; per-column step counts
     DBuf<unsigned long long> mr_stamps;   // MINRES phase times when tracing
     DBuf<int64_t> mr_blk;       // per-block SELL slot ranges of the fused MINRES kernel

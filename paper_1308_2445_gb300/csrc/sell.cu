@@ -16,6 +16,7 @@
 #include <numeric>
 
 #include "common.h"
+#include "df64.h"
 
 namespace hbsd {
 
@@ -108,6 +109,12 @@ int sell_build(Sell& m, int64_t n, const int64_t* row_ptr, const int32_t* col_id
 // of magnitude.
 int sell_fill_fp32(Sell& m, const double2* hs, const int32_t* cols, const int32_t* slot_row) {
     std::vector<float2> hs32(m.stored, make_float2(0.f, 0.f));
+    std::vector<float4> hsdf(m.stored, make_float4(0.f, 0.f, 0.f, 0.f));
+    // double-float pair of a double: the nearest float, then the nearest float to the remainder
+    auto pair = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
     for (int64_t sl = 0; sl < m.n_slices; ++sl) {
         const int64_t len = (m.h_slice_ptr[sl + 1] - m.h_slice_ptr[sl]) / m.C;
         for (int t = 0; t < m.C; ++t) {
@@ -117,10 +124,16 @@ int sell_fill_fp32(Sell& m, const double2* hs, const int32_t* cols, const int32_
                 const int64_t pos = m.h_slice_ptr[sl] + j * m.C + t;
                 const double f = m.h_dscale[r] * m.h_dscale[cols[pos]];
                 hs32[pos] = make_float2((float)(f * hs[pos].x), (float)(f * hs[pos].y));
+                float a, b, c, d;
+                pair(f * hs[pos].x, a, b);
+                pair(f * hs[pos].y, c, d);
+                hsdf[pos] = make_float4(a, b, c, d);
             }
         }
     }
     HBSD_CUDA(cudaMemcpy(m.hs32.p, hs32.data(), hs32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    HBSD_TRY(m.hsdf.alloc(m.stored));
+    HBSD_CUDA(cudaMemcpy(m.hsdf.p, hsdf.data(), hsdf.size() * sizeof(float4), cudaMemcpyHostToDevice));
     return 0;
 }
 
@@ -288,6 +301,121 @@ static int spmm_launch(Session* s, const Sell& m, const T* X, int64_t ldx, int k
         HBSD_LAUNCHED(s);
     }
     return 0;
+}
+
+// ---- double-float SpMM on the scaled pencil (mixed form) ------------------------------------------
+// X2 = D^-1 X as double-float pairs (the FP64 scaling, then split_d's exact bit split)
+__global__ void k_split_scaled(const double* __restrict__ X, int64_t ldx, int k, int64_t n,
+                               const double* __restrict__ dinv, float2* __restrict__ X2, int64_t ld2) {
+    const int64_t total = n * k;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / k;
+        const int j = (int)(t - i * k);
+        X2[i * ld2 + j] = df::split_d(X[i * ldx + j] * dinv[i]);
+    }
+}
+
+// Pair mode of k_spmm in double-float: per stored entry the (hi, lo) of D Hs D and of D S D, per
+// column pair one float4 of X2; sums by df::dfma, renormalised every 8 entries; the row result is
+// scaled back by D^-1 in FP64.
+template <int CH>
+__global__ void __launch_bounds__(256) k_spmm_df64(
+    const int64_t* __restrict__ slice_ptr, const int32_t* __restrict__ slice_len, const int32_t* __restrict__ cols,
+    const float4* __restrict__ hsdf, const int32_t* __restrict__ slot_row, int64_t n_slots, int C,
+    const float2* __restrict__ X2, int64_t ld2, int k, int lpr_log2, const double* __restrict__ dinv,
+    double* __restrict__ Y0, int64_t ld0, double* __restrict__ Y1, int64_t ld1) {
+    const int lpr = 1 << lpr_log2;
+    const int lane = threadIdx.x & (lpr - 1);
+    const int64_t slot = (int64_t)blockIdx.x * (blockDim.x >> lpr_log2) + (threadIdx.x >> lpr_log2);
+    if (slot >= n_slots) return;
+    const int64_t sl = slot / C;
+    const int t = (int)(slot - sl * C);
+    const int64_t base = slice_ptr[sl] + t;
+    const int len = slice_len[sl];
+    float ah[CH][2][2], as[CH][2][2];   // [chunk][column of the pair][hi, lo]
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+#pragma unroll
+        for (int v = 0; v < 2; ++v) { ah[c][v][0] = ah[c][v][1] = as[c][v][0] = as[c][v][1] = 0.f; }
+    int col0[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) col0[c] = 2 * (lane + c * lpr);
+    for (int j = 0; j < len; ++j) {
+        const int64_t e = base + (int64_t)j * C;
+        const int cj = __ldg(cols + e);
+        const float4 hv = __ldg(hsdf + e);
+        const float2 h2 = make_float2(hv.x, hv.y), s2 = make_float2(hv.z, hv.w);
+        const float2* xr = X2 + (int64_t)cj * ld2;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            if (col0[c] < k) {
+                const float4 x = __ldg(reinterpret_cast<const float4*>(xr + col0[c]));
+                const float2 x0 = make_float2(x.x, x.y), x1 = make_float2(x.z, x.w);
+                df::dfma(h2, x0, ah[c][0][0], ah[c][0][1]);
+                df::dfma(s2, x0, as[c][0][0], as[c][0][1]);
+                df::dfma(h2, x1, ah[c][1][0], ah[c][1][1]);
+                df::dfma(s2, x1, as[c][1][0], as[c][1][1]);
+            }
+        }
+        if ((j & 7) == 7) {
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    df::renorm(ah[c][v][0], ah[c][v][1]);
+                    df::renorm(as[c][v][0], as[c][v][1]);
+                }
+        }
+    }
+    const int row = slot_row[slot];
+    if (row < 0) return;
+    const double di = dinv[row];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const int cc = col0[c];
+        if (cc >= k) continue;
+#pragma unroll
+        for (int v = 0; v < 2; ++v) {
+            if (cc + v >= k) break;
+            Y0[(int64_t)row * ld0 + cc + v] = df::to_d(ah[c][v][0], ah[c][v][1]) * di;
+            Y1[(int64_t)row * ld1 + cc + v] = df::to_d(as[c][v][0], as[c][v][1]) * di;
+        }
+    }
+}
+
+int spmm_pair_df64(Session* s, const Sell& m, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx,
+                   double* SX, int64_t ldsx, cudaStream_t st) {
+    if (k <= 0) return 0;
+    const int64_t ld2 = round_up(k, 2);
+    HBSD_TRY(s->x2.alloc((size_t)m.n * ld2));
+    {
+        const int64_t total = m.n * k;
+        const int g = (int)std::min<int64_t>(std::max<int64_t>(1, (total + 255) / 256), 8192);
+        k_split_scaled<<<g, 256, 0, st>>>(X, ldx, k, m.n, m.dinv.p, s->x2.p, ld2);
+        HBSD_LAUNCHED(s);
+    }
+    const int pass_cols = 32 * 2 * 4;
+    for (int c0 = 0; c0 < k; c0 += pass_cols) {
+        const int kk = std::min(pass_cols, k - c0);
+        const int vecs = ceil_div(kk, 2);
+        int lpr = 1, lg = 0;
+        while (lpr < vecs && lpr < 32) { lpr <<= 1; ++lg; }
+        const int ch = ceil_div(vecs, lpr);
+        const int rows_per_cta = 256 / lpr;
+        const int grid = ceil_div(m.n_slots, rows_per_cta);
+#define HBSD_SPMM_DF_CASE(CHV)                                                                                 case CHV:                                                                                                      k_spmm_df64<CHV><<<grid, 256, 0, st>>>(m.slice_ptr.p, m.slice_len.p, m.cols.p, m.hsdf.p, m.slot_row.p,                                                  m.n_slots, m.C, s->x2.p + c0, ld2, kk, lg, m.dinv.p, HX + c0, ldhx,                                                SX + c0, ldsx);                                                     break;
+        switch (ch) {
+            HBSD_SPMM_DF_CASE(1)
+            HBSD_SPMM_DF_CASE(2)
+            HBSD_SPMM_DF_CASE(3)
+            HBSD_SPMM_DF_CASE(4)
+            default:
+                return fail(HBSD_ERR_ARG, "spmm_df64: internal chunking error");
+        }
+#undef HBSD_SPMM_DF_CASE
+        HBSD_LAUNCHED(s);
+    }
+    return nl_apply_add<double>(s, X, ldx, k, HX, ldhx, st);
 }
 
 // Both add the nonlocal term F G F^T X of the session (Eq. fgf) to the H product.

@@ -245,6 +245,15 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
     const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
     const bool tcu = o.precision == HBSD_PRECISION_MIXED && o.tc_update != 0;   // tensor-core update
+    // products of steps 3/7 and the Psi_H, Psi_S recomputation: double-float on the scaled pencil
+    // in the mixed form (spmm_df64), FP64 otherwise
+    const bool dfs = std::is_same<T, double>::value && o.precision == HBSD_PRECISION_MIXED && o.spmm_df64 != 0;
+    auto products = [&](const T* Xp, int64_t ldx, int k, T* HXp, int64_t ldh, T* SXp, int64_t lds) -> int {
+        if constexpr (std::is_same<T, double>::value) {
+            if (dfs) return spmm_pair_df64(S, S->A, Xp, ldx, k, HXp, ldh, SXp, lds, st);
+        }
+        return spmm_pair<T>(S, S->A, Xp, ldx, k, HXp, ldh, SXp, lds, st);
+    };
     // Psi_H, Psi_S updated with W (steps 10-11 as printed) or recomputed from the new Psi by the
     // fused SpMM: the same blocks up to rounding, the SpMM costing less than two block updates here
     // per update of width q: update_hs = 1 updates, 0 recomputes; -1 (auto) updates in the FP64
@@ -253,13 +262,13 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     auto upd_hs_for = [&](int qq) -> bool {
         if (o.update_hs >= 0) return o.update_hs > 0;
         if (o.precision == HBSD_PRECISION_FP64) return true;
-        return !((double)qq * (double)n > 3.5 * (double)S->nnz);
+        return !((double)qq * (double)n > (dfs ? 1.5 : 3.5) * (double)S->nnz);
     };
     bool hs_fresh = false;   // Psi_H, Psi_S recomputed in FP64 by the last update step
     bool certified = false;   // Psi_H, Psi_S freshly recomputed in FP64 (mixed form)
     // steps 1-3: Psi_H, Psi_S, Rayleigh-Ritz on span(Psi)
     ti = tm.begin(StepTimer::MATVEC, st);
-    HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+    HBSD_TRY(products(B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw));
     tm.end(ti, st);
     stt.matvec_cols += w;
     ti = tm.begin(StepTimer::GRAM, st);
@@ -276,7 +285,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     tm.end(ti, st);
     stt.rr_fallbacks += info[0];
     bool upd_hs = upd_hs_for(w);
-    hs_fresh = !upd_hs;
+    hs_fresh = !upd_hs && !dfs;
     ti = tm.begin(StepTimer::UPDATE, st);
     HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, (const T*)nullptr, 0, 0, n, C.W.p, w, st, true));
     if (upd_hs) {
@@ -287,7 +296,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     stt.update_fma += (upd_hs ? 3.0 : 1.0) * n * w * w;
     if (!upd_hs) {   // Psi_H = Hs Psi, Psi_S = S Psi by the fused SpMM of steps 3/7
         ti = tm.begin(StepTimer::MATVEC, st);
-        HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+        HBSD_TRY(products(B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw));
         tm.end(ti, st);
         stt.matvec_cols += w;
     }
@@ -318,7 +327,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             // the mixed form carries Psi_H, Psi_S through double-float updates: before accepting,
             // recompute them from Psi in FP64 and test the residual again (a failing test just
             // continues the iteration from the recomputed blocks)
-            if (dfp && !hs_fresh && !certified) {
+            if ((dfp || dfs) && !hs_fresh && !certified) {
                 certified = true;
                 hs_fresh = true;
                 ti = tm.begin(StepTimer::MATVEC, st);
@@ -414,7 +423,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         }
         // step 7
         ti = tm.begin(StepTimer::MATVEC, st);
-        HBSD_TRY(spmm_pair<T>(S, S->A, B.P.p, ldp, p, B.PH.p, ldp, B.PS.p, ldp, st));
+        HBSD_TRY(products(B.P.p, ldp, p, B.PH.p, ldp, B.PS.p, ldp));
         tm.end(ti, st);
         stt.matvec_cols += p;
         // step 8
@@ -440,7 +449,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
                          count_nonfinite(C.theta.p, w, st), count_nonfinite(C.W.p, (int64_t)q * w, st));
         // steps 10-11
         upd_hs = upd_hs_for(q);
-        hs_fresh = !upd_hs;
+        hs_fresh = !upd_hs && !dfs;
         ti = tm.begin(StepTimer::UPDATE, st);
         HBSD_TRY(update_block<T>(S, dfp, tcu, B, B.Psi, ldw, w, B.P.p, ldp, p, n, C.W.p, w, st, true));
         if (upd_hs) {
@@ -451,7 +460,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         stt.update_fma += (upd_hs ? 3.0 : 1.0) * n * q * w;
         if (!upd_hs) {   // Psi_H = Hs Psi, Psi_S = S Psi by the fused SpMM of steps 3/7
             ti = tm.begin(StepTimer::MATVEC, st);
-            HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+            HBSD_TRY(products(B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw));
             tm.end(ti, st);
             stt.matvec_cols += w;
         }
@@ -617,6 +626,7 @@ void hbsd_options_default(hbsd_options* opt) {
     opt->tc_update = 0;
     opt->update_hs = -1;
     opt->minres_f32 = 1;
+    opt->spmm_df64 = 1;
 }
 
 const char* hbsd_status_string(int status) {
@@ -950,6 +960,15 @@ int hbsd_spmm_pair(hbsd_handle* h, const double* X, int64_t ldx, int k, double* 
         if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
         if (!ld_ok(ldx, k) || !ld_ok(ldhx, k) || !ld_ok(ldsx, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
         return spmm_pair<double>(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
+    });
+}
+
+int hbsd_spmm_pair_df64(hbsd_handle* h, const double* X, int64_t ldx, int k, double* HX, int64_t ldhx, double* SX,
+                        int64_t ldsx) {
+    return guarded([&]() -> int {
+        if (!h || !X || !HX || !SX || k < 0) return fail(HBSD_ERR_ARG, "bad arguments");
+        if (!ld_ok(ldx, k) || !ld_ok(ldhx, k) || !ld_ok(ldsx, k)) return fail(HBSD_ERR_ARG, "leading dimension below the block width");
+        return spmm_pair_df64(&h->s, h->s.A, X, ldx, k, HX, ldhx, SX, ldsx, h->s.stream);
     });
 }
 

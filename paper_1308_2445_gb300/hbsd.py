@@ -48,7 +48,8 @@ class hbsd_options(C.Structure):
     _fields_ = [("sigma_bar", C.c_double), ("sigma0", C.c_double), ("m0", C.c_int), ("tau1", C.c_double),
                 ("tau2", C.c_double), ("eta", C.c_double), ("max_minres", C.c_int), ("max_outer", C.c_int),
                 ("precision", C.c_int), ("precond", C.c_int), ("seed", C.c_uint64), ("local_solver", C.c_int),
-                ("tc_update", C.c_int), ("update_hs", C.c_int), ("minres_f32", C.c_int)]
+                ("tc_update", C.c_int), ("update_hs", C.c_int), ("minres_f32", C.c_int),
+                ("spmm_df64", C.c_int)]
 
 
 class hbsd_server_opts(C.Structure):
@@ -112,6 +113,7 @@ _SIGS = {
     "hbsd_spmm_pair": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
     "hbsd_spmm_shifted": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, _P, C.c_int64]),
     "hbsd_spmm_pair_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
+    "hbsd_spmm_pair_df64": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64, _P, C.c_int64]),
     "hbsd_precond_apply_f32": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P, C.c_int64]),
     "hbsd_dscale": (C.c_int, [_P, _D]),
     "hbsd_residual": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64, _P, C.c_int, _P, C.c_int64, _P]),
@@ -317,6 +319,10 @@ class Session:
     def residual(self, PsiH, PsiS, E, m, R, res):
         check(lib().hbsd_residual(self.h, ptr(PsiH), ld(PsiH), ptr(PsiS), ld(PsiS), ptr(E), m, ptr(R),
                                   ld(R) if R is not None else 0, ptr(res)), "hbsd_residual")
+
+    def spmm_pair_df64(self, X, HX, SX):
+        check(lib().hbsd_spmm_pair_df64(self.h, ptr(X), ld(X), X.shape[1], ptr(HX), ld(HX), ptr(SX), ld(SX)),
+              "hbsd_spmm_pair_df64")
 
     def spmm_pair_f32(self, X, HX, SX):
         check(lib().hbsd_spmm_pair_f32(self.h, ptr(X), ld(X), X.shape[1], ptr(HX), ld(HX), ptr(SX), ld(SX)),

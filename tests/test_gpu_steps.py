@@ -414,3 +414,21 @@ def test_precond_f32_columns_independent_of_the_block_width(mid):
         Pk = fbuf(p.n, len(cols))
         s.precond_apply_f32(fdev(R[:, cols]), Pk)
         assert np.array_equal(host(Pk), full[:, cols]), cols[:3]
+
+
+@pytest.mark.parametrize("k", [1, 7, 64, 130, 300])
+def test_spmm_pair_df64_against_fp64(mid, k):
+    """Steps 3/7 of the mixed form in double-float on the scaled pencil: within 2^-42 of |Hs||X|
+    (resp. |S||X|) of the FP64 product, entry by entry, including the columns of a second pass
+    (k = 300 > 256) and a ragged last column pair."""
+    p, s = mid
+    Hs, S, _ = L.make_shifted(p)
+    X = pi.seed_normal_block(60 + k, p.n, k) * np.logspace(-3, 3, k)
+    Xd = dev(X)
+    HX, SX, HX2, SX2 = [dbuf(p.n, k) for _ in range(4)]
+    s.spmm_pair(Xd, HX, SX)
+    s.spmm_pair_df64(Xd, HX2, SX2)
+    bH = np.abs(Hs.loc) @ np.abs(X)
+    bS = np.abs(S) @ np.abs(X)
+    assert np.all(np.abs(host(HX2) - host(HX)) <= 2.0 ** -42 * bH + 1e-300)
+    assert np.all(np.abs(host(SX2) - host(SX)) <= 2.0 ** -42 * bS + 1e-300)
