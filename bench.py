@@ -250,6 +250,8 @@ def roofline_object(st, nnz, nl_nnz, peak64, precision, workload, peak32=None):
     mixed form by the FP32 pipes: DF_FP32_OPS FP32 instructions per double-float multiply-add
     against the measured FP32 FMA instruction rate (peak32 / 2)."""
     mixed = precision == "mixed"
+    # in the mixed form the products of steps 3/7 run in double-float and MINRES's operator products
+    # in FP32 (the library's defaults spmm_df64 = 1, minres_f32 = 1)
     classes = {
         "precond": (st["t_precond_ms"], 4.0 * st["nnz_L"] * st["precond_cols"],
                     "supernodal triangular solves of step 6(a): 2 FMA per factor entry per column"),
@@ -276,6 +278,24 @@ def roofline_object(st, nnz, nl_nnz, peak64, precision, workload, peak32=None):
                 "traffic": None, "kernel": dom,
                 "what": "FP32 supernodal sweeps of step 6(a): the FP32 panels read once per sweep, 8 nnz(L) bytes per call",
                 "peak_source": source, "step_ms": step_ms}
+    if dom == "matvec" and mixed and peak32:
+        # 2 double-float multiply-adds per stored nonzero per column, DF_FP32_OPS FP32 instructions each
+        dfma = (2.0 * nnz) * st["matvec_cols"]
+        achieved = DF_FP32_OPS * dfma / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+        peak = peak32 / 2.0 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 instr/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom,
+                "what": "steps 3/7 and the Psi_H, Psi_S recomputation: fused SpMM in double-float on the scaled pencil, "
+                        f"2 double-float multiply-adds (h and s) per stored nonzero per column, {DF_FP32_OPS} FP32 "
+                        "instructions each (the FP64 products of the convergence check counted alike)",
+                "peak_source": "FP32 FMA probe (hbsd_probe_peak) measured in this run, one instruction per FMA",
+                "step_ms": step_ms}
+    if dom == "minres" and mixed and peak32:
+        achieved = flops / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0
+        return {"bound": "alu", "achieved": achieved, "peak": peak32 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (peak32 / 1e12), "traffic": None, "kernel": dom,
+                "what": what + " (FP32 products on the scaled pencil, FP64 recurrences)",
+                "peak_source": "FP32 FMA probe (hbsd_probe_peak) measured in this run", "step_ms": step_ms}
     if dom in ("update", "gram") and mixed and peak32:
         # FP32 instructions per second of the double-float products against the FP32 FMA issue rate
         achieved = DF_FP32_OPS * (flops / 2.0) / (t_ms * 1e-3) / 1e12 if t_ms > 0 else 0.0

@@ -19,8 +19,9 @@ CUDA-event time of each launch (the 64^3 workload reaches Q = 538, K = 282, N = 
 columns (the Psi and P blocks of the solve).
 
 --sweep32 K runs step 6(a) of the mixed form (hbsd_precond_apply_f32, the FP32 supernodal sweeps)
-three times on a seeded K-column block of the workload's scaled pencil; --spmm K runs the fused FP64
-SpMM of steps 3/7 (hbsd_spmm_pair) three times on K columns.  Both print the CUDA-event times.
+three times on a seeded K-column block of the workload's scaled pencil; --spmm K runs the fused SpMM
+of steps 3/7 three times in FP64 (hbsd_spmm_pair), then three times in double-float on the scaled
+pencil (hbsd_spmm_pair_df64), on K columns.  Both print the CUDA-event times.
 """
 import argparse
 import json
@@ -137,6 +138,7 @@ def step_only(workload, k_sweep, k_spmm):
                   for _ in range(2)]
         out["spmm_k"] = k_spmm
         out["spmm_ms"] = timed(lambda: s.spmm_pair(X, HX, SX))
+        out["spmm_df64_ms"] = timed(lambda: s.spmm_pair_df64(X, HX, SX))
     print(json.dumps(out))
 
 

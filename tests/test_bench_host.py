@@ -22,7 +22,7 @@ def stats(**kw):
 
 def test_minres_dominant_is_an_fp64_alu_roofline():
     st = stats()
-    r = bench.roofline_object(st, 2_951_752, 0, 1.25e12, "mixed", "medium")
+    r = bench.roofline_object(st, 2_951_752, 0, 1.25e12, "fp64", "medium")
     assert r["kernel"] == "minres" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     flops = 4.0 * 2_951_752 * st["minres_spmm_cols"]
     assert r["achieved"] == pytest.approx(flops / 0.240 / 1e12)
@@ -84,3 +84,13 @@ def test_angles_at_gaps_sees_a_small_rotation():
     lam = np.array([1.0, 2.0, 3.0, 3.0000001, 5.0, 6.0])
     got = bench.angles_at_gaps(Xa.T @ Xa, Xb.T @ Xb, Xa.T @ Xb, lam, 6)
     assert abs(got - 1e-7) <= 2e-8
+
+
+def test_mixed_form_products_are_fp32_pipe_rooflines():
+    # double-float SpMM of steps 3/7 and FP32 MINRES products in the mixed form
+    st = stats(t_matvec_ms=900.0)
+    r = bench.roofline_object(st, 2_951_752, 0, 1.25e12, "mixed", "medium", peak32=80e12)
+    assert r["kernel"] == "matvec" and r["unit"] == "T FP32 instr/s"
+    assert r["achieved"] == pytest.approx(bench.DF_FP32_OPS * 2.0 * 2_951_752 * st["matvec_cols"] / 0.9 / 1e12)
+    r = bench.roofline_object(stats(), 2_951_752, 0, 1.25e12, "mixed", "medium", peak32=80e12)
+    assert r["kernel"] == "minres" and r["unit"] == "TFLOP/s" and r["peak"] == pytest.approx(80.0)
