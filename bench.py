@@ -48,6 +48,9 @@ WORKLOADS = {
               "tol=1e-8",
 }
 WORKLOADS["medium-nonlocal"] = WORKLOADS["medium"] + ", nonlocal F G F^T with s+p projectors per atom (k=32, r_p=0.2)"
+WORKLOADS["batched"] = ("independent instances solved by hbsd_solve_batch: mesh from {16^3, 24^3, 32^3, 40^3}, 4-16 "
+                        "atoms Z=4, 2-4 enrichment dofs/node within r_c=0.15, nev from {32, 64, 128} (seeded draws), "
+                        "mixed form, tol=1e-8")
 
 
 def parse(argv=None):
@@ -69,6 +72,8 @@ def parse(argv=None):
     ap.add_argument("--workload", default="large", choices=sorted(WORKLOADS),
                     help="large: 64^3, nev 256 (default); medium: 32^3, nev 64; medium-nonlocal: with the "
                          "nonlocal term H_nl = F G F^T (Sec. 4)")
+    ap.add_argument("--batch-count", type=int, default=64, help="batched workload: instances per batch")
+    ap.add_argument("--batch-concurrent", type=int, default=8, help="batched workload: sessions solved at once")
     ap.add_argument("--m0", type=int, default=-1,
                     help="guard columns (remark 1; default max(3, ceil(nev/10))); the medium workloads "
                          "have stored oracle runs for m0 = 21")
@@ -341,6 +346,10 @@ def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
         return
+    if args.workload == "batched":
+        print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no reference arm of its own; "
+                          "the gb300 line's cpu_baseline times the oracle on its smallest instance"}), flush=True)
+        return
     nev = problem_nev(args.workload)
     swl, snev, scale, target_iters, how = oracle_sample_plan(args.workload, args.m0)
     t_factor, d = oracle_iteration_times(swl, snev, args.m0 if swl == args.workload else -1,
@@ -392,10 +401,84 @@ def timed_solves(sess, nev, X0, lam, X, warmup, steps, stream, ws, clocks=None):
     return e0.elapsed_time(e1), converged, stats, ck
 
 
+def batched_cpu_baseline(inst, iters_gpu, iters=2):
+    """The oracle, as it stands, on the batch's smallest instance: its library factorisation
+    (excluded, as the sessions' are), the initial Rayleigh-Ritz and `iters` BPSD iterations;
+    eigenpairs/s = nev / (per-iteration time x the GPU's iteration count for that instance)."""
+    from oracle import labpsd as L
+    from paper_1308_2445_gb300 import pufe_inputs as pi
+    i = min(range(len(inst)), key=lambda j: inst[j][0].n * inst[j][1])
+    p, nev, _ = inst[i]
+    m0 = m0_of(nev, -1)
+    X0 = pi.seed_normal_block(1, p.n, nev + m0)
+    t0 = time.perf_counter()
+    Hs, S, s0 = L.make_shifted(p)
+    K = L.GlobalPreconditioner(Hs, p.dof_node, p.grid)
+    t_factor = time.perf_counter() - t0
+    marks = [time.perf_counter()]
+    L.labpsd(p, nev, TOL, X0=X0, precond=K, opts=L.Options(max_outer=iters, m0=m0),
+             on_iteration=lambda it, res: marks.append(time.perf_counter()))
+    d = [marks[k + 1] - marks[k] for k in range(len(marks) - 1)]
+    per_iter = sum(d[1:]) / len(d[1:]) if len(d) > 1 else d[0]
+    its = max(1, iters_gpu[i])
+    return {"value": nev / (per_iter * its), "unit": "eigenpairs/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"instance {i} of the batch (n = {p.n}, nev = {nev}, the smallest): library factorisation "
+                       f"({t_factor:.1f} s, excluded) + initial Rayleigh-Ritz + {iters} BPSD iterations "
+                       f"({per_iter:.2f} s each after the first); solve time = per-iteration time x the GPU's "
+                       f"{its} iterations on that instance"),
+            "t_factor_s": t_factor, "t_iter_s": per_iter}
+
+
+def run_batched(args):
+    """The batched workload: hbsd_solve_batch over seeded uneven instances (one GPU, replicas
+    only under torchrun: each rank its own batch)."""
+    import torch
+    from paper_1308_2445_gb300 import batch_bench
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    a = argparse.Namespace(count=args.batch_count, seed=1 + rank, concurrent=args.batch_concurrent,
+                           arms="batched,one_at_a_time,fp64" if args.fp64_steps > 0 else "batched,one_at_a_time",
+                           meshes="16,24,32,40", tol=TOL)
+    inst_holder = {}
+    res = batch_bench.run(a, args.steps, args.warmup, clocks=Clocks(local), keep=inst_holder)
+    b = res["batched"]
+    wall_ms, conv = aggregate_replicas(b["wall_s"] * 1e3, b["converged_eigenpairs"], "cuda")
+    line = {"metric": METRIC + ", batched form", "value": conv / (wall_ms * 1e-3), "unit": "eigenpairs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["batched"], "instances": res["count"], "concurrent": res["concurrent"],
+                       "total_nev": res["total_nev"], "n": res["instances"]["n"], "nev": res["instances"]["nev"],
+                       "mesh": res["instances"]["mesh"], "iters": b["iters"], "run_ms": b["run_ms"],
+                       "tune": res.get("tune"), "t_create_s": res.get("t_create_mixed_s"),
+                       "t_autotune_s": res.get("t_autotune_s"),
+                       "timing": "host wall clock between device synchronisations around each batch call (the "
+                                 "solves run on one stream per session); median of the timed calls",
+                       "l2": "working set > L2 (all sessions' factors and blocks resident)",
+                       "one_at_a_time": res.get("one_at_a_time"), "fp64": res.get("fp64"),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "roofline": None,
+            "roofline_note": "a batch mixes every kernel of many problem sizes; the per-kernel roofs are those of "
+                             "the 64^3 and 32^3 lines",
+            "e2e": res.get("e2e"), "gpu_launches": int(b["gpu_launches_per_call"] * args.steps),
+            "clocks": res.get("clocks")}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = batched_cpu_baseline(inst_holder["inst"], b["iters"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     import numpy as np
     import torch
     ws, rank, local = dist()

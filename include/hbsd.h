@@ -73,8 +73,10 @@ typedef struct {
 } hbsd_local_blocks;
 
 #define HBSD_PRECISION_FP64   0   /* every step in FP64                                  */
-#define HBSD_PRECISION_MIXED  1   /* step 6(a) in FP32 on the scaled pencil, steps 8 and 10-11
-                                     in double-float, every other step in FP64             */
+#define HBSD_PRECISION_MIXED  1   /* step 6(a) and MINRES's operator products in FP32 on the
+                                     scaled pencil; steps 3/7, 8 and 10-11 in double-float
+                                     (options minres_f32, spmm_df64); residual norms,
+                                     Rayleigh-Ritz and the convergence test in FP64         */
 
 #define HBSD_PRECOND_HYBRID   0   /* steps 6(a) + 6(b) (Sec. 3 hybrid scheme)           */
 #define HBSD_PRECOND_GLOBAL   1   /* step 6(a) only (Eq. globalprecond)                  */
@@ -124,7 +126,13 @@ typedef struct {
                            FP64; 0 in FP64 throughout.  The FP64 form ignores it.                      */
     int spmm_df64;      /* mixed form: 1 (default) computes the products of steps 3 and 7 and the
                            recomputation of Psi_H, Psi_S as hbsd_spmm_pair_df64 does, and checks
-                           convergence on FP64 products; 0 in FP64.  The FP64 form ignores it.        */
+                           convergence on FP64 products; 0 in FP64.  Double-float sums carry about
+                           48 bits: where the terms of H x, or of the Gram and update sums, cancel
+                           strongly, the residuals stop short of tol.  So when the best Res_max has
+                           not halved in 10 outer iterations once below 1e4 tol (or in 30 at any
+                           level), the mixed form recomputes Psi_H and Psi_S in FP64 and runs the
+                           products, the Gram and the update in FP64 from then on
+                           (hbsd_stats.fp64_from_iter).  The FP64 form ignores it.                   */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */
@@ -162,6 +170,10 @@ typedef struct {
     double gram_fma;         /* algorithmic multiply-adds of step 8 over the solve: n q (q+1)
                                 per call (both reduced matrices, one triangle each)            */
     double update_fma;       /* algorithmic multiply-adds of steps 10-11: 3 n q w per call     */
+    int fp64_from_iter;      /* mixed form: the outer iteration from which the products of
+                                steps 3/7, the Gram and the update ran in FP64 because Res_max
+                                had stalled in double-float (no halving of its best value in 10
+                                iterations once below 1e4 tol, or in 30); -1: never            */
 } hbsd_stats;
 
 typedef struct hbsd_handle hbsd_handle;
@@ -441,6 +453,72 @@ int hbsd_session_release(hbsd_server* sv, int64_t session_id);
 /* Waits for the running requests, stops the workers and frees every session; queued requests
  * are dropped. */
 void hbsd_server_destroy(hbsd_server* sv);
+
+/* ---- Batched form (many resident sessions solved in one call) --------------------------------
+ *
+ * Independent problems of uneven size -- k-points, SCF runs, configurations (Sec. 5: each is a
+ * separate eigenproblem of the same method) -- created beforehand with hbsd_create, each with
+ * its own stream, and solved together: worker threads take the sessions longest-first by the
+ * estimated cost nev' (nnz + n nev') with nev' the block width, and run each solve on its
+ * session's stream, so that the kernels of different sessions overlap on the device.  Before
+ * that, each session that has not been tuned for its block width is tuned (hbsd_autotune).
+ *
+ * Autotuner: for one session and block width w, times the candidate launch shapes of the two
+ * steps whose best shape depends on the problem's size, on seeded data on the session's stream,
+ * and keeps the fastest for the session's later solves:
+ *   - the fused SpMM of steps 3/7 (in the session's precision form; w columns): the most lanes
+ *     per matrix row, 4, 8, 16 or 32 (fewer lanes per row put more rows in a CTA and more
+ *     column chunks in a lane);
+ *   - the cooperative MINRES launch of step 6(b) (min(w, 32) columns, 10 steps): its CTA count,
+ *     the whole GPU or 1/2 ... 1/32 of it; the smallest count within 10% of the fastest is kept
+ *     (cheaper grid barriers, and SMs left to the other sessions of a batch).
+ * Results of sessions with equal precision form, block width and n, nnz within 6% are shared
+ * (a process-wide table), so a batch of similar problems is timed once per size class.  Tuning
+ * changes the order of floating-point sums in those two steps only; a tuned session solved alone
+ * gives bit for bit the results it gives in a batch. */
+typedef struct {
+    int width;                 /* block width tuned for                                         */
+    int spmm_lanes;            /* chosen most lanes per row of the fused SpMM                   */
+    int minres_ctas;           /* chosen CTA count of the MINRES launch                          */
+    int minres_ctas_full;      /* the whole-GPU CTA count                                        */
+    int from_table;            /* 1: taken from an earlier session of the same size class       */
+    double spmm_ms[4];         /* time per candidate (4, 8, 16, 32 lanes), ms; 0 if not timed    */
+    double minres_ms[6];       /* time per candidate (full, 1/2, ..., 1/32 of the CTAs), ms     */
+} hbsd_tune;
+
+/* Tune session h for solves of block width `width` (nev + m0, or 2 (nev + m0) on a complex
+ * session; see hbsd_solve).  Synchronous; allocates and frees scratch blocks of n x width.
+ * out: nullable.  HBSD_ERR_ARG for width < 1. */
+int hbsd_autotune(hbsd_handle* h, int width, hbsd_tune* out);
+
+typedef struct {
+    hbsd_handle* h;            /* a session; each at most once per call                          */
+    int nev;
+    double tol;
+    const double* X0_dev;      /* as hbsd_solve_device: device start block or NULL              */
+    int64_t ldx0;
+    double* lambda_dev;        /* device, nev doubles                                            */
+    double* X_dev;             /* device, n x nev row-major (ld = ldx), or NULL                  */
+    int64_t ldx;
+    /* out */
+    int status;                /* of this session's solve: HBSD_OK, HBSD_NOT_CONVERGED, error   */
+    int iters;
+    double res_max;
+    double run_ms;             /* wall time of this session's solve                             */
+    double start_ms;           /* its start, from the call's start                              */
+} hbsd_batch_item;
+
+typedef struct {
+    int max_concurrent;        /* sessions solved at once (1..64); default 8                     */
+    int autotune;              /* 1 (default): tune untuned sessions first; 0: built-in shapes  */
+    int longest_first;         /* 1 (default): by estimated cost; 0: in the given order          */
+} hbsd_batch_opts;
+
+void hbsd_batch_opts_default(hbsd_batch_opts* opts);
+/* Solves every item; returns HBSD_OK when every item's status is HBSD_OK, else the first item's
+ * status (in item order) that is not.  HBSD_ERR_ARG (nothing run) for a NULL or repeated
+ * handle, count < 0, max_concurrent outside [1, 64]. */
+int hbsd_solve_batch(hbsd_batch_item* items, int count, const hbsd_batch_opts* opts);
 
 /* Double-float forms of hbsd_gram and hbsd_update, the ones the mixed form (HBSD_PRECISION_MIXED)
  * runs: FP64 inputs and outputs, products and short sums in pairs of floats (about 48 bits per

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhbsd.so")
 
-SOURCES = ["sell.cu", "dense.cu", "chol.cu", "minres.cu", "solver.cu", "probe.cu", "rr.cu", "df64.cu", "server.cu", "nonlocal.cu", "complex.cu", "tc_gemm.cu", "oz.cu"]
+SOURCES = ["sell.cu", "dense.cu", "chol.cu", "minres.cu", "solver.cu", "probe.cu", "rr.cu", "df64.cu", "server.cu", "nonlocal.cu", "complex.cu", "tc_gemm.cu", "oz.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-I", INCLUDE, "-I", CSRC]

@@ -355,7 +355,16 @@ struct Session {
     DBuf<double2> cx_a, cx_l, cx_m;  // recovery: Gram (eliminated in place), Cholesky columns, inverse
     DBuf<int> cx_piv;
     std::vector<double> res_hist;   // Res_max at each convergence test of the last solve
+    // launch shapes picked by the autotuner (batch.cu); 0 = the built-in choice
+    int tune_spmm_lpr = 0;          // most lanes per row of the fused SpMM (4, 8, 16 or 32)
+    int tune_mr_grid = 0;           // CTAs of the cooperative MINRES launch
+    int tuned_width = 0;            // block width the session was tuned for (0: not tuned)
 };
+
+// nev + m0 real columns of the block a solve of nev pairs runs on (twice that on a complex session)
+int block_width(const Session& s, int nev);
+// time the candidate launch shapes on this session and keep the fastest (batch.cu)
+int autotune(Session* s, int width, hbsd_tune* out);
 
 // nonlocal term (nonlocal.cu)
 int nl_set(Session* s, int k, const double* F, int64_t ldf, const double* G);

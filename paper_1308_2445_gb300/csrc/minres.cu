@@ -889,7 +889,10 @@ int minres_batch(Session* s, const T* R, int64_t ldr, const T* e, int k, double 
         blocks_per_sm[ti] = std::min(nb, nb2);
     }
     if (blocks_per_sm[ti] < 1) return fail(HBSD_ERR_UNSUPPORTED, "minres: kernel cannot be resident");
-    const int grid = blocks_per_sm[ti] * num_sms;
+    // the whole GPU, or fewer CTAs where the autotuner found them as fast (small problems: cheaper
+    // grid barriers, and SMs left to the other sessions of a batch)
+    const int full = blocks_per_sm[ti] * num_sms;
+    const int grid = s->tune_mr_grid > 0 ? std::min(s->tune_mr_grid, full) : full;
     init_lk.unlock();
     const int64_t kp = round_up(k, 4);
     HBSD_TRY(s->mr_red.alloc((size_t)2 * grid * kp));

@@ -262,6 +262,12 @@ const double2* values_of<double>(const Sell& m) { return m.hs.p; }
 template <>
 const float2* values_of<float>(const Sell& m) { return m.hs32.p; }
 
+// most lanes per row: the autotuner's choice for the session, else 32
+static int spmm_lanes(const Session* s) {
+    const int v = s ? s->tune_spmm_lpr : 0;
+    return (v == 4 || v == 8 || v == 16) ? v : 32;
+}
+
 template <class T, int MODE>
 static int spmm_launch(Session* s, const Sell& m, const T* X, int64_t ldx, int k, T* Y0, int64_t ld0,
                        T* Y1, int64_t ld1, const T* e, cudaStream_t st) {
@@ -269,13 +275,16 @@ static int spmm_launch(Session* s, const Sell& m, const T* X, int64_t ldx, int k
     if (k <= 0) return 0;
     if ((ldx % VW) || (ld0 % VW) || (MODE == 0 && (ld1 % VW)))
         return fail(HBSD_ERR_ARG, "spmm: leading dimensions must be multiples of the vector width");
-    // columns are processed in passes of at most 32 lanes * VW * 4 chunks
-    const int pass_cols = 32 * VW * 4;
+    // columns are processed in passes of at most lpr_max lanes * VW * 4 chunks; each row gets the
+    // smallest power-of-two number of lanes (up to lpr_max, the autotuner's choice) that covers
+    // its vectors in at most 4 chunks
+    const int lpr_max = spmm_lanes(s);
+    const int pass_cols = lpr_max * VW * 4;
     for (int c0 = 0; c0 < k; c0 += pass_cols) {
         const int kk = std::min(pass_cols, k - c0);
         int vecs = ceil_div(kk, VW);
         int lpr = 1, lg = 0;
-        while (lpr < vecs && lpr < 32) { lpr <<= 1; ++lg; }
+        while (lpr < vecs && lpr < lpr_max) { lpr <<= 1; ++lg; }
         const int ch = ceil_div(vecs, lpr);
         const int rows_per_cta = 256 / lpr;
         const int grid = ceil_div(m.n_slots, rows_per_cta);
@@ -394,12 +403,13 @@ int spmm_pair_df64(Session* s, const Sell& m, const double* X, int64_t ldx, int 
         k_split_scaled<<<g, 256, 0, st>>>(X, ldx, k, m.n, m.dinv.p, s->x2.p, ld2);
         HBSD_LAUNCHED(s);
     }
-    const int pass_cols = 32 * 2 * 4;
+    const int lpr_max = spmm_lanes(s);
+    const int pass_cols = lpr_max * 2 * 4;
     for (int c0 = 0; c0 < k; c0 += pass_cols) {
         const int kk = std::min(pass_cols, k - c0);
         const int vecs = ceil_div(kk, 2);
         int lpr = 1, lg = 0;
-        while (lpr < vecs && lpr < 32) { lpr <<= 1; ++lg; }
+        while (lpr < vecs && lpr < lpr_max) { lpr <<= 1; ++lg; }
         const int ch = ceil_div(vecs, lpr);
         const int rows_per_cta = 256 / lpr;
         const int grid = ceil_div(m.n_slots, rows_per_cta);

@@ -243,11 +243,12 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     // runs) would treat scaled-S_R pivots below 1e-6 as dependent directions: its Gram entries
     // carry ~1e-7 relative noise.
     const double drop_tol = sizeof(T) == 4 ? 1e-6 : 0.0;
-    const bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
+    bool dfp = o.precision == HBSD_PRECISION_MIXED && S->opt_df64;   // double-float Gram / update
     const bool tcu = o.precision == HBSD_PRECISION_MIXED && o.tc_update != 0;   // tensor-core update
     // products of steps 3/7 and the Psi_H, Psi_S recomputation: double-float on the scaled pencil
     // in the mixed form (spmm_df64), FP64 otherwise
-    const bool dfs = std::is_same<T, double>::value && o.precision == HBSD_PRECISION_MIXED && o.spmm_df64 != 0;
+    bool dfs = std::is_same<T, double>::value && o.precision == HBSD_PRECISION_MIXED && o.spmm_df64 != 0;
+    stt.fp64_from_iter = -1;
     auto products = [&](const T* Xp, int64_t ldx, int k, T* HXp, int64_t ldh, T* SXp, int64_t lds) -> int {
         if constexpr (std::is_same<T, double>::value) {
             if (dfs) return spmm_pair_df64(S, S->A, Xp, ldx, k, HXp, ldh, SXp, lds, st);
@@ -342,6 +343,35 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         }
         certified = false;
         if (iters >= rule.max_iters) break;
+        // precision escalation: double-float sums carry ~48 bits, and where the terms of H x, or of
+        // the Gram and update sums, cancel strongly the residuals stall above tol (measured: near
+        // 1e-6 on enriched 16^3-40^3 problems whose FP64 solves converge in 23-160 iterations; on
+        // some only FP64 products restore convergence, on others also an FP64 Gram and update).
+        // A stall -- no halving of the best Res_max over the last 10 iterations once it has been
+        // below 1e4 tol, or over the last 30 at any level (the plateaus of a cluster cut by the
+        // block edge, as at 32^3 with m0 = 7, last fewer than 30 around 1e-2) -- switches the
+        // products of steps 3/7, the Gram and the update to FP64 for the rest of the solve; Psi_H
+        // and Psi_S are recomputed from Psi in FP64 and the residual test repeated.
+        auto stalled = [&](int win, double below) -> bool {
+            if ((int)hist.size() <= win) return false;
+            double best_before = hist[0];
+            for (size_t i = 0; i + win < hist.size(); ++i) best_before = std::min(best_before, hist[i]);
+            double best_recent = hist[hist.size() - win];
+            for (size_t i = hist.size() - win; i < hist.size(); ++i) best_recent = std::min(best_recent, hist[i]);
+            return best_before < below && best_recent > 0.5 * best_before;
+        };
+        if ((dfs || dfp) && (stalled(10, 1e4 * rule.tol) || stalled(30, 1e300))) {
+            dfs = false;
+            dfp = false;
+            stt.fp64_from_iter = iters;
+            hs_fresh = true;
+            ti = tm.begin(StepTimer::MATVEC, st);
+            HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));
+            tm.end(ti, st);
+            stt.matvec_cols += w;
+            hist.pop_back();
+            continue;
+        }
         if (rule.stagnation && (int)hist.size() > rule.window) {
             double best_before = hist[0];
             for (size_t i = 0; i + rule.window < hist.size(); ++i) best_before = std::min(best_before, hist[i]);
@@ -508,13 +538,15 @@ __global__ void k_convert_block(const S_* __restrict__ src, int64_t lds, int k, 
     }
 }
 
-// Whole solve.  FP64: every step in FP64.  Mixed: the same FP64 iteration with step 6(a) -- the
-// global preconditioner, which only shapes the search directions -- in FP32 on the diagonally
-// scaled pencil (D A D, D = diag(S)^{-1/2}, which keeps the numbers inside the FP32 range).
-// Residuals, MINRES, block products, Gram and Rayleigh-Ritz stay FP64: the directions K r carry
-// components along the shared near-null space of H and S amplified ~1e11; extracting the
-// subspace from them in FP32 diverges, and FP32 MINRES on them multiplies the outer iterations
-// (both measured on the 32^3 workload).
+// Whole solve.  FP64: every step in FP64.  Mixed: the same iteration with step 6(a) -- the global
+// preconditioner, which only shapes the search directions -- in FP32 on the diagonally scaled
+// pencil (D A D, D = diag(S)^{-1/2}, which keeps the numbers inside the FP32 range); the operator
+// products inside MINRES in FP32 on that pencil (vectors and recurrences FP64); the block
+// products of steps 3/7, the Gram and the update in double-float (~48 bits) on the FP32 pipes,
+// with the products escalated to FP64 when the residual stalls; residual norms, Rayleigh-Ritz and
+// the final convergence test in FP64.  The directions K r carry components along the shared
+// near-null space of H and S amplified ~1e11: extracting the subspace from them in plain FP32
+// diverges (measured on the 32^3 workload), hence the double-float Gram and update.
 static int labpsd_solve(Session* S, int m, double tol, const double* X0, int64_t ldx0, double* lam_dev,
                         double* X_dev, int64_t ldx, int* iters_out, int m0_force = -1) {
     cudaStream_t st = S->stream;
@@ -758,6 +790,10 @@ void hbsd_get_stats(const hbsd_handle* h, hbsd_stats* st) {
 }
 
 static int m0_of(const Session& S, int nev) { return S.opt.m0 >= 0 ? S.opt.m0 : std::max(3, (nev + 9) / 10); }
+
+extern "C++" {
+int hbsd::block_width(const Session& s, int nev) { return (nev + m0_of(s, nev)) * (s.cplx ? 2 : 1); }
+}
 
 // Complex session: LABPSD on the real-equivalent pencil for 2 nev pairs from the realified start
 // block Yb (2 n_c x 2 (nev + m0), ld ldy; columns J-paired), then the complex recovery.

@@ -82,10 +82,31 @@ class hbsd_stats(C.Structure):
                 ("t_local_ms", C.c_double), ("t_gram_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_update_ms", C.c_double), ("matvec_cols", C.c_int64), ("minres_spmm_cols", C.c_int64),
                 ("precond_calls", C.c_int), ("local_calls", C.c_int64), ("neg_pivots", C.c_int64),
-                ("gram_fma", C.c_double), ("update_fma", C.c_double)]
+                ("gram_fma", C.c_double), ("update_fma", C.c_double), ("fp64_from_iter", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hbsd_tune(C.Structure):
+    _fields_ = [("width", C.c_int), ("spmm_lanes", C.c_int), ("minres_ctas", C.c_int), ("minres_ctas_full", C.c_int),
+                ("from_table", C.c_int), ("spmm_ms", C.c_double * 4), ("minres_ms", C.c_double * 6)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["spmm_ms"] = list(self.spmm_ms)
+        d["minres_ms"] = list(self.minres_ms)
+        return d
+
+
+class hbsd_batch_item(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("nev", C.c_int), ("tol", C.c_double), ("X0_dev", C.c_void_p), ("ldx0", C.c_int64),
+                ("lambda_dev", C.c_void_p), ("X_dev", C.c_void_p), ("ldx", C.c_int64), ("status", C.c_int),
+                ("iters", C.c_int), ("res_max", C.c_double), ("run_ms", C.c_double), ("start_ms", C.c_double)]
+
+
+class hbsd_batch_opts(C.Structure):
+    _fields_ = [("max_concurrent", C.c_int), ("autotune", C.c_int), ("longest_first", C.c_int)]
 
 
 _P = C.c_void_p
@@ -136,6 +157,9 @@ _SIGS = {
     "hbsd_server_destroy": (None, [C.c_void_p]),
     "hbsd_probe_peak": (C.c_int, [C.c_int, _P, C.POINTER(C.c_double)]),
     "hbsd_seed_normals": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int64, _D]),
+    "hbsd_autotune": (C.c_int, [_P, C.c_int, C.POINTER(hbsd_tune)]),
+    "hbsd_batch_opts_default": (None, [C.POINTER(hbsd_batch_opts)]),
+    "hbsd_solve_batch": (C.c_int, [C.POINTER(hbsd_batch_item), C.c_int, C.POINTER(hbsd_batch_opts)]),
 }
 
 _lib = None
@@ -308,6 +332,16 @@ class Session:
                    "hbsd_solve_device")
         return it.value, rc, st.as_dict()
 
+    def block_width(self, nev):
+        """Real columns of the block a solve of nev pairs runs on."""
+        return (nev + self.m0(nev)) * (2 if self.is_complex else 1)
+
+    def autotune(self, nev):
+        """hbsd_autotune for solves of nev pairs; returns the chosen shapes and the timings."""
+        t = hbsd_tune()
+        check(lib().hbsd_autotune(self.h, self.block_width(nev), C.byref(t)), "hbsd_autotune")
+        return t.as_dict()
+
     # ---- step-level calls on torch CUDA tensors (row-major, float64) ----
     def spmm_pair(self, X, HX, SX):
         check(lib().hbsd_spmm_pair(self.h, ptr(X), ld(X), X.shape[1], ptr(HX), ld(HX), ptr(SX), ld(SX)),
@@ -387,6 +421,32 @@ def seed_normals(seed, stream, count):
     out = np.empty(count)
     check(lib().hbsd_seed_normals(seed, stream, count, out.ctypes.data_as(_D)), "hbsd_seed_normals")
     return out
+
+
+def solve_batch(entries, max_concurrent=8, autotune=True, longest_first=True):
+    """hbsd_solve_batch.  entries: (session, nev, tol, X0 or None, lam, X or None) with device tensors
+    as in Session.solve_device.  Returns (status, [per-entry dict of status, iters, res_max, run_ms,
+    start_ms])."""
+    items = (hbsd_batch_item * max(1, len(entries)))()
+    for i, (sess, nev, tol, X0, lam, X) in enumerate(entries):
+        it = items[i]
+        it.h = sess.h
+        it.nev = nev
+        it.tol = tol
+        it.X0_dev = ptr(X0)
+        it.ldx0 = ld(X0) if X0 is not None else 0
+        it.lambda_dev = ptr(lam)
+        it.X_dev = ptr(X)
+        it.ldx = ld(X) if X is not None else 0
+    o = hbsd_batch_opts()
+    lib().hbsd_batch_opts_default(C.byref(o))
+    o.max_concurrent = max_concurrent
+    o.autotune = int(bool(autotune))
+    o.longest_first = int(bool(longest_first))
+    rc = check(lib().hbsd_solve_batch(items, len(entries), C.byref(o)), "hbsd_solve_batch")
+    out = [{"status": items[i].status, "iters": items[i].iters, "res_max": items[i].res_max,
+            "run_ms": items[i].run_ms, "start_ms": items[i].start_ms} for i in range(len(entries))]
+    return rc, out
 
 
 class Server:

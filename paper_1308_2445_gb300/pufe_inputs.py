@@ -425,6 +425,41 @@ def large_case(seed: int = 1) -> Problem:
 LARGE_NEV = 256
 
 
+# ---- the batched workload: uneven independent instances ---------------------------------
+
+BATCH_MESHES = (16, 24, 32, 40)
+BATCH_NEVS = (32, 64, 128)
+BATCH_RC = 0.15
+
+
+def batch_spec(seed: int, count: int = 64, meshes=BATCH_MESHES, nevs=BATCH_NEVS):
+    """Instance list of the batched workload, drawn from (seed, STREAM_BATCH): per instance
+    (mesh, atoms, enrichment dofs per node, instance seed, nev) with the mesh from `meshes`,
+    4-16 atoms, 2-4 enrichment dofs within r_c = 0.15 and nev from `nevs`, all uniform."""
+    u = uniform(seed, STREAM_BATCH, 5 * count).reshape(count, 5)
+    out = []
+    for i in range(count):
+        out.append((int(meshes[min(len(meshes) - 1, int(u[i, 0] * len(meshes)))]),
+                    4 + min(12, int(u[i, 1] * 13)),
+                    2 + min(2, int(u[i, 2] * 3)),
+                    1 + int(u[i, 3] * (1 << 30)),
+                    int(nevs[min(len(nevs) - 1, int(u[i, 4] * len(nevs)))])))
+    return out
+
+
+def batch_instance(spec) -> tuple:
+    """(Problem, nev, atoms placed) of one batch_spec entry, real (Gamma point).  Where the drawn
+    number of atoms does not fit with non-overlapping r_c spheres, one fewer is tried."""
+    mesh, atoms, enr, s, nev = spec
+    while True:
+        try:
+            return generate(mesh, atoms, enr, BATCH_RC, s), nev, atoms
+        except (ValueError, RuntimeError):
+            if atoms <= 1:
+                raise
+            atoms -= 1
+
+
 def closed_form_eigenvalues(n_el: int, v0: float, kpt=None) -> np.ndarray:
     """All eigenvalues of the unenriched periodic Q1 pair with constant V = v0, ascending.
 

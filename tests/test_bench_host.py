@@ -1,6 +1,7 @@
 """Host logic of bench.py's roofline object, on synthetic step statistics (no GPU): the dominant
 step class is chosen by device time; FP64 classes are reported against the FP64 FMA rate, the
 FP32 sweeps of the mixed form against HBM bandwidth with their algorithmic bytes."""
+import json
 import os
 import sys
 
@@ -94,3 +95,12 @@ def test_mixed_form_products_are_fp32_pipe_rooflines():
     assert r["achieved"] == pytest.approx(bench.DF_FP32_OPS * 2.0 * 2_951_752 * st["matvec_cols"] / 0.9 / 1e12)
     r = bench.roofline_object(stats(), 2_951_752, 0, 1.25e12, "mixed", "medium", peak32=80e12)
     assert r["kernel"] == "minres" and r["unit"] == "TFLOP/s" and r["peak"] == pytest.approx(80.0)
+
+
+def test_batched_workload_is_a_bench_choice_and_has_no_reference_arm(capsys):
+    import bench
+    a = bench.parse(["--workload", "batched", "--impl", "reference"])
+    assert a.workload == "batched" and a.batch_count == 64 and a.batch_concurrent == 8
+    bench.run_reference(a)
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and "unavailable" in line

@@ -80,3 +80,19 @@ def test_scf_noise_changes_h_only():
     assert np.array_equal(a.s_val, b.s_val)
     assert not np.array_equal(a.h_val, b.h_val)
     assert np.abs(a.h_val - b.h_val).max() < 0.05 * np.abs(a.h_val).max()
+
+
+def test_batch_spec_is_seeded_and_within_the_recipe():
+    a = pi.batch_spec(1, 64)
+    assert a == pi.batch_spec(1, 64) and a != pi.batch_spec(2, 64)
+    assert pi.batch_spec(1, 8) == a[:8]   # a prefix of the same draws
+    for mesh, atoms, enr, seed, nev in a:
+        assert mesh in pi.BATCH_MESHES and nev in pi.BATCH_NEVS
+        assert 4 <= atoms <= 16 and 2 <= enr <= 4 and seed >= 1
+    # every mesh size and nev of the recipe occurs in 64 draws
+    assert {x[0] for x in a} == set(pi.BATCH_MESHES) and {x[4] for x in a} == set(pi.BATCH_NEVS)
+
+
+def test_batch_instance_places_fewer_atoms_when_they_do_not_fit():
+    p, nev, atoms = pi.batch_instance((8, 4, 2, 3, 16))
+    assert nev == 16 and 1 <= atoms <= 4 and p.n > 8 ** 3
