@@ -143,6 +143,29 @@ def test_brute_force_dense(case):
         assert _angles(r.X[:, :j], V[:, :j], Sd) < 1e-6
 
 
+def test_brute_force_extended_precision_at_kappa_3e10():
+    """A tiny case whose S is far worse conditioned than the 8^3 case (4^3 mesh, four enrichment
+    functions per node within r_c = 0.3: n = 92, kappa(D S D) = 2.6e10), where FP64 dense solvers
+    themselves err near 1e-10 relative.  Reference: the generalized eigenvalues in 40-digit
+    arithmetic (Cholesky S = L L^T, then the symmetric eigenvalues of L^-1 H L^-T, both in mpmath).
+    The oracle at Res <= 1e-8 meets the solver's bar, |dlambda| <= 1e-9 max|lambda|."""
+    mp = pytest.importorskip("mpmath")
+    p = pi.generate(4, 1, 4, 0.3, 1)
+    H, S = p.scipy_pair()
+    Hd, Sd = H.toarray(), S.toarray()
+    d = np.diag(Sd) ** -0.5
+    ks = np.linalg.eigvalsh(Sd * d[:, None] * d[None, :])
+    assert ks[-1] / ks[0] > 1e10
+    with mp.workdps(40):
+        Li = mp.inverse(mp.cholesky(mp.matrix(Sd.tolist())))
+        C = Li * mp.matrix(Hd.tolist()) * Li.T
+        ref = np.array(sorted(float(x) for x in mp.eigsy((C + C.T) / 2, eigvals_only=True)))
+    nev = 8
+    r = L.labpsd(p, nev, 1e-8, seed=1)
+    assert r.converged
+    assert np.abs(r.lam - ref[:nev]).max() <= 1e-9 * np.abs(ref[:nev]).max()
+
+
 def test_inertia_count_small(small_problem):
     # Sylvester: #eigenvalues below sigma = #negative eigenvalues of H - sigma S
     p = small_problem
