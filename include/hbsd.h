@@ -131,8 +131,9 @@ typedef struct {
                            strongly, the residuals stop short of tol.  So when the best Res_max has
                            not halved in 10 outer iterations once below 1e4 tol (or in 30 at any
                            level), the mixed form recomputes Psi_H and Psi_S in FP64 and runs the
-                           products, the Gram and the update in FP64 from then on
-                           (hbsd_stats.fp64_from_iter).  The FP64 form ignores it.                   */
+                           products in FP64 from then on (hbsd_stats.fp64_from_iter); after a
+                           further stall, the Gram and the update too (fp64_gram_from_iter).  The
+                           FP64 form ignores it.                                                     */
 } hbsd_options;
 
 /* Statistics of one solve (all counts cumulative over the solve). */
@@ -171,9 +172,11 @@ typedef struct {
                                 per call (both reduced matrices, one triangle each)            */
     double update_fma;       /* algorithmic multiply-adds of steps 10-11: 3 n q w per call     */
     int fp64_from_iter;      /* mixed form: the outer iteration from which the products of
-                                steps 3/7, the Gram and the update ran in FP64 because Res_max
-                                had stalled in double-float (no halving of its best value in 10
-                                iterations once below 1e4 tol, or in 30); -1: never            */
+                                steps 3/7 ran in FP64 because Res_max had stalled in double-
+                                float (no halving of its best value in 10 iterations once below
+                                1e4 tol, or in 30); -1: never                                   */
+    int fp64_gram_from_iter; /* mixed form: the same for the Gram and the update (a second
+                                stall after the first switch); -1: never                       */
 } hbsd_stats;
 
 typedef struct hbsd_handle hbsd_handle;
@@ -472,7 +475,7 @@ void hbsd_server_destroy(hbsd_server* sv);
  *   - the cooperative MINRES launch of step 6(b) (min(w, 32) columns, 10 steps): its CTA count,
  *     the whole GPU or 1/2 ... 1/32 of it; the smallest count within 10% of the fastest is kept
  *     (cheaper grid barriers, and SMs left to the other sessions of a batch).
- * Results of sessions with equal precision form, block width and n, nnz within 6% are shared
+ * Results of sessions with equal precision form, block width and n, nnz within 20% are shared
  * (a process-wide table), so a batch of similar problems is timed once per size class.  Tuning
  * changes the order of floating-point sums in those two steps only; a tuned session solved alone
  * gives bit for bit the results it gives in a batch. */

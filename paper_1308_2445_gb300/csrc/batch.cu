@@ -46,7 +46,7 @@ std::mutex g_tune_mu;
 std::vector<TuneEntry> g_tune_table;
 
 bool same_class(const TuneKey& a, const TuneKey& b) {
-    auto close = [](int64_t x, int64_t y) { return std::fabs((double)x - (double)y) <= 0.06 * (double)std::max(x, y); };
+    auto close = [](int64_t x, int64_t y) { return std::fabs((double)x - (double)y) <= 0.2 * (double)std::max(x, y); };
     return a.precision == b.precision && a.width == b.width && a.cplx == b.cplx && close(a.n, b.n) && close(a.nnz, b.nnz);
 }
 

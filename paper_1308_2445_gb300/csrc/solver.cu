@@ -248,7 +248,8 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
     // products of steps 3/7 and the Psi_H, Psi_S recomputation: double-float on the scaled pencil
     // in the mixed form (spmm_df64), FP64 otherwise
     bool dfs = std::is_same<T, double>::value && o.precision == HBSD_PRECISION_MIXED && o.spmm_df64 != 0;
-    stt.fp64_from_iter = -1;
+    stt.fp64_from_iter = stt.fp64_gram_from_iter = -1;
+    size_t esc_mark = 0;   // history length at the last precision switch
     auto products = [&](const T* Xp, int64_t ldx, int k, T* HXp, int64_t ldh, T* SXp, int64_t lds) -> int {
         if constexpr (std::is_same<T, double>::value) {
             if (dfs) return spmm_pair_df64(S, S->A, Xp, ldx, k, HXp, ldh, SXp, lds, st);
@@ -346,14 +347,15 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         // precision escalation: double-float sums carry ~48 bits, and where the terms of H x, or of
         // the Gram and update sums, cancel strongly the residuals stall above tol (measured: near
         // 1e-6 on enriched 16^3-40^3 problems whose FP64 solves converge in 23-160 iterations; on
-        // some only FP64 products restore convergence, on others also an FP64 Gram and update).
-        // A stall -- no halving of the best Res_max over the last 10 iterations once it has been
-        // below 1e4 tol, or over the last 30 at any level (the plateaus of a cluster cut by the
-        // block edge, as at 32^3 with m0 = 7, last fewer than 30 around 1e-2) -- switches the
-        // products of steps 3/7, the Gram and the update to FP64 for the rest of the solve; Psi_H
-        // and Psi_S are recomputed from Psi in FP64 and the residual test repeated.
+        // some FP64 products restore convergence, on others only FP64 products with an FP64 Gram
+        // and update).  A stall -- no halving of the best Res_max over the last 10 iterations once
+        // it has been below 1e4 tol, or over the last 30 at any level -- first moves the products
+        // of steps 3/7 to FP64 (Psi_H and Psi_S recomputed from Psi in FP64, the residual test
+        // repeated); a further stall, counted from that switch, moves the Gram and the update to
+        // FP64 too.  The first stage is cheap, so a false alarm on a slow but healthy trajectory
+        // (a plateau of a cluster cut by the block edge) costs little.
         auto stalled = [&](int win, double below) -> bool {
-            if ((int)hist.size() <= win) return false;
+            if ((int)(hist.size() - esc_mark) <= win) return false;
             double best_before = hist[0];
             for (size_t i = 0; i + win < hist.size(); ++i) best_before = std::min(best_before, hist[i]);
             double best_recent = hist[hist.size() - win];
@@ -361,9 +363,14 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
             return best_before < below && best_recent > 0.5 * best_before;
         };
         if ((dfs || dfp) && (stalled(10, 1e4 * rule.tol) || stalled(30, 1e300))) {
-            dfs = false;
-            dfp = false;
-            stt.fp64_from_iter = iters;
+            if (dfs) {
+                dfs = false;
+                stt.fp64_from_iter = iters;
+            } else {
+                dfp = false;
+                stt.fp64_gram_from_iter = iters;
+            }
+            esc_mark = hist.size() - 1;
             hs_fresh = true;
             ti = tm.begin(StepTimer::MATVEC, st);
             HBSD_TRY(spmm_pair<T>(S, S->A, B.Psi.p, ldw, w, B.PsiH.p, ldw, B.PsiS.p, ldw, st));

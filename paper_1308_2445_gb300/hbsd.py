@@ -82,7 +82,7 @@ class hbsd_stats(C.Structure):
                 ("t_local_ms", C.c_double), ("t_gram_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_update_ms", C.c_double), ("matvec_cols", C.c_int64), ("minres_spmm_cols", C.c_int64),
                 ("precond_calls", C.c_int), ("local_calls", C.c_int64), ("neg_pivots", C.c_int64),
-                ("gram_fma", C.c_double), ("update_fma", C.c_double), ("fp64_from_iter", C.c_int)]
+                ("gram_fma", C.c_double), ("update_fma", C.c_double), ("fp64_from_iter", C.c_int), ("fp64_gram_from_iter", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
