@@ -607,8 +607,10 @@ def main():
                        "nnz_L": st["nnz_L"], "res_max": st["res_max"], "rr_fallbacks": st["rr_fallbacks"],
                        "minres_steps": st["minres_steps"],
                        "l2": "working set > L2 (factor %.0f MB + matrix %.0f MB)" % (st["nnz_L"] * 8e-6, p.nnz * 20e-6),
-                       "kappa_S": "diagonally scaled kappa(S) 1.6e11 on the 32^3 workload (shift-invert Lanczos); "
-                                  "64^3 not measured",
+                       "kappa_S": {"large": 2.2e12, "medium": 1.6e11,
+                                   "what": "kappa(D S D), D = diag(S)^-1/2: lambda_max by Lanczos (scipy), lambda_min "
+                                           "by an FP64 solve of (D S D) x = lambda x with the library (its factor of D "
+                                           "S D as the preconditioner; the 32^3 value matches shift-invert Lanczos)"},
                        "fp64": fp64,
                        "parallelism": "replicas" if ws > 1 else "single"},
             "accuracy": acc,

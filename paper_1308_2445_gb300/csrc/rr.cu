@@ -854,8 +854,18 @@ __global__ void __launch_bounds__(RR_THREADS_C, 1)
             for (int l = lane; l < i; l += 32) xv[l] = fma(-li[l], xi, xv[l]);
             __syncwarp();
         }
-        for (int i = lane; i < q; i += 32) Wout[(int64_t)i * k + j] = dv[i] * xv[i];
-        if (lane == 0) theta[j] = W.lamr[ord[j]];
+        bool bad = false;   // a non-finite output (an eigenvector block that CholeskyQR could not
+                            // orthonormalise) sends the call to the single-CTA QL solver
+        for (int i = lane; i < q; i += 32) {
+            const double v = dv[i] * xv[i];
+            bad |= !isfinite(v);
+            Wout[(int64_t)i * k + j] = v;
+        }
+        if (lane == 0) {
+            theta[j] = W.lamr[ord[j]];
+            bad |= !isfinite(theta[j]);
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&info[2], 1);
         __syncwarp();
     }
     if (rank == 0 && tid == 0) {
@@ -1003,7 +1013,10 @@ int rayleigh_ritz_cluster(Session* s, const double* HR, const double* SR, int q,
                      q, k, used_nc, used_stage, (t[1] - t[0]) * 1e-3, (t[2] - t[1]) * 1e-3, (t[3] - t[2]) * 1e-3,
                      (t[4] - t[3]) * 1e-3, (t[7] - t[4]) * 1e-3, (t[5] - t[7]) * 1e-3, (t[6] - t[5]) * 1e-3);
     }
-    if (info[3]) return rayleigh_ritz(s, HR, SR, q, k, theta, W, info_host, st);   // Cholesky breakdown
+    // Cholesky breakdown (info[3]) or a non-finite output (info[2]): the single-CTA kernel, whose
+    // implicit QL iteration gives orthonormal eigenvectors of T whatever the multiplicities (the
+    // J-paired blocks of a complex session have every eigenvalue twice)
+    if (info[3] || info[2]) return rayleigh_ritz(s, HR, SR, q, k, theta, W, info_host, st);
     if (info_host) { info_host[0] = info[0]; info_host[1] = info[1]; }
     if (info[1] < k) return fail(HBSD_ERR_RR_RANK, "rayleigh_ritz: search space rank below k");
     return 0;

@@ -161,3 +161,27 @@ def test_complex_and_real_inputs_do_not_mix():
     h = C.c_void_p()
     rc = hbsd.lib().hbsd_create(C.byref(H), C.byref(S), C.byref(lb), C.byref(o), None, C.byref(h))
     assert rc == hbsd.HBSD_ERR_ARG and h.value is None
+
+
+@pytest.mark.parametrize("mesh,atoms,enr,seed,kpt,nev", [
+    (24, 4, 3, 764689141, (-0.5 * np.pi, 0.5 * np.pi, 0.5 * np.pi), 32),
+    (16, 10, 2, 855858841, (0.5 * np.pi, 0.5 * np.pi, -0.5 * np.pi), 64)])
+def test_bloch_solves_where_the_cluster_rayleigh_ritz_broke_down(mesh, atoms, enr, seed, kpt, nev):
+    """Two Bloch problems of the served request mix on which the 16-CTA Rayleigh-Ritz once returned
+    non-finite eigenvectors in the mixed form (the J-paired search block has every eigenvalue
+    twice, and CholeskyQR of the inverse-iteration vectors broke down); such a call now falls
+    back to the single-CTA kernel and its implicit QL iteration.  Both forms converge, to the same
+    eigenvalues, with S-orthonormal complex eigenvectors."""
+    p = pi.generate(mesh, atoms, enr, 0.15, seed, kpt=kpt)
+    out = {}
+    for prec in (hb().PRECISION_MIXED, hb().PRECISION_FP64):
+        s = hb().Session.from_problem(p, precision=prec)
+        lam, X, it, rc, st = s.solve(nev, 1e-8)
+        s.close()
+        assert rc == 0 and np.all(np.isfinite(lam))
+        out[prec] = (lam, X)
+    lam_m, X = out[hb().PRECISION_MIXED]
+    lam_d, _ = out[hb().PRECISION_FP64]
+    assert np.abs(lam_m - lam_d).max() <= 1e-9 * np.abs(lam_d).max()
+    H, S = p.scipy_pair()
+    assert np.abs(X.conj().T @ (S @ X) - np.eye(nev)).max() <= 1e-9
