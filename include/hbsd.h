@@ -394,7 +394,12 @@ int hbsd_update(double* Z, int64_t ldz, int64_t n, int q, const double* W, int k
  * resident for follow-up requests (SCF steps, Sec. 3: new H values on the same pattern, warm
  * start from the previous block; the factor of the session's first H is kept, reading R2).
  * Idle sessions are evicted least-recently-used first when memory is short, or released by the
- * caller.  Device-memory use is estimated per problem from n, nnz and nev.  All functions are
+ * caller.  Admission reserves a per-problem estimate of device memory (from n, nnz and nev,
+ * scaled by the largest ratio of a request's peak device allocation to its estimate seen so
+ * far, at least 1.25); once a request ends,
+ * its session's measured footprint (the device memory its create and solves left allocated)
+ * replaces the reservation.  A request whose allocation still fails on the device frees every
+ * idle session and retries once before it reports HBSD_ERR_OOM.  All functions are
  * thread-safe. */
 typedef struct {
     size_t hbm_budget_bytes;  /* device memory the server may hold; 0 = 80% of the free memory */

@@ -62,6 +62,10 @@ int guarded(F&& body) noexcept {
 
 struct Session;
 void count_launch(Session* s);
+// device bytes held by the DBufs this thread allocated minus those it released (a thread's
+// difference across a call is what the call left allocated; the served form's footprints)
+int64_t& tl_dev_bytes();
+int64_t& tl_dev_peak();   // the largest value tl_dev_bytes() has reached on this thread
 
 // ---- device memory owned by a session ---------------------------------------------------
 template <class T>
@@ -88,12 +92,17 @@ int DBuf<T>::alloc(size_t count) {
         return fail(HBSD_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
     }
     n = count;
+    tl_dev_bytes() += (int64_t)(count * sizeof(T));
+    if (tl_dev_bytes() > tl_dev_peak()) tl_dev_peak() = tl_dev_bytes();
     return 0;
 }
 
 template <class T>
 void DBuf<T>::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        cudaFree(p);
+        tl_dev_bytes() -= (int64_t)(n * sizeof(T));
+    }
     p = nullptr;
     n = 0;
 }

@@ -10,6 +10,7 @@
 // eviction of idle sessions when memory is short.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -49,7 +50,8 @@ struct Request {
     std::vector<double> X0;
     double* lam_out = nullptr;
     double* X_out = nullptr;
-    size_t est_bytes = 0;
+    size_t est_raw = 0;      // footprint estimate from n, nnz, nev (new problem)
+    size_t est_bytes = 0;    // what admission reserved: est_raw times the server's calibration
     Clock::time_point t_submit;
 };
 
@@ -67,12 +69,17 @@ struct SessionRec {
 };
 
 size_t estimate_bytes(int64_t n, int64_t nnz, int nev, int nl_k) {
-    // matrix (index + (h, s) pair), factor panels and solve panels (FP64 + FP32), ~16 nnz
-    // of fill per nonzero for 3-D nested dissection, ~16 FP64 blocks of n x (nev + m0), and
-    // with a nonlocal term the dense Fhat (FP64 + FP32) and its setup block
+    // matrix: ~1.2 nnz stored SELL entries x (index, FP64 pair, FP32 pair, double-float pair);
+    // factor: 24 bytes per entry (FP64 panels and their explicit inverses, two FP32 copies), its
+    // fill nnz(L)/nnz measured at 16.5 on the 32^3 workload (n = 47,620) and growing as n^0.35
+    // (39 at 64^3), plus a quarter for the factorisation's fronts; ~20 blocks of n x (nev + m0)
+    // doubles (the solve's blocks, MINRES vectors, FP32 and double-float copies, start block and
+    // warm-start copy); with a nonlocal term the dense Fhat (FP64 + FP32) and its setup block.
+    // The server scales this by the largest measured footprint / estimate seen so far.
     const int64_t w = nev + std::max(3, (nev + 9) / 10);
-    return (size_t)(20 * nnz + 16 * 20 * nnz + (int64_t)16 * 8 * n * w + (int64_t)20 * n * nl_k +
-                    ((int64_t)64 << 20));
+    const double fill = 16.5 * std::pow((double)std::max<int64_t>(n, 1000) / 47620.0, 0.35);
+    return (size_t)(56.0 * (double)nnz + 30.0 * fill * (double)nnz + 160.0 * (double)n * (double)w +
+                    20.0 * (double)n * (double)nl_k + (double)(64 << 20));
 }
 
 }  // namespace
@@ -86,7 +93,8 @@ struct hbsd_server {
     std::unordered_map<uint64_t, hbsd::ResultRec> results;
     std::unordered_map<int64_t, hbsd::SessionRec> sessions;
     std::vector<std::thread> workers;
-    size_t used = 0;   // estimated device bytes of resident sessions and running requests
+    size_t used = 0;   // device bytes of resident sessions (measured) and running requests (reserved)
+    double est_scale = 1.25;  // largest measured peak footprint / estimate so far (only grows)
     uint64_t next_ticket = 1;
     int64_t next_session = 0;
     int running = 0;
@@ -128,6 +136,16 @@ void bury(hbsd_server* sv) {
     }
 }
 
+// Evicts every idle session and destroys the evicted ones now (a request that met a device
+// out-of-memory error retries after this).  mu not held.
+void free_idle(hbsd_server* sv) {
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        evict_for(sv, sv->opts.hbm_budget_bytes + 1);   // as much as possible: every idle session
+    }
+    bury(sv);
+}
+
 // Next runnable request in arrival order, or null.  mu held.
 std::unique_ptr<Request> take_runnable(hbsd_server* sv) {
     for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
@@ -141,7 +159,7 @@ std::unique_ptr<Request> take_runnable(hbsd_server* sv) {
             }
             if (s->second.busy) continue;
         }
-        const size_t need = r.is_new ? r.est_bytes : 0;
+        const size_t need = r.is_new ? (size_t)((double)r.est_raw * sv->est_scale) : 0;
         if (sv->used + need > sv->opts.hbm_budget_bytes) {
             evict_for(sv, need);
             if (sv->used + need > sv->opts.hbm_budget_bytes && sv->running > 0) continue;   // wait for memory
@@ -155,6 +173,8 @@ std::unique_ptr<Request> take_runnable(hbsd_server* sv) {
 
 void run_request(hbsd_server* sv, Request& rq) {
     const Clock::time_point t_start = Clock::now();
+    const int64_t dev0 = tl_dev_bytes();   // this thread's device bytes before the request
+    tl_dev_peak() = dev0;
     hbsd_result res{};
     res.ticket = rq.ticket;
     int64_t sid = rq.session_id;
@@ -172,6 +192,10 @@ void run_request(hbsd_server* sv, Request& rq) {
             lb.dof_cluster = rq.dof_cluster.empty() ? nullptr : rq.dof_cluster.data();
             std::memcpy(lb.grid, rq.grid, sizeof(lb.grid));
             rc = hbsd_create(&H, &S, &lb, &rq.opt, stream, &h);
+            if (rc == HBSD_ERR_OOM) {   // the device ran short despite admission: free every idle session, retry once
+                free_idle(sv);
+                rc = hbsd_create(&H, &S, &lb, &rq.opt, stream, &h);
+            }
             if (rc >= 0 && rq.nl_k > 0) {
                 rc = hbsd_set_nonlocal(h, rq.nl_k, rq.nl_F.data(), rq.nl_k, rq.nl_G.data());
                 if (rc < 0) {
@@ -183,13 +207,14 @@ void run_request(hbsd_server* sv, Request& rq) {
             if (rc < 0) {
                 cudaStreamDestroy(stream);
                 sv->used -= std::min(sv->used, rq.est_bytes);
+                rq.est_bytes = 0;
             } else {
                 sid = sv->next_session++;
                 SessionRec rec;
                 rec.h = h;
                 rec.stream = stream;
                 rec.busy = true;
-                rec.bytes = rq.est_bytes;
+                rec.bytes = 0;   // set from the measured footprint when the request ends
                 rec.last_use = Clock::now();
                 sv->sessions[sid] = rec;
             }
@@ -206,10 +231,19 @@ void run_request(hbsd_server* sv, Request& rq) {
         hbsd_stats st{};
         rc = hbsd_solve(h, rq.nev, rq.tol, rq.X0.empty() ? nullptr : rq.X0.data(), rq.warm, rq.lam_out, rq.X_out,
                         &iters, &st);
+        if (rc == HBSD_ERR_OOM) {
+            free_idle(sv);
+            rc = hbsd_solve(h, rq.nev, rq.tol, rq.X0.empty() ? nullptr : rq.X0.data(), rq.warm, rq.lam_out, rq.X_out,
+                            &iters, &st);
+        }
         res.iters = iters;
         res.res_max = st.res_max;
     }
     const Clock::time_point t_end = Clock::now();
+    // the session's footprint: what this request left allocated (all of a new session: its
+    // matrix, factor and solve buffers; a follow-up's growth), replacing the reservation
+    const int64_t grown = std::max<int64_t>(0, tl_dev_bytes() - dev0);
+    const int64_t peak = std::max<int64_t>(grown, tl_dev_peak() - dev0);   // with the factorisation's fronts
     res.status = rc;
     res.session_id = rc >= 0 || !rq.is_new ? sid : -1;
     res.queue_ms = std::chrono::duration<double, std::milli>(t_start - rq.t_submit).count();
@@ -220,6 +254,14 @@ void run_request(hbsd_server* sv, Request& rq) {
     if (s != sv->sessions.end()) {
         s->second.busy = false;
         s->second.last_use = Clock::now();
+        if (rq.is_new) {
+            sv->used -= std::min(sv->used, rq.est_bytes);
+            s->second.bytes = (size_t)grown;
+            if (rq.est_raw > 0) sv->est_scale = std::max(sv->est_scale, (double)peak / (double)rq.est_raw);
+        } else {
+            s->second.bytes += (size_t)grown;
+        }
+        sv->used += (size_t)grown;
     }
     ResultRec& rr = sv->results[rq.ticket];
     rr.r = res;
@@ -241,6 +283,7 @@ void worker(hbsd_server* sv) {
                 auto s = sv->sessions.find(rq->session_id);
                 if (s != sv->sessions.end()) s->second.busy = true;
             } else {
+                rq->est_bytes = (size_t)((double)rq->est_raw * sv->est_scale);
                 sv->used += rq->est_bytes;
             }
             ++sv->running;
@@ -359,9 +402,9 @@ int hbsd_submit(hbsd_server* sv, const hbsd_request* rq, double* lambda_out, dou
                 r->nl_G.assign(rq->nl_G, rq->nl_G + (size_t)rq->nl_k * rq->nl_k);
             }
             // a complex problem runs as the real pencil of size 2n (4 nnz entries, 2 nev columns)
-            r->est_bytes = r->is_complex ? estimate_bytes(2 * n, 4 * r->nnz, 2 * rq->nev, 0)
-                                         : estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
-            if (r->est_bytes > sv->opts.hbm_budget_bytes) return fail(HBSD_ERR_OOM, "request exceeds the server's memory budget");
+            r->est_raw = r->is_complex ? estimate_bytes(2 * n, 4 * r->nnz, 2 * rq->nev, 0)
+                                       : estimate_bytes(n, r->nnz, rq->nev, r->nl_k);
+            if (r->est_raw > sv->opts.hbm_budget_bytes) return fail(HBSD_ERR_OOM, "request exceeds the server's memory budget");
         } else {   // follow-up of a resident session: new H values (optional), warm start or X0
             std::lock_guard<std::mutex> lk(sv->mu);
             auto s = sv->sessions.find(rq->session_id);

@@ -17,6 +17,17 @@
 namespace hbsd {
 
 static thread_local std::string g_last_error;
+
+int64_t& tl_dev_bytes() {
+    static thread_local int64_t bytes = 0;
+    return bytes;
+}
+
+int64_t& tl_dev_peak() {
+    static thread_local int64_t peak = 0;
+    return peak;
+}
+
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int code, const std::string& msg) {
     g_last_error = msg;

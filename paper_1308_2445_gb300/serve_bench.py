@@ -20,6 +20,7 @@ factor kept).  Every request runs in the mixed form to Res_max <= 1e-8.
 Prints one JSON line.
 """
 import argparse
+import dataclasses
 import json
 import os
 import sys
@@ -80,6 +81,7 @@ def run(hbsd, pool, reqs, slots, arrivals=None):
     returns per-request results and the wall time."""
     sv = hbsd.Server(max_slots=slots)
     sessions = {}   # pool index -> (session id, nev of its last solve)
+    evicted = [0]   # follow-ups whose session the server had evicted (resubmitted as new problems)
     done = []
     t0 = time.perf_counter()
     pending = {}
@@ -87,10 +89,19 @@ def run(hbsd, pool, reqs, slots, arrivals=None):
     def submit(k):
         i, nev, fol = reqs[k]
         name, p, follow = pool[i]
+        t = None
         if fol >= 0 and i in sessions and sessions[i][1] == nev:
-            t = sv.submit(nev, 1e-8, session_id=sessions[i][0], H_val=follow[fol], warm=True, want_vectors=False,
-                          is_complex=bool(np.iscomplexobj(p.h_val)))
-        else:
+            try:
+                t = sv.submit(nev, 1e-8, session_id=sessions[i][0], H_val=follow[fol], warm=True, want_vectors=False,
+                              is_complex=bool(np.iscomplexobj(p.h_val)))
+            except hbsd.HbsdError as e:
+                if e.code != hbsd.HBSD_ERR_ARG:
+                    raise
+                # the server evicted the session (memory): the SCF step goes in as a new problem
+                sessions.pop(i, None)
+                evicted[0] += 1
+                p = dataclasses.replace(p, h_val=follow[fol])
+        if t is None:
             t = sv.submit(nev, 1e-8, problem=p, want_vectors=False, precision=hbsd.PRECISION_MIXED)
         pending[t] = (k, time.perf_counter())
 
@@ -134,6 +145,7 @@ def run(hbsd, pool, reqs, slots, arrivals=None):
                 time.sleep(0.0002)
     wall = time.perf_counter() - t0
     sv.close()
+    run.evicted = evicted[0]
     return done, wall
 
 
@@ -156,17 +168,27 @@ def main():
     run(hbsd, pool, reqs[:1], 1)
     closed, t_closed = run(hbsd, pool, reqs, a.slots)
     capacity = len(reqs) / t_closed
+    print(json.dumps({"phase": "closed_loop", "requests": len(reqs), "wall_s": t_closed, "capacity_req_per_s": capacity,
+                      "failed": int(sum(1 for _, r in closed if r["status"] != 0))}), file=sys.stderr, flush=True)
     rng = np.random.default_rng(a.seed + 2)
     gaps = rng.exponential(1.0 / (a.load * capacity), size=len(reqs))
     arrivals = np.cumsum(gaps) - gaps[0]
+    evicted_closed = run.evicted
     served, t_served = run(hbsd, pool, reqs, a.slots, arrivals=arrivals)
+    evicted_served = run.evicted
     single, t_single = run(hbsd, pool, reqs, 1) if not a.skip_one_slot else ([], float("nan"))
     lat = np.array([r["latency_ms"] for _, r in served])
     conv = sum(reqs[k][1] for k, r in served if r["status"] == 0 and r["res_max"] <= 1e-8)
     conv_closed = sum(reqs[k][1] for k, r in closed if r["status"] == 0 and r["res_max"] <= 1e-8)
     conv_single = sum(reqs[k][1] for k, r in single if r["status"] == 0 and r["res_max"] <= 1e-8)
+    from collections import Counter
+    status_counts = {str(k): v for k, v in sorted(Counter(r["status"] for _, r in served).items())}
+    failures = [{"problem": pool[reqs[k][0]][0], "nev": reqs[k][1], "followup": reqs[k][2] >= 0,
+                 "status": r["status"], "iters": r["iters"], "res_max": r["res_max"]}
+                for k, r in served if r["status"] != 0][:20]
     line = {
         "metric": "served LABPSD solves: p50/p99 latency at Poisson arrivals, eigenpairs/s",
+        "status_counts": status_counts, "failures_first20": failures,
         "requests": len(reqs), "slots": a.slots, "load": a.load,
         "capacity_req_per_s": capacity,
         "served": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
@@ -175,6 +197,7 @@ def main():
         "closed_loop": {"eigenpairs_per_s": conv_closed / t_closed, "wall_s": t_closed},
         "one_slot": {"eigenpairs_per_s": conv_single / t_single, "wall_s": t_single},
         "followups": int(sum(1 for r in reqs if r[2] >= 0)),
+        "followups_resubmitted_after_eviction": {"closed_loop": evicted_closed, "served": evicted_served},
         "pool": [name for name, _, _ in pool],
         "precision": "mixed",
         "data": "synthetic",
