@@ -44,7 +44,7 @@ extern "C" {
 #define HBSD_ERR_RR_RANK    (-4)   /* search space rank below the number of wanted pairs   */
 #define HBSD_ERR_TIMEOUT    (-5)   /* a device-side wait gave up                           */
 #define HBSD_ERR_CUDA       (-6)   /* CUDA runtime error; see hbsd_last_error()            */
-#define HBSD_ERR_UNSUPPORTED (-7)  /* valid request for a feature this build does not have */
+#define HBSD_ERR_UNSUPPORTED (-7)  /* valid request for a feature the library lacks        */
 
 /* ---- problem description ----------------------------------------------------------- */
 
