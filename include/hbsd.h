@@ -258,6 +258,14 @@ int hbsd_solve_device(hbsd_handle* h, int nev, double tol, const double* X0_dev,
  * how many there are. */
 int hbsd_res_history(const hbsd_handle* h, double* out, int cap);
 
+/* The stall test of the mixed form's precision escalation (hbsd_options.spmm_df64), on a history
+ * of Res_max values (host, len doubles, in order): 1 when more than win entries follow index mark
+ * (the history length at the last switch), the best value before the last win entries is below
+ * `below`, and the best of the last win entries is above half of it; else 0.  The solve applies it
+ * with (win, below) = (10, 1e4 tol) and (30, +inf).  HBSD_ERR_ARG for len < 0, mark outside
+ * [0, len], win < 1 or a NULL hist with len > 0.  Host only. */
+int hbsd_res_stalled(const double* hist, int len, int mark, int win, double below);
+
 void hbsd_destroy(hbsd_handle* h);
 const char* hbsd_status_string(int status);
 const char* hbsd_last_error(void);

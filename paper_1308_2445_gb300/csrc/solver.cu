@@ -236,6 +236,17 @@ struct PhaseRule {
     int window;
 };
 
+// True when Res_max has stalled: more than `win` entries since `mark`, the best of the entries
+// before the last `win` is below `below`, and the best of the last `win` is above half of it.
+static bool res_stalled(const double* hist, size_t len, size_t mark, int win, double below) {
+    if (win < 1 || len < mark || (int64_t)(len - mark) <= win) return false;
+    double best_before = hist[0];
+    for (size_t i = 0; i + win < len; ++i) best_before = std::min(best_before, hist[i]);
+    double best_recent = hist[len - win];
+    for (size_t i = len - win; i < len; ++i) best_recent = std::min(best_recent, hist[i]);
+    return best_before < below && best_recent > 0.5 * best_before;
+}
+
 // LABPSD outline (Sec. 3) in precision T on the blocks of B, starting from Psi (n x w, ld ldw):
 // steps 1-3 (Rayleigh-Ritz on span(Psi)) then steps 4-11 until the rule stops it.  E_host and
 // Eprev carry the Ritz values across phases (remark 4 needs the previous ones).
@@ -366,12 +377,7 @@ static int labpsd_phase(Session* S, SolveBufs<T>& B, SolveCommon& C, int m, int 
         // FP64 too.  The first stage is cheap, so a false alarm on a slow but healthy trajectory
         // (a plateau of a cluster cut by the block edge) costs little.
         auto stalled = [&](int win, double below) -> bool {
-            if ((int)(hist.size() - esc_mark) <= win) return false;
-            double best_before = hist[0];
-            for (size_t i = 0; i + win < hist.size(); ++i) best_before = std::min(best_before, hist[i]);
-            double best_recent = hist[hist.size() - win];
-            for (size_t i = hist.size() - win; i < hist.size(); ++i) best_recent = std::min(best_recent, hist[i]);
-            return best_before < below && best_recent > 0.5 * best_before;
+            return res_stalled(hist.data(), hist.size(), esc_mark, win, below);
         };
         if ((dfs || dfp) && (stalled(10, 1e4 * rule.tol) || stalled(30, 1e300))) {
             if (dfs) {
@@ -989,6 +995,13 @@ int hbsd_seed_normals(uint64_t seed, uint64_t stream, int64_t count, double* out
 // ---- step-level entry points ---------------------------------------------------------------
 // A row-major block of `width` columns needs ld >= width (kernels would read past a row).
 static bool ld_ok(int64_t ld, int64_t width) { return width <= 0 || ld >= width; }
+
+int hbsd_res_stalled(const double* hist, int len, int mark, int win, double below) {
+    return guarded([&]() -> int {
+        if (len < 0 || mark < 0 || mark > len || win < 1 || (len > 0 && !hist)) return fail(HBSD_ERR_ARG, "bad arguments");
+        return res_stalled(hist, (size_t)len, (size_t)mark, win, below) ? 1 : 0;
+    });
+}
 
 int hbsd_res_history(const hbsd_handle* h, double* out, int cap) {
     return guarded([&]() -> int {

@@ -158,6 +158,7 @@ _SIGS = {
     "hbsd_probe_peak": (C.c_int, [C.c_int, _P, C.POINTER(C.c_double)]),
     "hbsd_seed_normals": (C.c_int, [C.c_uint64, C.c_uint64, C.c_int64, _D]),
     "hbsd_autotune": (C.c_int, [_P, C.c_int, C.POINTER(hbsd_tune)]),
+    "hbsd_res_stalled": (C.c_int, [_D, C.c_int, C.c_int, C.c_int, C.c_double]),
     "hbsd_batch_opts_default": (None, [C.POINTER(hbsd_batch_opts)]),
     "hbsd_solve_batch": (C.c_int, [C.POINTER(hbsd_batch_item), C.c_int, C.POINTER(hbsd_batch_opts)]),
 }
@@ -421,6 +422,13 @@ def seed_normals(seed, stream, count):
     out = np.empty(count)
     check(lib().hbsd_seed_normals(seed, stream, count, out.ctypes.data_as(_D)), "hbsd_seed_normals")
     return out
+
+
+def res_stalled(hist, mark, win, below):
+    """hbsd_res_stalled on a host history of Res_max values (True when the stall test fires)."""
+    h = np.ascontiguousarray(hist, dtype=np.float64)
+    return bool(check(lib().hbsd_res_stalled(h.ctypes.data_as(_D) if h.size else None, int(h.size), int(mark),
+                                             int(win), float(below)), "hbsd_res_stalled"))
 
 
 def solve_batch(entries, max_concurrent=8, autotune=True, longest_first=True):
