@@ -3,6 +3,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -163,3 +164,16 @@ def test_step_entry_points_refuse_a_short_leading_dimension(lib):
     # k > q is refused as before
     assert lib.hbsd_update(p, q, n, q, p, q + 1, None) == hbsd.HBSD_ERR_ARG
     assert b"bad arguments" in lib.hbsd_last_error()
+
+
+def test_server_admission_refuses_a_problem_beyond_its_budget_without_gpu():
+    # the footprint estimate of a new problem (matrix, factor at the measured fill, solve blocks)
+    # is checked against the budget at submission, on the host: a real 8^3 problem and its complex
+    # (Bloch) twin, whose real pencil is twice as large, against a 64 MiB budget
+    from paper_1308_2445_gb300 import hbsd, pufe_inputs as pi
+    sv = hbsd.Server(max_slots=1, hbm_budget_bytes=64 << 20)
+    for p in (pi.small_case(1), pi.generate(8, 2, 2, 0.25, 4, kpt=(0.5 * np.pi, 0.5 * np.pi, 0.5 * np.pi))):
+        with pytest.raises(hbsd.HbsdError) as e:
+            sv.submit(16, 1e-8, problem=p, want_vectors=False)
+        assert e.value.code == hbsd.HBSD_ERR_OOM
+    sv.close()
