@@ -516,3 +516,19 @@ def test_labpsd_with_an_interior_global_shift_matches_dense_eigh():
     r = L.labpsd(p, 16, 1e-10, seed=2, precond=K)
     assert r.converged
     assert np.allclose(r.lam, lam[:16], rtol=0, atol=1e-8 * np.abs(lam[:16]).max())
+
+
+def test_global_shift_has_little_influence(small_problem):
+    """Sec. 5: the choice of the global shift eps_bar barely matters.  Lowering it by 0.5 to 4
+    times its distance to zero (all below the spectrum) leaves the eigenvalues unchanged to
+    rounding and the outer iteration count within one of the generator's choice."""
+    import dataclasses
+    p = small_problem
+    X0 = pi.seed_normal_block(1, p.n, 16 + L.default_m0(16))
+    base = L.labpsd(p, 16, 1e-8, X0=X0)
+    assert base.converged
+    for f in (0.5, 2.0, 4.0):
+        q = dataclasses.replace(p, eps_bar=p.eps_bar - f * abs(p.eps_bar))
+        r = L.labpsd(q, 16, 1e-8, X0=X0)
+        assert r.converged and abs(r.iters - base.iters) <= 1
+        assert np.abs(r.lam - base.lam).max() <= 1e-12 * np.abs(base.lam).max()
