@@ -532,3 +532,16 @@ def test_global_shift_has_little_influence(small_problem):
         r = L.labpsd(q, 16, 1e-8, X0=X0)
         assert r.converged and abs(r.iters - base.iters) <= 1
         assert np.abs(r.lam - base.lam).max() <= 1e-12 * np.abs(base.lam).max()
+
+
+def test_minres_from_the_globally_preconditioned_start_needs_few_steps(small_problem):
+    """Sec. 3/5: started from the globally preconditioned vector, the local MINRES meets eta in a
+    handful of steps (the paper reports 2-5).  On the small case every refined column takes at
+    most 5, and a start from zero (the local-only scheme) takes more on average."""
+    p = small_problem
+    r = L.labpsd(p, 16, 1e-8, seed=1)
+    steps = np.concatenate([np.asarray(s) for s in r.minres_steps if len(s)])
+    assert r.converged and steps.size > 0 and steps.max() <= 5
+    lo = L.labpsd(p, 16, 1e-8, seed=1, opts=L.Options(use_global=False, max_outer=30))
+    steps0 = np.concatenate([np.asarray(s) for s in lo.minres_steps if len(s)])
+    assert steps0.mean() > steps.mean()
